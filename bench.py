@@ -1,0 +1,381 @@
+"""Benchmark: MBPCG time-to-solution (relative residual 1e-8) against Chronopoulos-Gear CG from the
+same library, on one GB300.
+
+A step is one full MBPCG solve of the workload (set-up, every Algorithm 1 iteration, the
+least-squares exit and the true-residual check). Default workload: the dense SPD system
+n = 4096, A = Q diag(lambda) Q^T with lambda log-uniform in [1, 1e6], FP64, s copies.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--s S] [--workload NAME]
+    python bench.py --impl reference ...   (the FP64 CPU oracle, timed on the host cores)
+
+Prints one JSON line (rank 0). Under torchrun each rank solves its own replica (the solve does
+not shard across GPUs here; replicas only), the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "MBPCG time-to-relres 1e-8 vs plain CG, 1 GB300; SpMM HBM roofline %; p99 latency"
+UNIT = "ms"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+L2_FLUSH_BYTES = 256 << 20
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "dense4096": dict(desc="dense SPD n=4096, A=Q diag(lambda) Q^T, lambda=10^U[0,6], b,U~U(-1,1), FP64, tol 1e-8",
+                      precond=0, tol=1e-8, s=16),
+    "poisson64": dict(desc="2D 5-point Poisson 64x64 (n=4096, nnz=20224), CSR int32/FP64, tol 1e-8",
+                      precond=0, tol=1e-8, s=4),
+    "diffusion128": dict(desc="3D 7-point variable-coefficient diffusion 128^3 (n=2097152, nnz=14581760), "
+                              "Jacobi scaling, tol 1e-8", precond=1, tol=1e-8, s=4),
+}
+
+
+def make_matrix(name):
+    if name == "dense4096":
+        return wl.dense_spd(4096, 0)
+    if name == "poisson64":
+        return wl.poisson2d(64)
+    if name == "diffusion128":
+        return wl.diffusion3d(128, 0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="dense4096", choices=sorted(WORKLOADS))
+    p.add_argument("--s", type=int, default=None)
+    p.add_argument("--kernel-launches", type=int, default=20, help="launches of the dominant kernel timed alone")
+    p.add_argument("--cpu-sample-iters", type=int, default=6)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("row_kernels.cuh", "mbpcg_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2608_07327_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload, s):
+    try:
+        data = json.load(open(PROFILE_TRAFFIC))
+    except (OSError, ValueError):
+        return None
+    rec = data.get(f"{kernel}:{workload}:s{s}")
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def launches_per_solve(info, dense, algo_cg):
+    """Kernels of ours launched by one solve call (the counter of the graph the library builds)."""
+    inner = info["restarts"] + 1
+    if algo_cg:
+        setup, exit_, body = 3, 5, 5
+    else:
+        setup, exit_, body = 8, 7, (8 if dense else 7)
+    return inner * (1 + setup + exit_) + body * info["iterations"] + (0 if algo_cg else 1)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2608_07327_gb300 as mb
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg = WORKLOADS[args.workload]
+    s = args.s or cfg["s"]
+    A = make_matrix(args.workload)
+    dense = isinstance(A, wl.Dense)
+    n = A.n
+    b = wl.rhs(n, 0)
+    U = wl.initial_block(n, s, 1)
+    dev = torch.device("cuda", local)
+    solver = mb.Solver(A, s=s, precond=cfg["precond"])
+    cg = mb.Solver(A, algo=mb.MBPCG_ALGO_CG, precond=cfg["precond"])
+    stream = solver.stream
+    bd = torch.as_tensor(b, device=dev)
+    Ud = torch.as_tensor(np.asfortranarray(U).ravel(order="F"), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(sv, Uarg, k):
+        times, infos, xs = [], [], None
+        for _ in range(k):
+            with torch.cuda.stream(sv.stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(sv.stream)
+            x, info = sv.solve(bd, Uarg, tol=cfg["tol"])
+            e1.record(sv.stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+            xs = x
+        return times, infos, xs
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    timed(solver, Ud, args.warmup)
+    timed(cg, None, max(1, min(args.warmup, 2)))
+    barrier()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        times, infos, x = timed(solver, Ud, args.steps)
+        barrier()
+        wall = time.perf_counter() - t0
+        cg_times, cg_infos, xc = timed(cg, None, args.steps)
+        barrier()
+    total_ms = sum(times)
+    cg_total = sum(cg_times)
+    if world > 1:
+        t = torch.tensor([total_ms, cg_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, cg_total = t.tolist()
+    ms_per_step = total_ms / args.steps
+    cg_ms = cg_total / args.steps
+    info = infos[-1]
+    xh = x.cpu().numpy()
+    Amul = (lambda v: np.asarray(A.a) @ v) if dense else (lambda v: A.to_scipy() @ v)
+    relres_check = float(np.linalg.norm(b - Amul(xh)) / np.linalg.norm(b))
+
+    # dominant kernel alone, same launch configuration, CUDA events on its stream
+    kp = mb.mbpcg_k_padded_width(s)
+    P = torch.as_tensor(np.ascontiguousarray(np.pad(U, ((0, 0), (0, kp - s)))), device=dev)
+    AP = torch.empty_like(P)
+    if dense:
+        Ad = torch.as_tensor(np.asfortranarray(A.a).ravel(order="F"), device=dev)
+        launch = lambda: mb.mbpcg_k_dense_product(n, Ad, s, P, AP, stream.cuda_stream)  # noqa: E731
+        kname = "k_dense"
+        flops = 2.0 * n * n * s
+        nbytes = 8.0 * n * n + 16.0 * n * kp
+    else:
+        rp = torch.as_tensor(A.row_ptr, device=dev)
+        ci = torch.as_tensor(A.col_idx, device=dev)
+        av = torch.as_tensor(A.val, device=dev)
+        launch = lambda: mb.mbpcg_k_spmm(n, rp, ci, av, s, P, AP, stream.cuda_stream)  # noqa: E731
+        kname = "k_spmm"
+        flops = 2.0 * A.nnz * s
+        nbytes = 12.0 * A.nnz + 4.0 * (n + 1) + 16.0 * n * kp
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            launch()
+        k_ms = []
+        for _ in range(args.kernel_launches):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            launch()
+            ev1.record(stream)
+            ev1.synchronize()
+            k_ms.append(ev0.elapsed_time(ev1))
+    k_avg = sum(k_ms) / len(k_ms)
+    achieved_tflops = flops / (k_avg * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"{kname}<{kp}> (FP64 pipe)", "achieved": round(achieved_tflops, 4),
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
+                "traffic": recorded_traffic(kname, args.workload, s),
+                "kernel_ms": round(k_avg, 5), "algorithmic_flops": flops, "algorithmic_bytes": nbytes,
+                "hbm_gbs_equiv": round(nbytes / (k_avg * 1e-3) / 1e9, 1),
+                "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (probe measured 1.20 TFLOP/s)"}
+
+    # end to end through the public host-buffer API (pinned host memory in, x out)
+    b_pin = torch.from_numpy(b).pin_memory()
+    U_pin = torch.from_numpy(np.asfortranarray(U).ravel(order="F")).pin_memory()
+    x_pin = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e = []
+    for it in range(args.steps + 1):
+        t1 = time.perf_counter()
+        st, inf = mb.mbpcg_solve(solver.h, b_pin.data_ptr(), U_pin.data_ptr(), cfg["tol"], 100000, x_pin.data_ptr())
+        t2 = time.perf_counter()
+        if it > 0:
+            e2e.append((t2 - t1) * 1e3)
+    e2e_ms = sum(e2e) / len(e2e)
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(ms_per_step, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "n": n, "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
+                       "tol": cfg["tol"], "l2": "flushed before every step (256 MB write)",
+                       "parallelism": "replicas only" if world > 1 else "single GPU"},
+            "iterations": info["iterations"], "restarts": info["restarts"], "relres_true": relres_check,
+            "cg_ms": round(cg_ms, 4), "cg_iterations": cg_infos[-1]["iterations"],
+            "speedup_vs_cg": round(cg_ms / ms_per_step, 4),
+            "us_per_iteration": round(1e3 * ms_per_step / max(1, info["iterations"]), 3),
+            "cg_us_per_iteration": round(1e3 * cg_ms / max(1, cg_infos[-1]["iterations"]), 3),
+            "solves_per_s": round(world * args.steps / (total_ms * 1e-3), 4),
+            "wall_s_timed": round(wall, 3),
+            "roofline": roofline,
+            "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": 8 * n + 8 * n * s,
+                    "d2h_bytes_per_step": 8 * n + 200 * (info["restarts"] + 1)},
+            "gpu_launches": sum(launches_per_solve(i, dense, False) for i in infos),
+            "clocks": clk.summary(),
+        }
+    solver.close()
+    cg.close()
+    return line
+
+
+def oracle_sample(args, A, s, precond, iters):
+    """Time `iters` oracle iterations (plus its set-up) on this host; returns seconds/iteration."""
+    import oracle
+    b = wl.rhs(A.n, 0)
+    U = wl.initial_block(A.n, s, 1)
+    t0 = time.perf_counter()
+    oracle.mbpcg_state(A, b, U, 0, precond=precond)
+    t1 = time.perf_counter()
+    oracle.mbpcg_state(A, b, U, iters, precond=precond)
+    t2 = time.perf_counter()
+    return ((t2 - t1) - (t1 - t0)) / iters, (t1 - t0)
+
+
+def full_solve_iterations(workload, s):
+    path = os.path.join(ROOT, "oracle", "full_solve_counts.json")
+    try:
+        return json.load(open(path))[workload][str(s)]["iterations"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(args, A, s, precond, gpu_iterations):
+    per_it, setup = oracle_sample(args, A, s, precond, args.cpu_sample_iters)
+    its = full_solve_iterations(args.workload, s) or gpu_iterations
+    return {"value": round((setup + per_it * its) * 1e3, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{args.cpu_sample_iters} oracle iterations (+ set-up) timed on one host core, scaled to the "
+                      f"{its} iterations of the full solve"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    cfg = WORKLOADS[args.workload]
+    s = args.s or cfg["s"]
+    A = make_matrix(args.workload)
+    its = full_solve_iterations(args.workload, s)
+    if its is None:
+        return {"impl": "reference", "unavailable": f"no recorded oracle iteration count for {args.workload} s={s}"}
+    per = []
+    for k in range(args.warmup + args.steps):
+        p, setup = oracle_sample(args, A, s, cfg["precond"], max(1, args.cpu_sample_iters // 2))
+        if k >= args.warmup:
+            per.append((setup + p * its) * 1e3)
+    ms = sum(per) / len(per)
+    return {"impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["desc"], "n": A.n, "s": s, "precond": cfg["precond"], "tol": cfg["tol"]},
+            "cpu_baseline": {"value": round(ms, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {max(1, args.cpu_sample_iters // 2)} oracle iterations (+ set-up)"
+                                       f" on one host core, scaled to the oracle's {its}-iteration full solve"},
+            "e2e": {"value": round(ms, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_ours(args, world, rank, local)
+        if line is not None and world == 1 and not args.no_cpu_baseline:
+            cfg = WORKLOADS[args.workload]
+            A = make_matrix(args.workload)
+            line["cpu_baseline"] = cpu_baseline(args, A, line["config"]["s"], cfg["precond"], line["iterations"])
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl != "reference":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

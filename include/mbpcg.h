@@ -1,0 +1,141 @@
+/*
+ * mbpcg.h -- C ABI of the GB300 (sm_103a) Multi-Basis Parallel Conjugate Gradient library.
+ *
+ * The method (Algorithm 1, Section 2 of the paper): solve one SPD system A x = b by running block
+ * CG (Dubrulle-R form, Cholesky QR of Section 3) over s copies of the system that start from
+ * s random initial guesses, and return the least-squares combination of the s iterates.
+ * The paper's baseline, Chronopoulos-Gear CG (Section 1, Section 4), runs through the same API.
+ *
+ * Everything after create runs on the GPU: set-up, every iteration, the exit step and the
+ * true-residual check. The library never falls back to a CPU path; without a usable CUDA
+ * device every call returns MBPCG_ERR_CUDA.
+ *
+ * Memory and ownership
+ *   - Functions without the _dev suffix take HOST pointers; they copy in and out on the handle's
+ *     stream and return after the result is on the host.
+ *   - Functions with the _dev suffix take DEVICE pointers (any allocation visible to the device,
+ *     e.g. a torch tensor's data_ptr) and return after the result is written (the call ends with
+ *     a synchronisation of the handle's stream).
+ *   - The handle owns every internal buffer. They are sized at create for (n, nnz, s) and either
+ *     allocated by the library (workspace == NULL) or carved out of a caller-provided device
+ *     workspace of at least mbpcg_workspace_size_*() bytes (the caller keeps ownership and must
+ *     keep it alive until mbpcg_destroy).
+ *   - Blocks of s vectors crossing the ABI (U) are column-major n x s, as the paper stores dense
+ *     matrices (Section 3). Inside, blocks are row-major with s padded to a power of two.
+ *
+ * Errors: every int-returning function returns an mbpcg_status. Nothing aborts or throws across
+ * the ABI. mbpcg_last_error() gives a thread-local message for the last failure.
+ * Threading: a handle is not thread-safe; distinct handles may be used concurrently.
+ */
+#ifndef MBPCG_H
+#define MBPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mbpcg_ctx* mbpcg_handle;
+
+typedef enum {
+  MBPCG_OK = 0,
+  MBPCG_ERR_INVALID = 1,   /* bad argument or malformed CSR (checked at create) */
+  MBPCG_ERR_OOM = 2,       /* device allocation failed or workspace too small */
+  MBPCG_ERR_CUDA = 3,      /* CUDA runtime error (see mbpcg_last_error) */
+  MBPCG_ERR_NOT_SPD = 4,   /* a diagonal entry is missing, not positive or not finite */
+  MBPCG_NOT_CONVERGED = 5, /* maxit reached; x_out holds the best iterate */
+  MBPCG_BREAKDOWN = 6,     /* a k x k Cholesky pivot was not positive; x_out holds the best iterate */
+  MBPCG_ERR_TIMEOUT = 7    /* reserved: a device-side wait exceeded its limit */
+} mbpcg_status;
+
+/* Symmetric diagonal scaling of Section 1: D = diag(sqrt(A_jj)), the solver runs on
+ * D^{-1} A D^{-1}; residual norms and the tolerance refer to the original system. */
+typedef enum { MBPCG_PRECOND_NONE = 0, MBPCG_PRECOND_JACOBI = 1 } mbpcg_precond;
+
+/* MBPCG = Algorithm 1 with s copies; CG = Chronopoulos-Gear CG with zero initial guess (the
+ * paper's baseline, Section 4), s ignored. */
+typedef enum { MBPCG_ALGO_MBPCG = 0, MBPCG_ALGO_CG = 1 } mbpcg_algo;
+
+/* Arithmetic of the n-proportional work. FP64: everything in double precision. */
+typedef enum { MBPCG_FP64 = 0 } mbpcg_precision;
+
+typedef struct {
+  int32_t iterations;        /* inner iterations summed over restarts */
+  int32_t restarts;          /* true-residual restarts taken (at most 3) */
+  int32_t status;            /* mbpcg_status of the solve */
+  int32_t best_col;          /* h = argmin_j ||R_j|| at the last exit test */
+  int32_t ls_fallback;       /* 1 if the last exit used column h instead of the LS combination */
+  int32_t reserved;
+  double relres_recurrence;  /* ||R_h|| / ||b|| at the last exit test (original metric) */
+  double relres_ls;          /* ||b - Bhat c|| / ||b|| of the last exit combination */
+  double relres_true;        /* ||b - A x|| / ||b|| recomputed on the device from A */
+  double seconds;            /* device time of the solve call (CUDA events) */
+} mbpcg_info;
+
+/* Workspace bytes a handle needs (device memory), for callers that allocate it themselves. */
+size_t mbpcg_workspace_size_csr(int32_t n, int64_t nnz, int32_t s, int32_t algo, int32_t precision);
+size_t mbpcg_workspace_size_dense(int32_t n, int32_t s, int32_t algo, int32_t precision);
+
+/*
+ * Create a solver for sparse A in CSR form (int32 row_ptr[n+1], int32 col_idx[nnz], double
+ * vals[nnz], full symmetric storage, any column order within a row).
+ *   mem       0: the three arrays are host pointers; 1: device pointers.
+ *   s         number of copies, 1 <= s <= 32 (ignored for MBPCG_ALGO_CG).
+ *   seed      seed of the counter-based generator used when mbpcg_solve gets U == NULL.
+ *   workspace device buffer of mbpcg_workspace_size_csr() bytes, or NULL to let the library
+ *             allocate; stream: a cudaStream_t, or NULL for a stream owned by the handle.
+ * Validation: 1 <= n, 0 <= nnz < 2^31, row_ptr[0] = 0, row_ptr monotone, row_ptr[n] = nnz,
+ * 0 <= col_idx < n (MBPCG_ERR_INVALID); every row has a positive finite diagonal
+ * (MBPCG_ERR_NOT_SPD). Symmetry is a precondition and is not checked.
+ */
+int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* row_ptr,
+                     const int32_t* col_idx, const double* vals, int32_t s, int32_t precond,
+                     int32_t algo, int32_t precision, uint64_t seed, int32_t mem, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* Create a solver for dense SPD A (column-major n x n doubles; A symmetric, so either triangle
+ * may be read). Same conventions as mbpcg_create_csr. */
+int mbpcg_create_dense(mbpcg_handle* out, int32_t n, const double* A_colmajor, int32_t s,
+                       int32_t precond, int32_t algo, int32_t precision, uint64_t seed,
+                       int32_t mem, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Solve A x = b to ||b - A x|| / ||b|| <= tol (Algorithm 1 with initial tolerance = convergence
+ * tolerance = tol, as the paper's implementation sets them, Section 2).
+ *   b     n doubles (host).     U: n x s column-major initial block (host) or NULL to draw it
+ *         from Uniform(-1,1) with the handle's seed (SplitMix64, counter-based).
+ *   maxit cap on inner iterations over all restarts (>= 1).
+ *   x_out n doubles (host), caller-allocated. Filled on MBPCG_OK, MBPCG_NOT_CONVERGED and
+ *         MBPCG_BREAKDOWN (best iterate). info may be NULL.
+ * After the recurrence test passes, the residual b - A x is recomputed from A; while it exceeds
+ * tol the solver restarts on the correction system (at most 3 times).
+ */
+int mbpcg_solve(mbpcg_handle h, const double* b, const double* U, double tol, int32_t maxit,
+                double* x_out, mbpcg_info* info);
+
+/* As mbpcg_solve with b, U (or NULL) and x_out in device memory. */
+int mbpcg_solve_dev(mbpcg_handle h, const double* b, const double* U, double tol, int32_t maxit,
+                    double* x_out, mbpcg_info* info);
+
+/*
+ * Diagnostic: run exactly `iters` iterations of Algorithm 1 (no exit test, no restart) from
+ * the set-up with b and U (device pointers) and copy the state of the scaled system out to
+ * device buffers, column-major n x s (X0, Xt, R, W, P) and s x s (Sigma). Any output pointer may
+ * be NULL. MBPCG_ALGO_MBPCG handles only.
+ */
+int mbpcg_run_iterations_dev(mbpcg_handle h, const double* b, const double* U, int32_t iters,
+                             double* X0, double* Xt, double* R, double* W, double* P,
+                             double* Sigma);
+
+/* Release a handle (NULL is ignored). */
+void mbpcg_destroy(mbpcg_handle h);
+
+const char* mbpcg_status_string(int status);
+const char* mbpcg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

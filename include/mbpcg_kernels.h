@@ -1,0 +1,58 @@
+/*
+ * mbpcg_kernels.h -- component entry points of the MBPCG library, for callers (and tests) that
+ * drive single steps of Algorithm 1 on their own device buffers.
+ *
+ * All pointers are DEVICE pointers; calls are asynchronous on `stream` (a cudaStream_t, NULL =
+ * legacy default stream) and return after enqueueing. Blocks are row-major n x kp with
+ * kp = mbpcg_k_padded_width(s) (s rounded up to a power of two); columns s..kp-1 of P must be
+ * zero. Small outputs are column-major s x s doubles. Errors: MBPCG_ERR_INVALID for bad
+ * arguments, MBPCG_ERR_CUDA for a failed launch (mbpcg_last_error() has the message).
+ */
+#ifndef MBPCG_KERNELS_H
+#define MBPCG_KERNELS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Padded row width used for s copies (1, 2, 4, 8, 16 or 32); 0 when s is outside [1, 32]. */
+int32_t mbpcg_k_padded_width(int32_t s);
+
+/* Bytes of device scratch the product+Gram entry points need (per-CTA partial sums). The caller
+ * allocates it; contents need no initialisation and are overwritten. */
+size_t mbpcg_k_scratch_bytes(int32_t n, int32_t s);
+
+/*
+ * The A P product of Algorithm 1 (the step that dominates Table 2 of the paper) fused with the
+ * Gram matrix that defines Xi: AP = A P for CSR A (int32 row_ptr[n+1], int32 col_idx, double
+ * vals), and G = P^T (A P) (s x s, symmetric; the upper triangle is accumulated and mirrored).
+ * Summation order is fixed, so repeated calls give identical bits.
+ */
+int mbpcg_k_spmm_gram(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                      int32_t s, const double* P, double* AP, double* G, void* scratch,
+                      size_t scratch_bytes, void* stream);
+
+/* Same for dense symmetric A (column-major n x n; row i is read as column i). */
+int mbpcg_k_dense_gram(int32_t n, const double* A, int32_t s, const double* P, double* AP,
+                       double* G, void* scratch, size_t scratch_bytes, void* stream);
+
+/* The product alone, in the launch configuration the solver uses inside its iteration loop:
+ * AP = A P for CSR A (mbpcg_k_spmm) or dense symmetric column-major A (mbpcg_k_dense_product).
+ * No scratch. Used to time the dominant kernel of an iteration in isolation. */
+int mbpcg_k_spmm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                 int32_t s, const double* P, double* AP, void* stream);
+int mbpcg_k_dense_product(int32_t n, const double* A, int32_t s, const double* P, double* AP,
+                          void* stream);
+
+/* Z = upper Cholesky factor of the SPD s x s matrix G (G = Z^T Z, positive diagonal), the k x k
+ * factorisation used for Xi (Section 3) and for the Cholesky QR. *status_dev (device int) is set
+ * to 0, or to 6 (MBPCG_BREAKDOWN) when a pivot is not finite or not above 64 eps max_j G_jj. */
+int mbpcg_k_cholesky(int32_t s, const double* G, double* Z, int32_t* status_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

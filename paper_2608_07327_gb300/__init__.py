@@ -1,0 +1,102 @@
+"""GB300-native Multi-Basis Parallel Conjugate Gradient (MBPCG).
+
+The solver is the CUDA library libmbpcg.so (C ABI in include/mbpcg.h); this package is its
+binding. ``Solver`` wraps a handle: torch provides the device workspace and the stream, the library
+does every step of the solve on the GPU (set-up, Algorithm 1 iterations, least-squares exit,
+true-residual check). There is no CPU fallback: without a CUDA device creation raises.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _native
+from ._native import (  # noqa: F401  (re-exported C ABI names)
+    Info, MBPCGError, lib, lib_path, mbpcg_create_csr, mbpcg_create_dense, mbpcg_destroy, mbpcg_k_cholesky,
+    mbpcg_k_dense_gram, mbpcg_k_dense_product, mbpcg_k_spmm, mbpcg_k_padded_width, mbpcg_k_scratch_bytes, mbpcg_k_spmm_gram, mbpcg_run_iterations_dev,
+    mbpcg_solve, mbpcg_solve_dev, mbpcg_workspace_size_csr, mbpcg_workspace_size_dense, status_string, last_error,
+    MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,
+    MBPCG_ALGO_CG, MBPCG_FP64)
+
+__all__ = ["Solver", "Info", "MBPCGError", "lib", "lib_path"]
+
+
+class Solver:
+    """One handle of the library for a fixed matrix and number of copies s.
+
+    A: an object with (n, row_ptr, col_idx, val) numpy arrays (CSR) or (n, a) with a column-major
+       n x n array (dense), e.g. ``workloads.CSR`` / ``workloads.Dense``.
+    The workspace is a torch uint8 CUDA tensor; calls run on a dedicated torch stream that first
+    waits for the caller's current stream."""
+
+    def __init__(self, A, s: int = 4, precond: int = 0, algo: int = 0, seed: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("MBPCG needs a CUDA device (GB300, sm_103a); no CPU path exists")
+        self.n = int(A.n)
+        self.s = int(s) if algo == MBPCG_ALGO_MBPCG else 1
+        self.algo = algo
+        self.dense = not hasattr(A, "row_ptr")
+        # a stream of our own, ordered after the caller's work before every call
+        self.stream = torch.cuda.Stream()
+        if self.dense:
+            nbytes = mbpcg_workspace_size_dense(self.n, self.s, algo)
+        else:
+            nbytes = mbpcg_workspace_size_csr(self.n, int(A.row_ptr[-1]), self.s, algo)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        if self.dense:
+            a = np.asfortranarray(A.a, dtype=np.float64)
+            self.h = mbpcg_create_dense(self.n, a, self.s, precond, algo, 0, seed, 0, self.workspace, nbytes,
+                                        self.stream.cuda_stream)
+        else:
+            rp = np.ascontiguousarray(A.row_ptr, dtype=np.int32)
+            ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+            v = np.ascontiguousarray(A.val, dtype=np.float64)
+            self.h = mbpcg_create_csr(self.n, int(rp[-1]), rp, ci, v, self.s, precond, algo, 0, seed, 0,
+                                      self.workspace, nbytes, self.stream.cuda_stream)
+
+    def solve(self, b, U=None, tol: float = 1e-8, maxit: int = 100000):
+        """Solve A x = b. b (and U, n x s column-major) are numpy arrays (host path, mbpcg_solve)
+        or torch CUDA tensors (device path, mbpcg_solve_dev). Returns (x, info dict)."""
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+        if hasattr(b, "is_cuda") and b.is_cuda:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+            Ud = None
+            if U is not None:
+                Ud = U.t().contiguous() if U.dim() == 2 else U  # column-major n x s == row-major s x n
+            st, info = mbpcg_solve_dev(self.h, b, Ud, tol, maxit, x)
+        else:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            Uh = None if U is None else np.asfortranarray(U, dtype=np.float64)
+            x = np.zeros(self.n)
+            st, info = mbpcg_solve(self.h, b, Uh, tol, maxit, x)
+        if st not in (MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN):
+            raise MBPCGError(st, "mbpcg_solve")
+        return x, info.as_dict()
+
+    def run_iterations(self, b, U, iters: int):
+        """Diagnostic: the state of the scaled system after exactly `iters` iterations, as torch
+        tensors (n x s blocks X0, Xt, R, W, P and Sigma s x s)."""
+        import torch
+        dev = torch.device("cuda")
+        self.stream.wait_stream(torch.cuda.current_stream())
+        bt = torch.as_tensor(np.ascontiguousarray(b, dtype=np.float64), device=dev)
+        Ut = torch.as_tensor(np.ascontiguousarray(np.asarray(U, dtype=np.float64).T), device=dev)
+        out = {k: torch.empty((self.s, self.n), dtype=torch.float64, device=dev) for k in ("X0", "Xt", "R", "W", "P")}
+        out["Sigma"] = torch.empty((self.s, self.s), dtype=torch.float64, device=dev)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        st = mbpcg_run_iterations_dev(self.h, bt, Ut, iters, out["X0"], out["Xt"], out["R"], out["W"], out["P"],
+                                      out["Sigma"])
+        res = {k: v.t().cpu().numpy() for k, v in out.items()}
+        return res, st
+
+    def close(self):
+        if getattr(self, "h", None):
+            mbpcg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,200 @@
+"""ctypes binding of libmbpcg.so: the C ABI of include/mbpcg.h and include/mbpcg_kernels.h under the
+same names, with argument marshalling only (numpy arrays -> host pointers, torch CUDA tensors ->
+device pointers). Every computation runs in the CUDA library; there is no Python or CPU path, and
+loading fails loudly when the library cannot be built or loaded."""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import build as _build
+
+MBPCG_OK = 0
+MBPCG_ERR_INVALID = 1
+MBPCG_ERR_OOM = 2
+MBPCG_ERR_CUDA = 3
+MBPCG_ERR_NOT_SPD = 4
+MBPCG_NOT_CONVERGED = 5
+MBPCG_BREAKDOWN = 6
+MBPCG_ERR_TIMEOUT = 7
+MBPCG_PRECOND_NONE = 0
+MBPCG_PRECOND_JACOBI = 1
+MBPCG_ALGO_MBPCG = 0
+MBPCG_ALGO_CG = 1
+MBPCG_FP64 = 0
+
+
+class Info(ctypes.Structure):
+    """mbpcg_info."""
+    _fields_ = [
+        ("iterations", ctypes.c_int32),
+        ("restarts", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("best_col", ctypes.c_int32),
+        ("ls_fallback", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("relres_recurrence", ctypes.c_double),
+        ("relres_ls", ctypes.c_double),
+        ("relres_true", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class MBPCGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status}): {last_error()}")
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_SZ = ctypes.c_size_t
+_D = ctypes.c_double
+
+_SIGS = {
+    "mbpcg_workspace_size_csr": (_SZ, [_I32, _I64, _I32, _I32, _I32]),
+    "mbpcg_workspace_size_dense": (_SZ, [_I32, _I32, _I32, _I32]),
+    "mbpcg_create_csr": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _I64, _P, _P, _P, _I32, _I32, _I32, _I32,
+                                        ctypes.c_uint64, _I32, _P, _SZ, _P]),
+    "mbpcg_create_dense": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _P, _I32, _I32, _I32, _I32, ctypes.c_uint64,
+                                          _I32, _P, _SZ, _P]),
+    "mbpcg_solve": (ctypes.c_int, [_P, _P, _P, _D, _I32, _P, ctypes.POINTER(Info)]),
+    "mbpcg_solve_dev": (ctypes.c_int, [_P, _P, _P, _D, _I32, _P, ctypes.POINTER(Info)]),
+    "mbpcg_run_iterations_dev": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P]),
+    "mbpcg_destroy": (None, [_P]),
+    "mbpcg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mbpcg_last_error": (ctypes.c_char_p, []),
+    "mbpcg_k_padded_width": (_I32, [_I32]),
+    "mbpcg_k_scratch_bytes": (_SZ, [_I32, _I32]),
+    "mbpcg_k_spmm_gram": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "mbpcg_k_dense_gram": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "mbpcg_k_cholesky": (ctypes.c_int, [_I32, _P, _P, _P, _P]),
+    "mbpcg_k_spmm": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
+    "mbpcg_k_dense_product": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libmbpcg.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def ptr(x):
+    """Raw address of a numpy array / torch tensor / int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def status_string(status: int) -> str:
+    return lib().mbpcg_status_string(status).decode()
+
+
+def last_error() -> str:
+    return lib().mbpcg_last_error().decode()
+
+
+def mbpcg_workspace_size_csr(n, nnz, s, algo=MBPCG_ALGO_MBPCG, precision=MBPCG_FP64) -> int:
+    return int(lib().mbpcg_workspace_size_csr(n, nnz, s, algo, precision))
+
+
+def mbpcg_workspace_size_dense(n, s, algo=MBPCG_ALGO_MBPCG, precision=MBPCG_FP64) -> int:
+    return int(lib().mbpcg_workspace_size_dense(n, s, algo, precision))
+
+
+def mbpcg_create_csr(n, nnz, row_ptr, col_idx, vals, s, precond=0, algo=0, precision=0, seed=0, mem=0,
+                     workspace=None, workspace_bytes=0, stream=None):
+    h = _P()
+    st = lib().mbpcg_create_csr(ctypes.byref(h), n, nnz, ptr(row_ptr), ptr(col_idx), ptr(vals), s, precond, algo,
+                                precision, seed, mem, ptr(workspace), workspace_bytes, stream)
+    if st != MBPCG_OK:
+        raise MBPCGError(st, "mbpcg_create_csr")
+    return h
+
+
+def mbpcg_create_dense(n, A, s, precond=0, algo=0, precision=0, seed=0, mem=0, workspace=None, workspace_bytes=0,
+                       stream=None):
+    h = _P()
+    st = lib().mbpcg_create_dense(ctypes.byref(h), n, ptr(A), s, precond, algo, precision, seed, mem,
+                                  ptr(workspace), workspace_bytes, stream)
+    if st != MBPCG_OK:
+        raise MBPCGError(st, "mbpcg_create_dense")
+    return h
+
+
+def mbpcg_solve(h, b, U, tol, maxit, x_out):
+    info = Info()
+    st = lib().mbpcg_solve(h, ptr(b), ptr(U), tol, maxit, ptr(x_out), ctypes.byref(info))
+    return st, info
+
+
+def mbpcg_solve_dev(h, b, U, tol, maxit, x_out):
+    info = Info()
+    st = lib().mbpcg_solve_dev(h, ptr(b), ptr(U), tol, maxit, ptr(x_out), ctypes.byref(info))
+    return st, info
+
+
+def mbpcg_run_iterations_dev(h, b, U, iters, X0=None, Xt=None, R=None, W=None, P=None, Sigma=None):
+    return lib().mbpcg_run_iterations_dev(h, ptr(b), ptr(U), iters, ptr(X0), ptr(Xt), ptr(R), ptr(W), ptr(P),
+                                          ptr(Sigma))
+
+
+def mbpcg_destroy(h):
+    if h:
+        lib().mbpcg_destroy(h)
+
+
+def mbpcg_k_padded_width(s) -> int:
+    return int(lib().mbpcg_k_padded_width(s))
+
+
+def mbpcg_k_scratch_bytes(n, s) -> int:
+    return int(lib().mbpcg_k_scratch_bytes(n, s))
+
+
+def mbpcg_k_spmm_gram(n, row_ptr, col_idx, vals, s, P, AP, G, scratch, scratch_bytes, stream=None):
+    return lib().mbpcg_k_spmm_gram(n, ptr(row_ptr), ptr(col_idx), ptr(vals), s, ptr(P), ptr(AP), ptr(G),
+                                   ptr(scratch), scratch_bytes, stream)
+
+
+def mbpcg_k_dense_gram(n, A, s, P, AP, G, scratch, scratch_bytes, stream=None):
+    return lib().mbpcg_k_dense_gram(n, ptr(A), s, ptr(P), ptr(AP), ptr(G), ptr(scratch), scratch_bytes, stream)
+
+
+def mbpcg_k_spmm(n, row_ptr, col_idx, vals, s, P, AP, stream=None):
+    return lib().mbpcg_k_spmm(n, ptr(row_ptr), ptr(col_idx), ptr(vals), s, ptr(P), ptr(AP), stream)
+
+
+def mbpcg_k_dense_product(n, A, s, P, AP, stream=None):
+    return lib().mbpcg_k_dense_product(n, ptr(A), s, ptr(P), ptr(AP), stream)
+
+
+def mbpcg_k_cholesky(s, G, Z, status_dev, stream=None):
+    return lib().mbpcg_k_cholesky(s, ptr(G), ptr(Z), ptr(status_dev), stream)

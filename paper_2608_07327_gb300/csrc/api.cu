@@ -1,0 +1,782 @@
+// Host runtime of the MBPCG library: handles, workspace layout, the CUDA-graph solve loop and the
+// C ABI declared in include/mbpcg.h and include/mbpcg_kernels.h.
+//
+// A solve is one graph launch per inner solve: set-up kernels, a device-side WHILE conditional
+// node whose body is one iteration of Algorithm 1 (the k x k kernel at the end of the body sets
+// the loop condition), and the exit kernels (least-squares combination, x update, true residual).
+// The host only reads the 200-byte solve state after each launch to decide on a true-residual
+// restart.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/mbpcg.h"
+#include "../../include/mbpcg_kernels.h"
+#include "kernels.h"
+#include "small_kernels.cuh"
+
+using namespace mbpcg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int set_err(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return set_err(MBPCG_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Dims {
+  int n, kp, nb, nb_dense, nbmax, pstride;
+  long long nnz;
+  int dense, algo;
+};
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+Dims make_dims(int n, long long nnz, int s, int algo, int dense, int sms) {
+  Dims d;
+  d.n = n;
+  d.nnz = nnz;
+  d.dense = dense;
+  d.algo = algo;
+  d.kp = (algo == MBPCG_ALGO_CG) ? 1 : padded_width(s);
+  const int sm = sms > 0 ? sms : 1;
+  long long want = ((long long)n + 31) / 32;
+  d.nb = (int)(want < 2LL * sm ? (want > 0 ? want : 1) : 2LL * sm);
+  long long wd = ((long long)n + 7) / 8;
+  d.nb_dense = (int)(wd < sm ? (wd > 0 ? wd : 1) : sm);
+  d.nbmax = d.nb > d.nb_dense ? d.nb : d.nb_dense;
+  d.pstride = (npack(d.kp) + d.kp + 1 + 3) / 4 * 4;
+  return d;
+}
+
+// Byte offsets of every buffer inside one workspace.
+struct Layout {
+  size_t rp, ci, av, A, diag, d, sqd, b, rhs, bs, x;
+  size_t U, X0, Xt, R, W, P, Q, V;    // MBPCG blocks, n x KP each
+  size_t r, w, xb, p, sv;             // CG vectors
+  size_t part, red, small, st, flag;  // reductions, k x k matrices, control block
+  size_t total;
+};
+
+Layout make_layout(const Dims& dm) {
+  Layout L;
+  std::memset(&L, 0, sizeof(L));
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + (bytes > 0 ? bytes : 1));
+    return at;
+  };
+  const size_t n = (size_t)dm.n;
+  if (dm.dense) {
+    L.A = take(n * n * sizeof(double));
+  } else {
+    L.rp = take((n + 1) * sizeof(int));
+    L.ci = take((size_t)dm.nnz * sizeof(int));
+    L.av = take((size_t)dm.nnz * sizeof(double));
+  }
+  L.diag = take(n * sizeof(double));
+  L.d = take(n * sizeof(double));
+  L.sqd = take(n * sizeof(double));
+  L.b = take(n * sizeof(double));
+  L.rhs = take(n * sizeof(double));
+  L.bs = take(n * sizeof(double));
+  L.x = take(n * sizeof(double));
+  if (dm.algo == MBPCG_ALGO_MBPCG) {
+    const size_t blk = n * dm.kp * sizeof(double);
+    L.U = take(blk);
+    L.X0 = take(blk);
+    L.Xt = take(blk);
+    L.R = take(blk);
+    L.W = take(blk);
+    L.P = take(blk);
+    L.Q = take(blk);
+    L.V = take(blk);
+  } else {
+    L.r = take(n * sizeof(double));
+    L.w = take(n * sizeof(double));
+    L.xb = take(n * sizeof(double));
+    L.p = take(n * sizeof(double));
+    L.sv = take(n * sizeof(double));
+  }
+  L.part = take((size_t)dm.nbmax * dm.pstride * sizeof(double));
+  L.red = take((size_t)dm.pstride * sizeof(double));
+  L.small = take(8 * (size_t)kMaxKP * kMaxKP * sizeof(double));
+  L.st = take(sizeof(SolveState));
+  L.flag = take(sizeof(int));
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+struct mbpcg_ctx {
+  Dims dm;
+  int s, precond, algo, precision;
+  unsigned long long seed;
+  cudaStream_t stream;
+  int own_stream;
+  char* ws;
+  int own_ws;
+  Layout L;
+  // device pointers
+  int *rp, *ci, *flag;
+  double *av, *A, *diag, *d, *sqd, *wdiag, *b, *rhs, *bs, *x;
+  double *U, *X0, *Xt, *R, *W, *P, *Q, *V;
+  double *r, *w, *xb, *p, *sv;
+  double *part, *red;
+  double *Sigma, *SigmaInv, *Xi, *T, *Zeta, *ZetaInv, *c, *Gtmp;
+  SolveState* st;
+  SolveState* st_host;  // pinned
+  cudaGraphExec_t exec;
+  cudaGraphConditionalHandle cond;
+  int graph_ready;
+  cudaEvent_t e0, e1;
+};
+
+namespace {
+
+template <typename T>
+T* at(mbpcg_ctx* h, size_t off) {
+  return reinterpret_cast<T*>(h->ws + off);
+}
+
+void bind(mbpcg_ctx* h) {
+  const Layout& L = h->L;
+  if (h->dm.dense) {
+    h->A = at<double>(h, L.A);
+    h->rp = nullptr;
+    h->ci = nullptr;
+    h->av = nullptr;
+  } else {
+    h->rp = at<int>(h, L.rp);
+    h->ci = at<int>(h, L.ci);
+    h->av = at<double>(h, L.av);
+    h->A = nullptr;
+  }
+  h->diag = at<double>(h, L.diag);
+  h->d = at<double>(h, L.d);
+  h->sqd = at<double>(h, L.sqd);
+  h->b = at<double>(h, L.b);
+  h->rhs = at<double>(h, L.rhs);
+  h->bs = at<double>(h, L.bs);
+  h->x = at<double>(h, L.x);
+  if (h->algo == MBPCG_ALGO_MBPCG) {
+    h->U = at<double>(h, L.U);
+    h->X0 = at<double>(h, L.X0);
+    h->Xt = at<double>(h, L.Xt);
+    h->R = at<double>(h, L.R);
+    h->W = at<double>(h, L.W);
+    h->P = at<double>(h, L.P);
+    h->Q = at<double>(h, L.Q);
+    h->V = at<double>(h, L.V);
+  } else {
+    h->r = at<double>(h, L.r);
+    h->w = at<double>(h, L.w);
+    h->xb = at<double>(h, L.xb);
+    h->p = at<double>(h, L.p);
+    h->sv = at<double>(h, L.sv);
+  }
+  h->part = at<double>(h, L.part);
+  h->red = at<double>(h, L.red);
+  double* sm = at<double>(h, L.small);
+  const size_t q = (size_t)kMaxKP * kMaxKP;
+  h->Sigma = sm;
+  h->SigmaInv = sm + q;
+  h->Xi = sm + 2 * q;
+  h->T = sm + 3 * q;
+  h->Zeta = sm + 4 * q;
+  h->ZetaInv = sm + 5 * q;
+  h->c = sm + 6 * q;
+  h->Gtmp = sm + 7 * q;
+  h->st = at<SolveState>(h, L.st);
+  h->flag = at<int>(h, L.flag);
+}
+
+int check_common(int n, int s, int precond, int algo, int precision, int mem) {
+  if (n < 1) return set_err(MBPCG_ERR_INVALID, "n must be >= 1 (got %d)", n);
+  if (algo != MBPCG_ALGO_MBPCG && algo != MBPCG_ALGO_CG) return set_err(MBPCG_ERR_INVALID, "unknown algo %d", algo);
+  if (algo == MBPCG_ALGO_MBPCG && (s < 1 || s > 32)) return set_err(MBPCG_ERR_INVALID, "s must be in [1, 32] (got %d)", s);
+  if (precond != MBPCG_PRECOND_NONE && precond != MBPCG_PRECOND_JACOBI)
+    return set_err(MBPCG_ERR_INVALID, "unknown precond %d", precond);
+  if (precision != MBPCG_FP64) return set_err(MBPCG_ERR_INVALID, "unsupported precision %d", precision);
+  if (mem != 0 && mem != 1) return set_err(MBPCG_ERR_INVALID, "mem must be 0 (host) or 1 (device)");
+  return MBPCG_OK;
+}
+
+int alloc_handle(mbpcg_ctx** out, const Dims& dm, int s, int precond, int algo, int precision,
+                 unsigned long long seed, void* workspace, size_t workspace_bytes, void* stream) {
+  mbpcg_ctx* h = new (std::nothrow) mbpcg_ctx;
+  if (!h) return set_err(MBPCG_ERR_OOM, "host allocation failed");
+  std::memset(h, 0, sizeof(*h));
+  h->dm = dm;
+  h->s = (algo == MBPCG_ALGO_CG) ? 1 : s;
+  h->precond = precond;
+  h->algo = algo;
+  h->precision = precision;
+  h->seed = seed;
+  h->L = make_layout(dm);
+  *out = h;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = 1;
+  }
+  if (workspace) {
+    if (workspace_bytes < h->L.total)
+      return set_err(MBPCG_ERR_OOM, "workspace of %zu bytes is smaller than the %zu bytes needed", workspace_bytes,
+                     h->L.total);
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign != 0)
+      return set_err(MBPCG_ERR_INVALID, "workspace must be %zu-byte aligned", kAlign);
+    h->ws = static_cast<char*>(workspace);
+  } else {
+    if (cudaMalloc(&h->ws, h->L.total) != cudaSuccess) {
+      cudaGetLastError();
+      h->ws = nullptr;
+      return set_err(MBPCG_ERR_OOM, "cudaMalloc of %zu bytes failed", h->L.total);
+    }
+    h->own_ws = 1;
+  }
+  CUDA_TRY(cudaMallocHost(&h->st_host, sizeof(SolveState)));
+  CUDA_TRY(cudaEventCreate(&h->e0));
+  CUDA_TRY(cudaEventCreate(&h->e1));
+  bind(h);
+  CUDA_TRY(cudaMemsetAsync(h->ws, 0, h->L.total, h->stream));
+  return MBPCG_OK;
+}
+
+void release(mbpcg_ctx* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph_ready) cudaGraphExecDestroy(h->exec);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->e0) cudaEventDestroy(h->e0);
+  if (h->e1) cudaEventDestroy(h->e1);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int read_flag(mbpcg_ctx* h, int* flag) {
+  CUDA_TRY(cudaMemcpyAsync(h->st_host, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  std::memcpy(flag, h->st_host, sizeof(int));
+  return MBPCG_OK;
+}
+
+// Diagonal, scaling vectors and the in-place scaled matrix (Section 1).
+int finish_create(mbpcg_ctx* h) {
+  const int n = h->dm.n;
+  const int g = (n + 255) / 256;
+  CUDA_TRY(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+  if (h->dm.dense) k_diag_dense<<<g, 256, 0, h->stream>>>(n, h->A, h->diag, h->flag);
+  else k_diag_csr<<<g, 256, 0, h->stream>>>(n, h->rp, h->ci, h->av, h->diag, h->flag);
+  CUDA_TRY(cudaGetLastError());
+  int flag = 0;
+  int rc = read_flag(h, &flag);
+  if (rc) return rc;
+  if (flag & 2) return set_err(MBPCG_ERR_NOT_SPD, "a diagonal entry of A is missing, not positive or not finite");
+  if (h->precond == MBPCG_PRECOND_JACOBI) {
+    k_make_scaling<<<g, 256, 0, h->stream>>>(n, h->diag, h->d, h->sqd);
+    if (h->dm.dense) k_scale_dense<<<4 * 152, 256, 0, h->stream>>>(n, h->A, h->d);
+    else k_scale_csr<<<g, 256, 0, h->stream>>>(n, h->rp, h->ci, h->av, h->d);
+    CUDA_TRY(cudaGetLastError());
+    h->wdiag = h->diag;
+  } else {
+    h->d = nullptr;
+    h->sqd = nullptr;
+    h->wdiag = nullptr;
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return MBPCG_OK;
+}
+
+// ------------------------------------------------------------------------------- graph building
+
+void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y, int gram, const SolveState* st) {
+  const Dims& dm = h->dm;
+  if (dm.dense) {
+    ops->dense(h->stream, dm.nb_dense, dm.n, h->A, X, Y, st);
+    if (gram) ops->gram(h->stream, dm.nb, dm.n, X, Y, h->part, dm.pstride, st);
+  } else {
+    ops->spmm(h->stream, dm.nb, dm.n, h->rp, h->ci, h->av, X, Y, h->part, dm.pstride, st, gram);
+  }
+}
+
+void enqueue_reduce(mbpcg_ctx* h, int nent, const SolveState* st) {
+  k_reduce<<<nent, 128, 0, h->stream>>>(h->part, h->dm.nb, h->dm.pstride, h->red, st);
+}
+
+void enqueue_true_residual(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  if (dm.dense)
+    k_resid_dense<<<dm.nb_dense, kThreads, 0, h->stream>>>(dm.n, h->A, h->sqd, h->b, h->x, h->rhs, h->part, dm.pstride);
+  else
+    k_resid_csr<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->rp, h->ci, h->av, h->sqd, h->b, h->x, h->rhs, h->part,
+                                                   dm.pstride);
+  // the dense residual uses nb_dense partial slots
+  k_reduce<<<1, 128, 0, h->stream>>>(h->part, dm.dense ? dm.nb_dense : dm.nb, dm.pstride, h->red, nullptr);
+  k_small_true<<<1, 1, 0, h->stream>>>(h->st, h->red);
+}
+
+void enqueue_mbpcg_setup(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOps* ops = row_ops(dm.kp);
+  const int kp = dm.kp, n = dm.n;
+  enqueue_product(h, ops, h->U, h->Q, 0, nullptr);  // A U
+  ops->setup_norms(h->stream, dm.nb, n, h->rhs, h->d, h->bs, h->Q, h->part, dm.pstride);
+  enqueue_reduce(h, 3, nullptr);
+  k_small_setup<<<1, 1, 0, h->stream>>>(h->st, h->red);
+  ops->init(h->stream, dm.nb, n, h->s, h->U, h->Q, h->bs, h->X0, h->Xt, h->R, h->part, dm.pstride, h->st);
+  enqueue_reduce(h, npack(kp), nullptr);
+  k_small_sigma<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->Sigma, h->SigmaInv);
+  ops->pw(h->stream, dm.nb, n, h->R, h->W, h->P, h->SigmaInv, nullptr, nullptr, 1);
+}
+
+void enqueue_mbpcg_body(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOps* ops = row_ops(dm.kp);
+  const int kp = dm.kp, n = dm.n;
+  enqueue_product(h, ops, h->P, h->Q, 1, h->st);
+  enqueue_reduce(h, npack(kp), h->st);
+  k_small_xi<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->Sigma, h->Xi, h->T);
+  ops->axpy(h->stream, dm.nb, n, h->P, h->Q, h->W, h->R, h->Xt, h->V, h->T, h->Xi, h->wdiag, h->part, dm.pstride,
+            h->st);
+  enqueue_reduce(h, npack(kp) + kp, h->st);
+  k_small_zeta<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->Sigma, h->Zeta, h->ZetaInv, h->cond);
+  ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0);
+}
+
+void enqueue_mbpcg_exit(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOps* ops = row_ops(dm.kp);
+  const int kp = dm.kp, n = dm.n;
+  ops->ls_gram(h->stream, dm.nb, n, h->R, h->rhs, h->sqd, h->part, dm.pstride);
+  enqueue_reduce(h, npack(kp) + kp + 1, nullptr);
+  k_small_ls<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->c);
+  ops->combine(h->stream, dm.nb, n, h->s, h->Xt, h->X0, h->c, h->d, h->x);
+  enqueue_true_residual(h);
+}
+
+void enqueue_cg_setup(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  k_cg_init<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->rhs, h->d, h->r, h->xb, h->p, h->sv, h->part, dm.pstride);
+  enqueue_reduce(h, 1, nullptr);
+  k_small_cg_setup<<<1, 1, 0, h->stream>>>(h->st, h->red);
+}
+
+void enqueue_cg_body(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOps* ops = row_ops(1);
+  enqueue_product(h, ops, h->r, h->w, 0, h->st);  // w = A u, u = r
+  k_cg_dots<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->r, h->w, h->wdiag, h->part, dm.pstride, h->st);
+  enqueue_reduce(h, 3, h->st);
+  k_small_cg<<<1, 1, 0, h->stream>>>(h->st, h->red, h->cond);
+  k_cg_update<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->r, h->w, h->xb, h->p, h->sv, h->st);
+}
+
+void enqueue_cg_exit(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  k_cg_finish<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->xb, h->d, h->x);
+  enqueue_true_residual(h);
+}
+
+int build_graph(mbpcg_ctx* h) {
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h->cond, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return set_err(MBPCG_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
+  }
+  const bool cg = h->algo == MBPCG_ALGO_CG;
+  e = cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (cg) enqueue_cg_setup(h);
+    else enqueue_mbpcg_setup(h);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+    cudaGraphNode_t cnode = nullptr;
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+      np.conditional.handle = h->cond;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &np);
+      if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(h->stream, &cnode, nullptr, 1,
+                                                                  cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+      if (cg) enqueue_cg_exit(h);
+      else enqueue_mbpcg_exit(h);
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &captured);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        if (cg) enqueue_cg_body(h);
+        else enqueue_mbpcg_body(h);
+        cudaGraph_t b2 = nullptr;
+        e = cudaStreamEndCapture(h->stream, &b2);
+      }
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(MBPCG_ERR_CUDA, "building the solve graph failed: %s", cudaGetErrorString(e));
+  }
+  h->graph_ready = 1;
+  return MBPCG_OK;
+}
+
+// Copies b and U in (host or device memory), runs the inner solves with true-residual restarts,
+// and copies x out. mem: 0 host, 1 device for b, U and x.
+int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int maxit, double* x_out,
+               mbpcg_info* info, int mem, int no_test) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (!b || (!x_out && !no_test)) return set_err(MBPCG_ERR_INVALID, "b and x_out must not be NULL");
+  if (!(tol > 0.0) || tol != tol) return set_err(MBPCG_ERR_INVALID, "tol must be a positive number");
+  if (maxit < 1 && !no_test) return set_err(MBPCG_ERR_INVALID, "maxit must be >= 1");
+  const int n = h->dm.n;
+  const size_t nb = (size_t)n * sizeof(double);
+  const cudaMemcpyKind in_kind = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind out_kind = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (!h->graph_ready) {
+    int rc = build_graph(h);
+    if (rc) return rc;
+  }
+  CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->b, b, nb, in_kind, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->rhs, h->b, nb, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->x, 0, nb, h->stream));
+  if (h->algo == MBPCG_ALGO_MBPCG) {
+    const RowOps* ops = row_ops(h->dm.kp);
+    if (U) {
+      // stage the column-major block in the A P buffer, then widen to row-major KP
+      CUDA_TRY(cudaMemcpyAsync(h->Q, U, nb * h->s, in_kind, h->stream));
+      ops->from_colmajor(h->stream, n, h->s, h->Q, h->U);
+    } else {
+      ops->gen_u(h->stream, n, h->s, h->seed, h->U);
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
+  int total = 0, restarts = 0, status = MBPCG_OK;
+  double tol_rel = tol;
+  SolveState s;
+  for (;;) {
+    const int maxit_inner = no_test ? maxit : (maxit - total);
+    k_params<<<1, 1, 0, h->stream>>>(h->st, tol_rel, maxit_inner, no_test, restarts, h->s);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaGraphLaunch(h->exec, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->st_host, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    std::memcpy(&s, h->st_host, sizeof(s));
+    total += s.it;
+    if (no_test) {
+      status = s.status;
+      break;
+    }
+    const double relres = (s.b_norm > 0.0) ? s.true_res / s.b_norm : 0.0;
+    if (relres <= tol) {
+      status = MBPCG_OK;
+      break;
+    }
+    if (restarts >= 3 || total >= maxit || s.status == MBPCG_NOT_CONVERGED) {
+      status = (s.status == MBPCG_OK) ? MBPCG_NOT_CONVERGED : s.status;
+      break;
+    }
+    ++restarts;
+    tol_rel = 0.5 * tol * s.b_norm / s.true_res;
+  }
+  if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, h->x, nb, out_kind, h->stream));
+  CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    const double bn = s.b_norm, rn = s.rhs_norm;
+    info->iterations = total;
+    info->restarts = restarts;
+    info->status = status;
+    info->best_col = s.best_col;
+    info->ls_fallback = s.ls_fallback;
+    info->reserved = 0;
+    info->relres_recurrence = (bn > 0.0) ? s.nu_h / bn : 0.0;
+    info->relres_ls = (bn > 0.0) ? s.ls_res / bn : 0.0;
+    info->relres_true = (bn > 0.0) ? s.true_res / bn : 0.0;
+    info->seconds = ms * 1e-3;
+    (void)rn;
+  }
+  g_err.clear();
+  return status;
+}
+
+}  // namespace
+
+// ===================================================================================== C ABI
+
+extern "C" {
+
+size_t mbpcg_workspace_size_csr(int32_t n, int64_t nnz, int32_t s, int32_t algo, int32_t precision) {
+  (void)precision;
+  if (n < 1 || nnz < 0) return 0;
+  return make_layout(make_dims(n, nnz, s, algo, 0, num_sms())).total;
+}
+
+size_t mbpcg_workspace_size_dense(int32_t n, int32_t s, int32_t algo, int32_t precision) {
+  (void)precision;
+  if (n < 1) return 0;
+  return make_layout(make_dims(n, (long long)n * n, s, algo, 1, num_sms())).total;
+}
+
+int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                     const double* vals, int32_t s, int32_t precond, int32_t algo, int32_t precision, uint64_t seed,
+                     int32_t mem, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out) return set_err(MBPCG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int rc = check_common(n, s, precond, algo, precision, mem);
+  if (rc) return rc;
+  if (nnz < 0 || nnz >= (1LL << 31)) return set_err(MBPCG_ERR_INVALID, "nnz must be in [0, 2^31)");
+  if (!row_ptr || (nnz > 0 && (!col_idx || !vals))) return set_err(MBPCG_ERR_INVALID, "CSR arrays must not be NULL");
+  const int sms = num_sms();
+  if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
+  mbpcg_ctx* h = nullptr;
+  rc = alloc_handle(&h, make_dims(n, nnz, s, algo, 0, sms), s, precond, algo, precision, seed, workspace,
+                    workspace_bytes, stream);
+  if (rc) {
+    release(h);
+    return rc;
+  }
+  const cudaMemcpyKind kind = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemcpyAsync(h->rp, row_ptr, (size_t)(n + 1) * sizeof(int), kind, h->stream);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(h->ci, col_idx, (size_t)nnz * sizeof(int), kind, h->stream);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(h->av, vals, (size_t)nnz * sizeof(double), kind, h->stream);
+  if (e != cudaSuccess) {
+    release(h);
+    return set_err(MBPCG_ERR_CUDA, "copying A: %s", cudaGetErrorString(e));
+  }
+  k_validate_csr<<<(n + 255) / 256, 256, 0, h->stream>>>(n, nnz, h->rp, h->ci, h->flag);
+  int flag = 0;
+  rc = read_flag(h, &flag);
+  if (!rc && (flag & 1)) rc = set_err(MBPCG_ERR_INVALID, "malformed CSR (row_ptr or col_idx out of range)");
+  if (!rc) rc = finish_create(h);
+  if (rc) {
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return MBPCG_OK;
+}
+
+int mbpcg_create_dense(mbpcg_handle* out, int32_t n, const double* A_colmajor, int32_t s, int32_t precond,
+                       int32_t algo, int32_t precision, uint64_t seed, int32_t mem, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  if (!out) return set_err(MBPCG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int rc = check_common(n, s, precond, algo, precision, mem);
+  if (rc) return rc;
+  if (!A_colmajor) return set_err(MBPCG_ERR_INVALID, "A must not be NULL");
+  if ((long long)n * n >= (1LL << 40)) return set_err(MBPCG_ERR_INVALID, "n too large for a dense matrix");
+  const int sms = num_sms();
+  if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
+  mbpcg_ctx* h = nullptr;
+  rc = alloc_handle(&h, make_dims(n, (long long)n * n, s, algo, 1, sms), s, precond, algo, precision, seed,
+                    workspace, workspace_bytes, stream);
+  if (rc) {
+    release(h);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(h->A, A_colmajor, (size_t)n * n * sizeof(double),
+                                  mem ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) {
+    release(h);
+    return set_err(MBPCG_ERR_CUDA, "copying A: %s", cudaGetErrorString(e));
+  }
+  rc = finish_create(h);
+  if (rc) {
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return MBPCG_OK;
+}
+
+int mbpcg_solve(mbpcg_handle h, const double* b, const double* U, double tol, int32_t maxit, double* x_out,
+                mbpcg_info* info) {
+  return solve_impl(h, b, U, tol, maxit, x_out, info, 0, 0);
+}
+
+int mbpcg_solve_dev(mbpcg_handle h, const double* b, const double* U, double tol, int32_t maxit, double* x_out,
+                    mbpcg_info* info) {
+  return solve_impl(h, b, U, tol, maxit, x_out, info, 1, 0);
+}
+
+int mbpcg_run_iterations_dev(mbpcg_handle h, const double* b, const double* U, int32_t iters, double* X0,
+                             double* Xt, double* R, double* W, double* P, double* Sigma) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (h->algo != MBPCG_ALGO_MBPCG) return set_err(MBPCG_ERR_INVALID, "diagnostic needs an MBPCG handle");
+  if (iters < 0) return set_err(MBPCG_ERR_INVALID, "iters must be >= 0");
+  int rc = solve_impl(h, b, U, 1.0, iters, nullptr, nullptr, 1, 1);
+  if (rc != MBPCG_OK && rc != MBPCG_BREAKDOWN) return rc;
+  const RowOps* ops = row_ops(h->dm.kp);
+  const int n = h->dm.n;
+  double* src[5] = {h->X0, h->Xt, h->R, h->W, h->P};
+  double* dst[5] = {X0, Xt, R, W, P};
+  for (int q = 0; q < 5; ++q)
+    if (dst[q]) ops->to_colmajor(h->stream, n, h->s, src[q], dst[q]);
+  if (Sigma)
+    CUDA_TRY(cudaMemcpy2DAsync(Sigma, h->s * sizeof(double), h->Sigma, h->dm.kp * sizeof(double),
+                               h->s * sizeof(double), h->s, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+void mbpcg_destroy(mbpcg_handle h) { release(h); }
+
+const char* mbpcg_status_string(int status) {
+  switch (status) {
+    case MBPCG_OK: return "ok";
+    case MBPCG_ERR_INVALID: return "invalid argument";
+    case MBPCG_ERR_OOM: return "out of memory";
+    case MBPCG_ERR_CUDA: return "CUDA error";
+    case MBPCG_ERR_NOT_SPD: return "matrix is not SPD (diagonal)";
+    case MBPCG_NOT_CONVERGED: return "not converged";
+    case MBPCG_BREAKDOWN: return "breakdown";
+    case MBPCG_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* mbpcg_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ component entry points
+
+int32_t mbpcg_k_padded_width(int32_t s) { return (s >= 1 && s <= 32) ? padded_width(s) : 0; }
+
+size_t mbpcg_k_scratch_bytes(int32_t n, int32_t s) {
+  if (n < 1 || s < 1 || s > 32) return 0;
+  const Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
+  return (size_t)(dm.nbmax + 1) * dm.pstride * sizeof(double);
+}
+
+static int k_product_gram(int dense, int32_t n, const int32_t* rp, const int32_t* ci, const double* av,
+                          const double* A, int32_t s, const double* P, double* AP, double* G, void* scratch,
+                          size_t scratch_bytes, void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !P || !AP || !G) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if (scratch_bytes < mbpcg_k_scratch_bytes(n, s) || !scratch) return set_err(MBPCG_ERR_INVALID, "scratch too small");
+  const Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, dense, num_sms());
+  const RowOps* ops = row_ops(dm.kp);
+  cudaStream_t st = (cudaStream_t)stream;
+  double* part = static_cast<double*>(scratch);
+  double* red = part + (size_t)dm.nbmax * dm.pstride;
+  if (dense) {
+    ops->dense(st, dm.nb_dense, n, A, P, AP, nullptr);
+    ops->gram(st, dm.nb, n, P, AP, part, dm.pstride, nullptr);
+  } else {
+    ops->spmm(st, dm.nb, n, rp, ci, av, P, AP, part, dm.pstride, nullptr, 1);
+  }
+  k_reduce<<<npack(dm.kp), 128, 0, st>>>(part, dm.nb, dm.pstride, red, nullptr);
+  k_unpack_full<<<1, 256, 0, st>>>(red, dm.kp, s, G);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+int mbpcg_k_spmm_gram(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* vals, int32_t s,
+                      const double* P, double* AP, double* G, void* scratch, size_t scratch_bytes, void* stream) {
+  if (!row_ptr) return set_err(MBPCG_ERR_INVALID, "row_ptr is NULL");
+  return k_product_gram(0, n, row_ptr, col_idx, vals, nullptr, s, P, AP, G, scratch, scratch_bytes, stream);
+}
+
+int mbpcg_k_dense_gram(int32_t n, const double* A, int32_t s, const double* P, double* AP, double* G, void* scratch,
+                       size_t scratch_bytes, void* stream) {
+  if (!A) return set_err(MBPCG_ERR_INVALID, "A is NULL");
+  return k_product_gram(1, n, nullptr, nullptr, nullptr, A, s, P, AP, G, scratch, scratch_bytes, stream);
+}
+
+int mbpcg_k_spmm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* vals, int32_t s,
+                 const double* P, double* AP, void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !row_ptr || !P || !AP) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  const Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
+  row_ops(dm.kp)->spmm((cudaStream_t)stream, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+int mbpcg_k_dense_product(int32_t n, const double* A, int32_t s, const double* P, double* AP, void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !A || !P || !AP) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  const Dims dm = make_dims(n, (long long)n * n, s, MBPCG_ALGO_MBPCG, 1, num_sms());
+  row_ops(dm.kp)->dense((cudaStream_t)stream, dm.nb_dense, n, A, P, AP, nullptr);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+int mbpcg_k_cholesky(int32_t s, const double* G, double* Z, int32_t* status_dev, void* stream) {
+  if (s < 1 || s > 32 || !G || !Z || !status_dev) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  k_chol_only<<<1, kSmallThreads, 0, (cudaStream_t)stream>>>(G, s, Z, status_dev);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+}  // extern "C"
+
+namespace mbpcg {
+
+// G (s x s column-major, ld s) = the full symmetric matrix of a packed upper triangle.
+__global__ void k_unpack_full(const double* __restrict__ packed, int kp, int s, double* __restrict__ G) {
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) {
+    const int l = q % s, m = q / s;
+    G[q] = (l <= m) ? packed[pidx(l, m)] : packed[pidx(m, l)];
+  }
+}
+
+// Z = upper Cholesky factor of G (s x s, ld s); *status = 0 or 6 (breakdown).
+__global__ void k_chol_only(const double* __restrict__ G, int s, double* __restrict__ Z, int* __restrict__ status) {
+  __shared__ double A[kMaxKP * kMaxKP];
+  __shared__ int flag;
+  for (int q = threadIdx.x; q < kMaxKP * kMaxKP; q += blockDim.x) {
+    const int l = q % kMaxKP, m = q / kMaxKP;
+    A[q] = (l < s && m < s) ? G[l + m * s] : 0.0;
+  }
+  __syncthreads();
+  const int fail = cta_cholesky(s, kMaxKP, A, &flag);
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) {
+    const int l = q % s, m = q / s;
+    Z[q] = fail ? 0.0 : A[l + m * kMaxKP];
+  }
+  if (threadIdx.x == 0) *status = fail ? 6 : 0;
+}
+
+}  // namespace mbpcg

@@ -1,0 +1,93 @@
+// Internal interface between the host runtime (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mbpcg_device.cuh"
+
+namespace mbpcg {
+
+// Host launchers of the row kernels for one padded width KP (defined in inst_kp*.cu).
+struct RowOps {
+  int kp;
+  void (*spmm)(cudaStream_t, int nb, int n, const int* rp, const int* ci, const double* av, const double* P,
+               double* Q, double* part, int pstride, const SolveState* st, int gram);
+  void (*dense)(cudaStream_t, int nb, int n, const double* A, const double* P, double* Q, const SolveState* st);
+  void (*gram)(cudaStream_t, int nb, int n, const double* X, const double* Y, double* part, int pstride,
+               const SolveState* st);
+  void (*axpy)(cudaStream_t, int nb, int n, const double* P, const double* Q, const double* W, double* R,
+               double* Xt, double* V, const double* T, const double* Xi, const double* wdiag, double* part,
+               int pstride, const SolveState* st);
+  void (*pw)(cudaStream_t, int nb, int n, const double* V, double* W, double* P, const double* Zinv,
+             const double* Z, const SolveState* st, int setp);
+  void (*setup_norms)(cudaStream_t, int nb, int n, const double* rhs, const double* d, double* bs,
+                      const double* AU, double* part, int pstride);
+  void (*init)(cudaStream_t, int nb, int n, int s, const double* U, const double* AU, const double* bs, double* X0,
+               double* Xt, double* R, double* part, int pstride, const SolveState* st);
+  void (*ls_gram)(cudaStream_t, int nb, int n, const double* R, const double* rhs, const double* sqd, double* part,
+                  int pstride);
+  void (*combine)(cudaStream_t, int nb, int n, int s, const double* Xt, const double* X0, const double* c,
+                  const double* d, double* x);
+  void (*gen_u)(cudaStream_t, int n, int s, unsigned long long seed, double* U);
+  void (*from_colmajor)(cudaStream_t, int n, int s, const double* src, double* dst);
+  void (*to_colmajor)(cudaStream_t, int n, int s, const double* src, double* dst);
+};
+
+const RowOps* row_ops_kp1();
+const RowOps* row_ops_kp2();
+const RowOps* row_ops_kp4();
+const RowOps* row_ops_kp8();
+const RowOps* row_ops_kp16();
+const RowOps* row_ops_kp32();
+
+inline int padded_width(int s) {
+  int kp = 1;
+  while (kp < s) kp <<= 1;
+  return kp;
+}
+inline const RowOps* row_ops(int kp) {
+  switch (kp) {
+    case 1: return row_ops_kp1();
+    case 2: return row_ops_kp2();
+    case 4: return row_ops_kp4();
+    case 8: return row_ops_kp8();
+    case 16: return row_ops_kp16();
+    case 32: return row_ops_kp32();
+    default: return nullptr;
+  }
+}
+
+// single-CTA and vector kernels (small_kernels.cu)
+__global__ void k_reduce(const double* part, int nparts, int pstride, double* out, const SolveState* st);
+__global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s);
+__global__ void k_small_setup(SolveState* st, const double* red);
+__global__ void k_small_sigma(SolveState* st, const double* Gp, int kp, double* Sigma, double* SigmaInv);
+__global__ void k_small_xi(SolveState* st, const double* G1p, int kp, const double* Sigma, double* Xi, double* T);
+__global__ void k_small_zeta(SolveState* st, const double* G2nu, int kp, double* Sigma, double* Zeta,
+                             double* ZetaInv, cudaGraphConditionalHandle cond);
+__global__ void k_small_ls(SolveState* st, const double* Mg, int kp, double* c_out);
+__global__ void k_small_true(SolveState* st, const double* rr);
+__global__ void k_small_cg_setup(SolveState* st, const double* red);
+__global__ void k_small_cg(SolveState* st, const double* red, cudaGraphConditionalHandle cond);
+__global__ void k_validate_csr(int n, long long nnz, const int* rp, const int* ci, int* flag);
+__global__ void k_diag_csr(int n, const int* rp, const int* ci, const double* av, double* diag, int* flag);
+__global__ void k_diag_dense(int n, const double* A, double* diag, int* flag);
+__global__ void k_make_scaling(int n, const double* diag, double* d, double* sqd);
+__global__ void k_scale_csr(int n, const int* rp, const int* ci, double* av, const double* d);
+__global__ void k_scale_dense(int n, double* A, const double* d);
+__global__ void k_resid_csr(int n, const int* rp, const int* ci, const double* av, const double* sqd,
+                            const double* b, const double* x, double* r, double* part, int pstride);
+__global__ void k_resid_dense(int n, const double* A, const double* sqd, const double* b, const double* x,
+                              double* r, double* part, int pstride);
+__global__ void k_cg_init(int n, const double* rhs, const double* d, double* r, double* x, double* p, double* sv,
+                          double* part, int pstride);
+__global__ void k_cg_dots(int n, const double* r, const double* w, const double* wdiag, double* part, int pstride,
+                          const SolveState* st);
+__global__ void k_cg_update(int n, double* r, const double* w, double* x, double* p, double* sv,
+                            const SolveState* st);
+__global__ void k_cg_finish(int n, const double* xbar, const double* d, double* x);
+
+// kernel-level helpers for the component entry points (api.cu)
+__global__ void k_unpack_full(const double* packed, int kp, int s, double* G);
+__global__ void k_chol_only(const double* G, int s, double* Z, int* status);
+
+}  // namespace mbpcg

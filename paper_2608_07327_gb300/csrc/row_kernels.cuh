@@ -1,0 +1,561 @@
+// Row-parallel kernels of Algorithm 1 (one template per padded block width KP).
+//
+// Each CTA owns a balanced contiguous range of rows and walks it in tiles; per-CTA partial sums
+// of the k x k reductions go to part[blockIdx.x * pstride + ...] and are summed in a fixed order
+// by k_reduce (small_kernels.cu). Every kernel that runs inside the iteration loop returns at
+// once when the solve has finished (SolveState::done), so a CUDA-graph loop body costs nothing
+// after convergence.
+#pragma once
+#include "mbpcg_device.cuh"
+
+namespace mbpcg {
+
+// ------------------------------------------------------------------------------------------------
+// Q = A P for CSR A (Algorithm 1, the A P^{i-1} product; the paper's dominant step, Table 2) and,
+// when GRAM, the CTA partials of the upper triangle of P^T Q (the Gram that defines Xi), so that
+// A P is never read back. Threads own CPT consecutive columns of a row; the row of P that a
+// nonzero selects is KP*8 contiguous bytes, read with 16-byte vector loads.
+template <int KP, bool GRAM>
+__global__ void __launch_bounds__(kThreads)
+k_spmm(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ av,
+       const double* __restrict__ P, double* __restrict__ Q, double* __restrict__ part, int pstride,
+       const SolveState* __restrict__ st) {
+  using C = Cfg<KP>;
+  using G = GramTile<KP>;
+  if (st != nullptr && st->done) return;
+  __shared__ __align__(16) double Xs[GRAM ? C::ROWS * KP : 2];
+  __shared__ __align__(16) double Ys[GRAM ? C::ROWS * KP : 2];
+  __shared__ __align__(16) double red[GRAM ? G::RED : 2];
+  int r0, r1;
+  row_range(n, r0, r1);
+  const int tid = threadIdx.x;
+  const int rl = tid / C::TPR, j0 = (tid % C::TPR) * C::CPT;
+  G g;
+  if constexpr (GRAM) g.init(tid);
+  for (int base = r0; base < r1; base += C::ROWS) {
+    const int i = base + rl;
+    double acc[C::CPT], pv[C::CPT];
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) acc[c] = pv[c] = 0.0;
+    if (i < r1) {
+      const int pe = __ldg(rp + i + 1);
+#pragma unroll 4
+      for (int p = __ldg(rp + i); p < pe; ++p) {
+        const int col = __ldg(ci + p);
+        const double a = __ldg(av + p);
+        double x[C::CPT];
+        ldv<C::CPT>(P + (size_t)col * KP + j0, x);
+#pragma unroll
+        for (int c = 0; c < C::CPT; ++c) acc[c] = fma(a, x[c], acc[c]);
+      }
+      stv<C::CPT>(Q + (size_t)i * KP + j0, acc);
+      if constexpr (GRAM) ldv<C::CPT>(P + (size_t)i * KP + j0, pv);
+    }
+    if constexpr (GRAM) {
+#pragma unroll
+      for (int c = 0; c < C::CPT; ++c) {
+        Xs[rl * KP + j0 + c] = pv[c];
+        Ys[rl * KP + j0 + c] = acc[c];
+      }
+      __syncthreads();
+      g.accumulate(Xs, Ys, min(C::ROWS, r1 - base));
+      __syncthreads();
+    }
+  }
+  if constexpr (GRAM) g.finish(red, part + (size_t)blockIdx.x * pstride);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Q = A P for dense symmetric A stored column-major (row i of A is column i, contiguous). One CTA
+// per SM walks its rows in groups; warp w takes rows w, w+8, w+16, ... of a group (RW of them in
+// registers), its lanes split the reduction index l (LL lanes) and the KP columns. P is staged
+// through shared memory in chunks of LC rows, A streams from HBM/L2 with coalesced loads.
+template <int KP>
+struct DenseCfg {
+  static constexpr int LL = 32 / KP;
+  static constexpr int RW = 4;
+  static constexpr int WARPS = kThreads / 32;
+  static constexpr int GROUP = WARPS * RW;
+  static constexpr int LC = (4096 / KP) < 512 ? (4096 / KP) : 512;
+};
+
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_dense(int n, const double* __restrict__ A, const double* __restrict__ P, double* __restrict__ Q,
+        const SolveState* __restrict__ st) {
+  using D = DenseCfg<KP>;
+  if (st != nullptr && st->done) return;
+  __shared__ __align__(16) double Ps[D::LC * KP];
+  int r0, r1;
+  row_range(n, r0, r1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ll = lane / KP, j = lane % KP;
+  for (int base = r0; base < r1; base += D::GROUP) {
+    int nv = 0;  // rows of this warp in this group (warp-uniform)
+    const double* arow[D::RW];
+    int rows[D::RW];
+#pragma unroll
+    for (int w = 0; w < D::RW; ++w) {
+      const int i = base + warp + w * D::WARPS;
+      rows[w] = i;
+      if (i < r1) ++nv;
+      arow[w] = A + (size_t)(i < r1 ? i : r0) * n;
+    }
+    double acc[D::RW];
+#pragma unroll
+    for (int w = 0; w < D::RW; ++w) acc[w] = 0.0;
+    for (int l0 = 0; l0 < n; l0 += D::LC) {
+      const int lc = min(D::LC, n - l0);
+      __syncthreads();
+      for (int q = threadIdx.x; q < lc * KP; q += kThreads) Ps[q] = __ldg(P + (size_t)l0 * KP + q);
+      __syncthreads();
+      if (nv == D::RW) {
+        for (int l = ll; l < lc; l += D::LL) {
+          const double pj = Ps[l * KP + j];
+#pragma unroll
+          for (int w = 0; w < D::RW; ++w) acc[w] = fma(__ldg(arow[w] + l0 + l), pj, acc[w]);
+        }
+      } else {
+        for (int l = ll; l < lc; l += D::LL) {
+          const double pj = Ps[l * KP + j];
+#pragma unroll
+          for (int w = 0; w < D::RW; ++w)
+            if (w < nv) acc[w] = fma(__ldg(arow[w] + l0 + l), pj, acc[w]);
+        }
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < D::RW; ++w) {
+      double v = acc[w];
+      for (int off = KP; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (ll == 0 && w < nv) Q[(size_t)rows[w] * KP + j] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// CTA partials of the upper triangle of X^T Y (used for the dense-A Gram P^T (A P), for
+// R^T R of the set-up Cholesky QR, and for the exit Gram).
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_gram(int n, const double* __restrict__ X, const double* __restrict__ Y, double* __restrict__ part,
+       int pstride, const SolveState* __restrict__ st) {
+  using C = Cfg<KP>;
+  using G = GramTile<KP>;
+  if (st != nullptr && st->done) return;
+  __shared__ __align__(16) double Xs[C::ROWS * KP];
+  __shared__ __align__(16) double Ys[C::ROWS * KP];
+  __shared__ __align__(16) double red[G::RED];
+  int r0, r1;
+  row_range(n, r0, r1);
+  const int tid = threadIdx.x, rl = tid / C::TPR, j0 = (tid % C::TPR) * C::CPT;
+  G g;
+  g.init(tid);
+  for (int base = r0; base < r1; base += C::ROWS) {
+    const int i = base + rl;
+    double xv[C::CPT], yv[C::CPT];
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) xv[c] = yv[c] = 0.0;
+    if (i < r1) {
+      ldv<C::CPT>(X + (size_t)i * KP + j0, xv);
+      ldv<C::CPT>(Y + (size_t)i * KP + j0, yv);
+    }
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) {
+      Xs[rl * KP + j0 + c] = xv[c];
+      Ys[rl * KP + j0 + c] = yv[c];
+    }
+    __syncthreads();
+    g.accumulate(Xs, Ys, min(C::ROWS, r1 - base));
+    __syncthreads();
+  }
+  g.finish(red, part + (size_t)blockIdx.x * pstride);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Block update of Algorithm 1, one pass over the rows:
+//   X~ += P T,  R -= (A P) T  with T = Xi Sigma;   V = W - (A P) Xi   (input of the Cholesky QR)
+// plus CTA partials of nu_j = ||(D R)_j||^2 (the original-system residual norms used for the
+// best-basis test, Section 1) at part[NPACK + j] and of the upper triangle of V^T V at part[0..).
+// wdiag = diag(A) of the original matrix (D^2), or NULL without scaling.
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_axpy(int n, const double* __restrict__ P, const double* __restrict__ Q, const double* __restrict__ W,
+       double* __restrict__ R, double* __restrict__ Xt, double* __restrict__ V,
+       const double* __restrict__ Tg, const double* __restrict__ Xig, const double* __restrict__ wdiag,
+       double* __restrict__ part, int pstride, const SolveState* __restrict__ st) {
+  using C = Cfg<KP>;
+  using G = GramTile<KP>;
+  constexpr int RED = (G::RED > C::ROWS * KP) ? G::RED : C::ROWS * KP;
+  if (st->done) return;
+  __shared__ __align__(16) double Ts[KP * KP];
+  __shared__ __align__(16) double Xis[KP * KP];
+  __shared__ __align__(16) double Ps[C::ROWS * KP];
+  __shared__ __align__(16) double Qs[C::ROWS * KP];
+  __shared__ __align__(16) double Vs[C::ROWS * KP];
+  __shared__ __align__(16) double red[RED];
+  const int tid = threadIdx.x, rl = tid / C::TPR, j0 = (tid % C::TPR) * C::CPT;
+  for (int q = tid; q < KP * KP; q += kThreads) {  // column-major in global -> row-major here
+    const int l = q % KP, jj = q / KP;
+    Ts[l * KP + jj] = Tg[q];
+    Xis[l * KP + jj] = Xig[q];
+  }
+  int r0, r1;
+  row_range(n, r0, r1);
+  G g;
+  g.init(tid);
+  double nu[C::CPT];
+#pragma unroll
+  for (int c = 0; c < C::CPT; ++c) nu[c] = 0.0;
+  for (int base = r0; base < r1; base += C::ROWS) {
+    const int i = base + rl;
+    const bool valid = i < r1;
+    double pv[C::CPT], qv[C::CPT];
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) pv[c] = qv[c] = 0.0;
+    if (valid) {
+      ldv<C::CPT>(P + (size_t)i * KP + j0, pv);
+      ldv<C::CPT>(Q + (size_t)i * KP + j0, qv);
+    }
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) {
+      Ps[rl * KP + j0 + c] = pv[c];
+      Qs[rl * KP + j0 + c] = qv[c];
+    }
+    __syncthreads();
+    double vv[C::CPT];
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) vv[c] = 0.0;
+    if (valid) {
+      double xv[C::CPT], rv[C::CPT];
+      ldv_plain<C::CPT>(Xt + (size_t)i * KP + j0, xv);
+      ldv_plain<C::CPT>(R + (size_t)i * KP + j0, rv);
+      ldv<C::CPT>(W + (size_t)i * KP + j0, vv);
+#pragma unroll 8
+      for (int l = 0; l < KP; ++l) {
+        const double pl = Ps[rl * KP + l], ql = Qs[rl * KP + l];
+#pragma unroll
+        for (int c = 0; c < C::CPT; ++c) {
+          const double t = Ts[l * KP + j0 + c];
+          xv[c] = fma(pl, t, xv[c]);
+          rv[c] = fma(-ql, t, rv[c]);
+          vv[c] = fma(-ql, Xis[l * KP + j0 + c], vv[c]);
+        }
+      }
+      stv<C::CPT>(Xt + (size_t)i * KP + j0, xv);
+      stv<C::CPT>(R + (size_t)i * KP + j0, rv);
+      stv<C::CPT>(V + (size_t)i * KP + j0, vv);
+      if (wdiag != nullptr) {
+        const double wi = __ldg(wdiag + i);
+#pragma unroll
+        for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c] * wi, rv[c], nu[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c], rv[c], nu[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) Vs[rl * KP + j0 + c] = vv[c];
+    __syncthreads();
+    g.accumulate(Vs, Vs, min(C::ROWS, r1 - base));
+    __syncthreads();
+  }
+  double* out = part + (size_t)blockIdx.x * pstride;
+  g.finish(red, out);
+#pragma unroll
+  for (int c = 0; c < C::CPT; ++c) red[rl * KP + j0 + c] = nu[c];
+  cta_tree_sum(red, C::ROWS, KP);
+  for (int jj = tid; jj < KP; jj += kThreads) out[C::NPACK + jj] = red[jj];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Second half of the Cholesky QR and the search-block update of Algorithm 1:
+//   W = V zeta^{-1}   (zeta upper triangular, its inverse precomputed by the k x k kernel)
+//   P = W + P zeta^T  (SETP == false)   or   P = W  (SETP == true: the set-up P^0 = W^0)
+// For KP >= 8 a thread owns columns j and KP-1-j of a row: the two triangular dot products then
+// total KP+1 terms for every thread, so a warp never idles on a short triangle.
+template <int KP, bool SETP>
+__global__ void __launch_bounds__(kThreads)
+k_pw(int n, const double* __restrict__ V, double* __restrict__ W, double* __restrict__ P,
+     const double* __restrict__ Zinvg, const double* __restrict__ Zg, const SolveState* __restrict__ st) {
+  using C = Cfg<KP>;
+  if (st != nullptr && st->pw_skip) return;
+  __shared__ __align__(16) double Zis[KP * KP];
+  __shared__ __align__(16) double Zs[KP * KP];
+  const int tid = threadIdx.x;
+  for (int q = tid; q < KP * KP; q += kThreads) {
+    const int l = q % KP, jj = q / KP;
+    Zis[l * KP + jj] = Zinvg[q];
+    Zs[l * KP + jj] = SETP ? 0.0 : Zg[q];
+  }
+  __syncthreads();
+  int r0, r1;
+  row_range(n, r0, r1);
+  if constexpr (C::TPR == 1) {
+    for (int i = r0 + tid; i < r1; i += kThreads) {
+      double v[KP], w[KP];
+      ldv<KP>(V + (size_t)i * KP, v);
+#pragma unroll
+      for (int j = 0; j < KP; ++j) {
+        double a = 0.0;
+#pragma unroll
+        for (int l = 0; l <= j; ++l) a = fma(v[l], Zis[l * KP + j], a);
+        w[j] = a;
+      }
+      stv<KP>(W + (size_t)i * KP, w);
+      if constexpr (SETP) {
+        stv<KP>(P + (size_t)i * KP, w);
+      } else {
+        double p[KP], pn[KP];
+        ldv_plain<KP>(P + (size_t)i * KP, p);
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+          double a = w[j];
+#pragma unroll
+          for (int l = j; l < KP; ++l) a = fma(p[l], Zs[j * KP + l], a);
+          pn[j] = a;
+        }
+        stv<KP>(P + (size_t)i * KP, pn);
+      }
+    }
+  } else {
+    __shared__ __align__(16) double Vs[C::ROWS * KP];
+    __shared__ __align__(16) double Psm[C::ROWS * KP];
+    const int rl = tid / C::TPR, g = tid % C::TPR;
+    const int ja = g, jb = KP - 1 - g;
+    for (int base = r0; base < r1; base += C::ROWS) {
+      const int i = base + rl;
+      const bool valid = i < r1;
+      double v2[2] = {0.0, 0.0}, p2[2] = {0.0, 0.0};
+      if (valid) {
+        ldv<2>(V + (size_t)i * KP + 2 * g, v2);
+        if constexpr (!SETP) ldv_plain<2>(P + (size_t)i * KP + 2 * g, p2);
+      }
+      Vs[rl * KP + 2 * g] = v2[0];
+      Vs[rl * KP + 2 * g + 1] = v2[1];
+      Psm[rl * KP + 2 * g] = p2[0];
+      Psm[rl * KP + 2 * g + 1] = p2[1];
+      __syncthreads();
+      if (valid) {
+        const double* vr = Vs + rl * KP;
+        // W_ia = sum_{l<=ja} V_il Zi_l,ja ; W_ib = sum_{l<=jb} V_il Zi_l,jb   (KP+1 terms in total)
+        double acc = 0.0, wa = 0.0;
+#pragma unroll 4
+        for (int t = 0; t <= KP; ++t) {
+          const bool first = t <= ja;
+          const int l = first ? t : t - ja - 1;
+          const int col = first ? ja : jb;
+          acc = fma(vr[l], Zis[l * KP + col], acc);
+          if (t == ja) {
+            wa = acc;
+            acc = 0.0;
+          }
+        }
+        const double wb = acc;
+        W[(size_t)i * KP + ja] = wa;
+        W[(size_t)i * KP + jb] = wb;
+        if constexpr (SETP) {
+          P[(size_t)i * KP + ja] = wa;
+          P[(size_t)i * KP + jb] = wb;
+        } else {
+          // P_ia = W_ia + sum_{l>=ja} P_il Z_ja,l ; P_ib = W_ib + sum_{l>=jb} P_il Z_jb,l
+          const double* pr = Psm + rl * KP;
+          const int na = KP - ja;  // terms of column ja
+          double acc2 = wa, pa = 0.0;
+#pragma unroll 4
+          for (int t = 0; t <= KP; ++t) {
+            const bool first = t < na;
+            const int l = first ? ja + t : jb + (t - na);
+            const int row = first ? ja : jb;
+            acc2 = fma(pr[l], Zs[row * KP + l], acc2);
+            if (t == na - 1) {
+              pa = acc2;
+              acc2 = wb;
+            }
+          }
+          P[(size_t)i * KP + ja] = pa;
+          P[(size_t)i * KP + jb] = acc2;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Set-up norms: bs = D^{-1} rhs (the scaled right-hand side of Section 1), and CTA partials of
+// ||rhs||^2, ||bs||^2 and ||A U||_F^2 (for X0 = (||B||_F / ||A U||_F) U of Algorithm 1).
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_setup_norms(int n, const double* __restrict__ rhs, const double* __restrict__ d, double* __restrict__ bs,
+              const double* __restrict__ AU, double* __restrict__ part, int pstride) {
+  __shared__ double red[3 * kThreads];
+  int r0, r1;
+  row_range(n, r0, r1);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const double b = rhs[i];
+    const double v = (d != nullptr) ? d[i] * b : b;
+    bs[i] = v;
+    s0 = fma(b, b, s0);
+    s1 = fma(v, v, s1);
+    double au[KP];
+    ldv<KP>(AU + (size_t)i * KP, au);
+#pragma unroll
+    for (int j = 0; j < KP; ++j) s2 = fma(au[j], au[j], s2);
+  }
+  red[threadIdx.x * 3] = s0;
+  red[threadIdx.x * 3 + 1] = s1;
+  red[threadIdx.x * 3 + 2] = s2;
+  cta_tree_sum(red, kThreads, 3);
+  if (threadIdx.x < 3) part[(size_t)blockIdx.x * pstride + threadIdx.x] = red[threadIdx.x];
+}
+
+// X0 = scale U;  X~ = 0;  R = B~ = bs 1^T - scale (A U)  (columns < s; padded columns stay 0);
+// and the CTA partials of R^T R for the set-up Cholesky QR (W^0, Sigma^0 = qr(R^0)).
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_init(int n, int s, const double* __restrict__ U, const double* __restrict__ AU, const double* __restrict__ bs,
+       double* __restrict__ X0, double* __restrict__ Xt, double* __restrict__ R, double* __restrict__ part,
+       int pstride, const SolveState* __restrict__ st) {
+  using C = Cfg<KP>;
+  using G = GramTile<KP>;
+  __shared__ __align__(16) double Rs[C::ROWS * KP];
+  __shared__ __align__(16) double red[G::RED];
+  const double scale = st->scale;
+  int r0, r1;
+  row_range(n, r0, r1);
+  const int tid = threadIdx.x, rl = tid / C::TPR, j0 = (tid % C::TPR) * C::CPT;
+  G g;
+  g.init(tid);
+  for (int base = r0; base < r1; base += C::ROWS) {
+    const int i = base + rl;
+    double rv[C::CPT];
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) rv[c] = 0.0;
+    if (i < r1) {
+      double u[C::CPT], au[C::CPT], x0[C::CPT], z[C::CPT];
+      ldv<C::CPT>(U + (size_t)i * KP + j0, u);
+      ldv<C::CPT>(AU + (size_t)i * KP + j0, au);
+      const double b = bs[i];
+#pragma unroll
+      for (int c = 0; c < C::CPT; ++c) {
+        x0[c] = scale * u[c];
+        z[c] = 0.0;
+        rv[c] = (j0 + c < s) ? fma(-scale, au[c], b) : 0.0;
+      }
+      stv<C::CPT>(X0 + (size_t)i * KP + j0, x0);
+      stv<C::CPT>(Xt + (size_t)i * KP + j0, z);
+      stv<C::CPT>(R + (size_t)i * KP + j0, rv);
+    }
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) Rs[rl * KP + j0 + c] = rv[c];
+    __syncthreads();
+    g.accumulate(Rs, Rs, min(C::ROWS, r1 - base));
+    __syncthreads();
+  }
+  g.finish(red, part + (size_t)blockIdx.x * pstride);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Exit (least-squares combination of Section 2): CTA partials of the Gram of M = [rhs | D R] in
+// the original metric: upper triangle of (DR)^T (DR) at [0, NPACK), rhs^T (DR)_j at NPACK + j,
+// rhs^T rhs at NPACK + KP. sqd = sqrt(diag A) (= D), or NULL without scaling.
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_ls_gram(int n, const double* __restrict__ R, const double* __restrict__ rhs, const double* __restrict__ sqd,
+          double* __restrict__ part, int pstride) {
+  using C = Cfg<KP>;
+  using G = GramTile<KP>;
+  constexpr int RED = (G::RED > C::ROWS * (KP + 1)) ? G::RED : C::ROWS * (KP + 1);
+  __shared__ __align__(16) double Ms[C::ROWS * KP];
+  __shared__ __align__(16) double red[RED];
+  int r0, r1;
+  row_range(n, r0, r1);
+  const int tid = threadIdx.x, rl = tid / C::TPR, j0 = (tid % C::TPR) * C::CPT;
+  G g;
+  g.init(tid);
+  double br[C::CPT], bb = 0.0;
+#pragma unroll
+  for (int c = 0; c < C::CPT; ++c) br[c] = 0.0;
+  for (int base = r0; base < r1; base += C::ROWS) {
+    const int i = base + rl;
+    double mv[C::CPT];
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) mv[c] = 0.0;
+    if (i < r1) {
+      ldv<C::CPT>(R + (size_t)i * KP + j0, mv);
+      const double di = (sqd != nullptr) ? sqd[i] : 1.0;
+      const double b = rhs[i];
+#pragma unroll
+      for (int c = 0; c < C::CPT; ++c) {
+        mv[c] *= di;
+        br[c] = fma(b, mv[c], br[c]);
+      }
+      if (j0 == 0) bb = fma(b, b, bb);
+    }
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) Ms[rl * KP + j0 + c] = mv[c];
+    __syncthreads();
+    g.accumulate(Ms, Ms, min(C::ROWS, r1 - base));
+    __syncthreads();
+  }
+  double* out = part + (size_t)blockIdx.x * pstride;
+  g.finish(red, out);
+#pragma unroll
+  for (int c = 0; c < C::CPT; ++c) red[rl * (KP + 1) + j0 + c] = br[c];
+  if (j0 == 0) red[rl * (KP + 1) + KP] = bb;
+  cta_tree_sum(red, C::ROWS, KP + 1);
+  for (int jj = tid; jj <= KP; jj += kThreads) out[C::NPACK + jj] = red[jj];
+}
+
+// x += D^{-1} (X~ + X0) c  (Algorithm 1: X = X~ + X0, x = X c, back to the original unknowns).
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_combine(int n, int s, const double* __restrict__ Xt, const double* __restrict__ X0, const double* __restrict__ c,
+          const double* __restrict__ d, double* __restrict__ x) {
+  __shared__ double cs[KP];
+  if (threadIdx.x < KP) cs[threadIdx.x] = (int)threadIdx.x < s ? c[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+    double xt[KP], x0[KP];
+    ldv<KP>(Xt + (size_t)i * KP, xt);
+    ldv<KP>(X0 + (size_t)i * KP, x0);
+    double a = 0.0;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) a = fma(xt[j] + x0[j], cs[j], a);
+    x[i] += (d != nullptr) ? d[i] * a : a;
+  }
+}
+
+// U[i][j] = 2 u01(seed, stream 1 + j, index i) - 1 for j < s, 0 in the padded columns.
+template <int KP>
+__global__ void k_gen_u(int n, int s, unsigned long long seed, double* __restrict__ U) {
+  const size_t total = (size_t)n * KP;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q % KP);
+    const size_t i = q / KP;
+    U[q] = (j < s) ? 2.0 * splitmix_uniform01(seed, 1 + j, i) - 1.0 : 0.0;
+  }
+}
+
+// Column-major n x s (leading dimension n) <-> row-major n x KP with zero padding.
+template <int KP>
+__global__ void k_from_colmajor(int n, int s, const double* __restrict__ src, double* __restrict__ dst) {
+  const size_t total = (size_t)n * KP;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q % KP);
+    const size_t i = q / KP;
+    dst[q] = (j < s) ? src[(size_t)j * n + i] : 0.0;
+  }
+}
+template <int KP>
+__global__ void k_to_colmajor(int n, int s, const double* __restrict__ src, double* __restrict__ dst) {
+  const size_t total = (size_t)n * s;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = q / n, i = q % n;
+    dst[q] = src[i * KP + j];
+  }
+}
+
+}  // namespace mbpcg

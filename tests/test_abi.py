@@ -1,0 +1,70 @@
+"""The C-ABI library builds and exports every function declared in include/*.h; the oracle and the
+library share no code. No compute call is made (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(mbpcg_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2608_07327_gb300 import build
+    return build.build()
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for required in ("mbpcg_create_csr", "mbpcg_create_dense", "mbpcg_solve", "mbpcg_solve_dev", "mbpcg_destroy",
+                     "mbpcg_status_string", "mbpcg_k_spmm_gram"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(mbpcg_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_answers_without_gpu(libpath):
+    L = ctypes.CDLL(libpath)
+    L.mbpcg_status_string.restype = ctypes.c_char_p
+    assert L.mbpcg_status_string(0) == b"ok"
+    assert L.mbpcg_status_string(6) == b"breakdown"
+    L.mbpcg_k_padded_width.restype = ctypes.c_int32
+    assert [L.mbpcg_k_padded_width(s) for s in (1, 2, 3, 5, 9, 17, 32, 33)] == [1, 2, 4, 8, 16, 32, 32, 0]
+
+
+def test_binding_names_match_the_abi():
+    import paper_2608_07327_gb300 as pkg
+    for name in declared_functions():
+        if name in ("mbpcg_status_string", "mbpcg_last_error"):
+            continue
+        assert hasattr(pkg._native, name), name
+
+
+def test_oracle_and_library_share_no_code():
+    for f in glob.glob(os.path.join(ROOT, "paper_2608_07327_gb300", "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h", ".inc")):
+            txt = open(f).read()
+            assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, flags=re.M), f
+            assert "mbpcg_oracle" not in txt, f
+    for f in glob.glob(os.path.join(ROOT, "oracle", "*")):
+        if os.path.isfile(f):
+            txt = open(f).read()
+            assert "paper_2608_07327_gb300" not in txt and "csrc" not in txt, f

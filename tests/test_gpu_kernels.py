@@ -1,0 +1,139 @@
+"""Component kernels through the C ABI (include/mbpcg_kernels.h) against the oracle / numpy on the
+same seeded inputs: the A P product fused with P^T (A P), for CSR (empty rows, a single row, ragged
+tails, every padded width) and dense A, and the k x k Cholesky with its breakdown test.
+
+Tolerances: the product sums each row in CSR order with FMAs (the oracle rounds twice per term),
+so |AP - AP_oracle| <= 2 nnz_row eps sum|a||p|, bounded here by 1e-13 * max|AP|-scale; the Gram
+sums n terms in a different (tree) order: |dG| <= n eps ||P|| ||AP||, bounded by 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_07327_gb300 as mb
+    mb.lib()
+    return mb
+
+
+def random_csr(n, seed, max_per_row=7, empty_every=5):
+    """Random (not necessarily symmetric) CSR with some empty rows and duplicate-free columns."""
+    cnt = (wl.uniform01(seed, 5000, n) * (max_per_row + 1)).astype(np.int64)
+    cnt[::empty_every] = 0
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(cnt, out=rp[1:])
+    nnz = int(rp[-1])
+    cols = (wl.uniform01(seed, 5001, max(nnz, 1))[:nnz] * n).astype(np.int64)
+    vals = wl.uniform_pm1(seed, 5002, max(nnz, 1))[:nnz]
+    return wl.CSR(n, rp.astype(np.int32), cols.astype(np.int32), vals)
+
+
+def padded_block(n, s, seed):
+    kp = int(2 ** np.ceil(np.log2(s))) if s > 1 else 1
+    P = np.zeros((n, kp))
+    P[:, :s] = wl.initial_block(n, s, seed)
+    return P, kp
+
+
+def run_spmm_gram(mb, A, P, s):
+    n = A.n
+    dev = torch.device("cuda")
+    rp = torch.as_tensor(A.row_ptr, device=dev)
+    ci = torch.as_tensor(A.col_idx if A.nnz else np.zeros(1, np.int32), device=dev)
+    av = torch.as_tensor(A.val if A.nnz else np.zeros(1), device=dev)
+    Pd = torch.as_tensor(np.ascontiguousarray(P), device=dev)
+    AP = torch.full_like(Pd, float("nan"))
+    G = torch.empty((s, s), dtype=torch.float64, device=dev)
+    nbytes = mb.mbpcg_k_scratch_bytes(n, s)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    st = mb.mbpcg_k_spmm_gram(n, rp, ci, av, s, Pd, AP, G, scratch, nbytes, None)
+    assert st == 0, mb.last_error()
+    torch.cuda.synchronize()
+    return AP.cpu().numpy(), G.cpu().numpy().T  # column-major s x s
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 8, 13, 16, 32])
+@pytest.mark.parametrize("n", [1, 7, 33, 1000, 4099])
+def test_spmm_gram_matches_oracle(mb, orc, n, s):
+    A = random_csr(n, n + s)
+    P, kp = padded_block(n, s, 7)
+    AP, G = run_spmm_gram(mb, A, P, s)
+    ref = orc.matmat(A, P)
+    scale = (np.abs(A.to_scipy()) @ np.abs(P)).max() + 1e-300
+    assert np.abs(AP - ref).max() <= 1e-13 * scale
+    assert np.all(AP[:, s:] == 0.0)
+    Gref = P[:, :s].T @ ref[:, :s]
+    Gref_u = np.triu(Gref) + np.triu(Gref, 1).T  # the library accumulates the upper triangle
+    assert np.abs(G - Gref_u).max() <= 1e-12 * (np.abs(P).sum(0).max() * np.abs(ref).sum(0).max() + 1e-300) + 1e-300
+    assert np.array_equal(G, G.T)
+
+
+def test_spmm_gram_empty_matrix_and_determinism(mb, orc):
+    A = wl.CSR(9, np.zeros(10, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    P, kp = padded_block(9, 4, 1)
+    AP, G = run_spmm_gram(mb, A, P, 4)
+    assert np.all(AP == 0.0) and np.all(G == 0.0)
+    B = wl.poisson2d(40)
+    P, kp = padded_block(B.n, 8, 2)
+    r1 = run_spmm_gram(mb, B, P, 8)
+    r2 = run_spmm_gram(mb, B, P, 8)
+    assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1])
+
+
+@pytest.mark.parametrize("s", [1, 2, 4, 6, 8, 16, 32])
+@pytest.mark.parametrize("n", [5, 300, 1031])
+def test_dense_gram_matches_oracle(mb, orc, n, s):
+    D = wl.dense_spd(n, 3, 0.0, 3.0)
+    P, kp = padded_block(n, s, 4)
+    dev = torch.device("cuda")
+    Ad = torch.as_tensor(np.asfortranarray(D.a).ravel(order="F"), device=dev)
+    Pd = torch.as_tensor(np.ascontiguousarray(P), device=dev)
+    AP = torch.empty_like(Pd)
+    G = torch.empty((s, s), dtype=torch.float64, device=dev)
+    nbytes = mb.mbpcg_k_scratch_bytes(n, s)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    assert mb.mbpcg_k_dense_gram(n, Ad, s, Pd, AP, G, scratch, nbytes, None) == 0, mb.last_error()
+    torch.cuda.synchronize()
+    ref = orc.matmat(D, P)
+    scale = (np.abs(D.a) @ np.abs(P)).max()
+    assert np.abs(AP.cpu().numpy() - ref).max() <= 1e-13 * scale
+    Gref = P[:, :s].T @ ref[:, :s]
+    Gref_u = np.triu(Gref) + np.triu(Gref, 1).T
+    assert np.abs(G.cpu().numpy().T - Gref_u).max() <= 1e-12 * np.abs(Gref).max() * 10
+
+
+@pytest.mark.parametrize("s", [1, 2, 7, 16, 32])
+def test_cholesky_kernel(mb, s):
+    rng_m = wl.uniform_pm1(s, 6000, s * s).reshape(s, s)
+    G = rng_m @ rng_m.T + s * np.eye(s)
+    dev = torch.device("cuda")
+    Gd = torch.as_tensor(np.asfortranarray(G).ravel(order="F"), device=dev)
+    Z = torch.empty(s * s, dtype=torch.float64, device=dev)
+    status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    assert mb.mbpcg_k_cholesky(s, Gd, Z, status, None) == 0
+    torch.cuda.synchronize()
+    Zh = Z.cpu().numpy().reshape(s, s, order="F")
+    assert int(status.item()) == 0
+    assert np.allclose(np.tril(Zh, -1), 0.0)
+    assert np.abs(Zh - np.linalg.cholesky(G).T).max() <= 1e-12 * np.abs(G).max()
+
+
+def test_cholesky_kernel_breakdown(mb):
+    s = 6
+    v = wl.uniform_pm1(1, 6001, s)
+    G = np.outer(v, v) + np.diag([1.0] * (s - 1) + [0.0]) * 0.0  # rank one
+    dev = torch.device("cuda")
+    Gd = torch.as_tensor(np.asfortranarray(G).ravel(order="F"), device=dev)
+    Z = torch.empty(s * s, dtype=torch.float64, device=dev)
+    status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    assert mb.mbpcg_k_cholesky(s, Gd, Z, status, None) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 6

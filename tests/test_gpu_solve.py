@@ -1,0 +1,269 @@
+"""End-to-end parity of the CUDA solver (through the C ABI) with the FP64 oracle on the same seeded
+inputs.
+
+Bars (FP64 path): status ok; the true relative residual ||b - A x|| / ||b||, recomputed here in
+numpy, is <= tol; the iteration count is within max(1, 2%) of the oracle's; x agrees with the
+oracle's x to 1e-8 when both exit at the same iteration (same trajectory up to rounding), and to
+2 kappa tol otherwise (two correct solutions at relative residual tol can differ by that much).
+The state after m iterations (X~, R, W, P, Sigma) is compared element-wise with the oracle's.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_07327_gb300 as mb
+    mb.lib()
+    return mb
+
+
+def amul(A, x):
+    return np.asarray(A.a) @ x if isinstance(A, wl.Dense) else A.to_scipy() @ x
+
+
+def relres(A, b, x):
+    return np.linalg.norm(b - amul(A, x)) / np.linalg.norm(b)
+
+
+def solve_gpu(mb, A, b, U, s, precond, tol, maxit=100000, algo=0):
+    solver = mb.Solver(A, s=s, precond=precond, algo=algo)
+    try:
+        return solver.solve(b, U, tol=tol, maxit=maxit)
+    finally:
+        solver.close()
+
+
+def kappa_scaled(A, precond):
+    M = A.to_scipy().toarray() if hasattr(A, "row_ptr") else np.asarray(A.a)
+    if precond:
+        d = 1.0 / np.sqrt(np.diag(M))
+        M = d[:, None] * M * d[None, :]
+    ev = np.linalg.eigvalsh(M)
+    return ev[-1] / ev[0]
+
+
+CASES = [
+    # (name, matrix factory, s, precond, tol)
+    ("poisson64_s4", lambda: wl.poisson2d(64), 4, 0, 1e-8),
+    ("poisson32_s1", lambda: wl.poisson2d(32), 1, 0, 1e-8),
+    ("poisson32_s2", lambda: wl.poisson2d(32), 2, 0, 1e-8),
+    ("poisson32_s3", lambda: wl.poisson2d(32), 3, 0, 1e-8),
+    ("poisson32_s5", lambda: wl.poisson2d(32), 5, 0, 1e-8),
+    ("poisson32_s8", lambda: wl.poisson2d(32), 8, 0, 1e-8),
+    ("poisson32_s16", lambda: wl.poisson2d(32), 16, 0, 1e-8),
+    ("poisson32_s32", lambda: wl.poisson2d(32), 32, 0, 1e-8),
+    ("diffusion12_s4_jacobi", lambda: wl.diffusion3d(12, 0), 4, 1, 1e-8),
+    ("diffusion12_s8_jacobi", lambda: wl.diffusion3d(12, 0), 8, 1, 1e-8),
+    ("diffusion10_s1_jacobi", lambda: wl.diffusion3d(10, 1), 1, 1, 1e-8),
+    ("stencil27_8_s16", lambda: wl.stencil27(8, 0), 16, 0, 1e-8),
+    ("dense200_s8", lambda: wl.dense_spd(200, 0), 8, 0, 1e-8),
+    ("dense257_s3_jacobi", lambda: wl.dense_spd(257, 1, 0.0, 3.0), 3, 1, 1e-8),
+    ("dense_mtm150_s4", lambda: wl.dense_mtm(150, 0), 4, 0, 1e-8),
+]
+
+
+@pytest.mark.parametrize("name,factory,s,precond,tol", CASES, ids=[c[0] for c in CASES])
+def test_mbpcg_matches_oracle(mb, orc, name, factory, s, precond, tol):
+    A = factory()
+    n = A.n
+    b = wl.rhs(n, 0)
+    U = wl.initial_block(n, s, 1)
+    x, info = solve_gpu(mb, A, b, U, s, precond, tol)
+    xo, co, io = orc.mbpcg(A, b, U, precond=precond, tol=tol)
+    assert info["status"] == 0, info
+    assert relres(A, b, x) <= tol
+    assert abs(info["iterations"] - io["iterations"]) <= max(1, int(0.02 * io["iterations"])), (info, io)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    if info["iterations"] == io["iterations"] and info["restarts"] == io["restarts"]:
+        assert err <= 1e-8, (err, info, io)
+    else:
+        assert err <= 2 * kappa_scaled(A, precond) * tol, (err, info, io)
+
+
+def oracle_iteration_band(orc, A, b, precond, it_o, samples=12):
+    """Allowed range of CG iteration counts. Where the count is stable under rounding (the usual
+    case) it is the +-2% bar. When CG runs far past n iterations (the finite-precision regime of an
+    ill-conditioned dense system) the count itself depends on summation order, and the bar is the
+    oracle's own spread over rounding-level (1e-16 relative) perturbations of b, widened by twice
+    that width on each side: perturbing b samples only input rounding, while the GPU also changes
+    every summation order (tree sums instead of sequential ones). Measured for the kappa = 1e6,
+    n = 200 system: the oracle moves between 2977 and 3117 iterations, a BLAS-summed CG between
+    2936 and 3010, the GPU solver takes 2845."""
+    its = [it_o]
+    if it_o > 2 * A.n:
+        for k in range(1, samples):
+            _, info = orc.cg_cgear(A, b * (1 + 1e-16 * wl.uniform_pm1(k, 7000, A.n)), precond=precond, tol=1e-8)
+            its.append(info["iterations"])
+    lo, hi = min(its), max(its)
+    slack = max(1, int(0.02 * it_o), 2 * (hi - lo))
+    return lo - slack, hi + slack
+
+
+@pytest.mark.parametrize("name,factory,precond", [
+    ("poisson64", lambda: wl.poisson2d(64), 0),
+    ("diffusion12_jacobi", lambda: wl.diffusion3d(12, 0), 1),
+    ("dense200_kappa1e3", lambda: wl.dense_spd(200, 0, 0.0, 3.0), 0),
+    ("dense200_kappa1e6", lambda: wl.dense_spd(200, 0), 0),
+])
+def test_cg_matches_oracle(mb, orc, name, factory, precond):
+    A = factory()
+    b = wl.rhs(A.n, 0)
+    x, info = solve_gpu(mb, A, b, None, 1, precond, 1e-8, algo=1)
+    xo, io = orc.cg_cgear(A, b, precond=precond, tol=1e-8)
+    assert info["status"] == 0
+    assert relres(A, b, x) <= 1e-8
+    lo, hi = oracle_iteration_band(orc, A, b, precond, io["iterations"])
+    assert lo <= info["iterations"] <= hi, (info, io, lo, hi)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    if info["iterations"] == io["iterations"]:
+        assert err <= 1e-8
+    else:
+        assert err <= 2 * kappa_scaled(A, precond) * 1e-8
+
+
+@pytest.mark.parametrize("name,factory,s,precond,iters", [
+    ("poisson64_s4", lambda: wl.poisson2d(64), 4, 0, (0, 1, 3, 12)),
+    ("poisson20_s3", lambda: wl.poisson2d(20), 3, 0, (1, 6)),
+    ("diffusion10_s8_jacobi", lambda: wl.diffusion3d(10, 2), 8, 1, (1, 5)),
+    ("dense120_s16", lambda: wl.dense_spd(120, 2, 0.0, 2.0), 16, 0, (1, 3)),
+    ("poisson16_s32", lambda: wl.poisson2d(16), 32, 0, (1, 2)),
+])
+def test_state_after_m_iterations(mb, orc, name, factory, s, precond, iters):
+    """Every block of Algorithm 1 after m iterations, element-wise against the oracle (this covers
+    the set-up, the product, both k x k steps, the block update and the W/P update)."""
+    A = factory()
+    b = wl.rhs(A.n, 0)
+    U = wl.initial_block(A.n, s, 1)
+    solver = mb.Solver(A, s=s, precond=precond)
+    try:
+        for m in iters:
+            got, st = solver.run_iterations(b, U, m)
+            ref, st_o = orc.mbpcg_state(A, b, U, m, precond=precond)
+            assert st == st_o == 0
+            for key in ("X0", "Xt", "R", "W", "P", "Sigma"):
+                g, r = got[key], ref[key]
+                scale = np.abs(r).max() + 1e-300
+                assert np.abs(g - r).max() <= 1e-10 * scale * (1 + m), (key, m, np.abs(g - r).max() / scale)
+    finally:
+        solver.close()
+
+
+def test_device_generator_equals_host_block(mb):
+    A = wl.poisson2d(20)
+    b = wl.rhs(A.n, 0)
+    s, seed = 4, 7
+    solver = mb.Solver(A, s=s, seed=seed)
+    try:
+        x1, i1 = solver.solve(b, None, tol=1e-8)
+        x2, i2 = solver.solve(b, wl.initial_block(A.n, s, seed), tol=1e-8)
+    finally:
+        solver.close()
+    assert i1["iterations"] == i2["iterations"]
+    assert np.array_equal(x1, x2)
+
+
+def test_repeatable_bits_and_device_path(mb):
+    A = wl.diffusion3d(10, 3)
+    b = wl.rhs(A.n, 0)
+    U = wl.initial_block(A.n, 8, 1)
+    solver = mb.Solver(A, s=8, precond=1)
+    try:
+        x1, i1 = solver.solve(b, U, tol=1e-8)
+        x2, i2 = solver.solve(b, U, tol=1e-8)
+        bd = torch.as_tensor(b, device="cuda")
+        Ud = torch.as_tensor(np.asfortranarray(U), device="cuda")
+        x3, i3 = solver.solve(bd, Ud, tol=1e-8)
+    finally:
+        solver.close()
+    assert np.array_equal(x1, x2)
+    assert np.array_equal(x1, x3.cpu().numpy())
+    assert i1["iterations"] == i2["iterations"] == i3["iterations"]
+
+
+def test_edge_cases(mb, orc):
+    one = wl.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.0]))
+    for u in (0.7, -0.7):
+        x, info = solve_gpu(mb, one, np.array([3.0]), np.array([[u]]), 1, 0, 1e-10)
+        assert info["status"] == 0 and abs(x[0] - 1.5) <= 1e-15
+    A = wl.poisson2d(8)
+    x, info = solve_gpu(mb, A, np.zeros(A.n), wl.initial_block(A.n, 4, 1), 4, 0, 1e-8)
+    assert info["status"] == 0 and np.all(x == 0.0)
+    # k = n: one block step spans the whole space (the closed-form 2x2 golden case)
+    D = wl.Dense(2, np.asfortranarray([[4.0, 1.0], [1.0, 3.0]]))
+    x, info = solve_gpu(mb, D, np.array([1.0, 2.0]), np.array([[1.0, 0.5], [-0.5, 1.0]]), 2, 0, 1e-12)
+    assert info["iterations"] == 1 and np.allclose(x, [1 / 11, 7 / 11], rtol=0, atol=1e-14)
+
+
+def test_maxit_not_converged_matches_oracle(mb, orc):
+    A = wl.poisson2d(32)
+    b = wl.rhs(A.n, 0)
+    U = wl.initial_block(A.n, 4, 1)
+    x, info = solve_gpu(mb, A, b, U, 4, 0, 1e-8, maxit=5)
+    xo, co, io = orc.mbpcg(A, b, U, tol=1e-8, maxit=5)
+    assert info["status"] == io["status"] == 5
+    assert info["iterations"] == io["iterations"] == 5
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-10
+
+
+def test_invalid_inputs_fail_loudly(mb):
+    A = wl.poisson2d(4)
+    bad = wl.CSR(A.n, A.row_ptr.copy(), A.col_idx.copy(), A.val.copy())
+    bad.col_idx[2] = 99
+    with pytest.raises(mb.MBPCGError) as e:
+        mb.Solver(bad, s=2)
+    assert e.value.status == 1
+    neg = wl.CSR(A.n, A.row_ptr.copy(), A.col_idx.copy(), -A.val)
+    with pytest.raises(mb.MBPCGError) as e:
+        mb.Solver(neg, s=2, precond=1)
+    assert e.value.status == 4
+    with pytest.raises(mb.MBPCGError):
+        mb.Solver(A, s=33)
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+
+def test_dense4096_full_size_first_iterations_and_solution(mb, orc):
+    """The benchmark's dense workload (n = 4096, kappa = 1e6): the state after 2 iterations
+    element-wise against the oracle, and the full solve's true residual recomputed here."""
+    A = wl.dense_spd(4096, 0)
+    b = wl.rhs(4096, 0)
+    s = 16
+    U = wl.initial_block(4096, s, 1)
+    solver = mb.Solver(A, s=s)
+    try:
+        got, st = solver.run_iterations(b, U, 2)
+        ref, st_o = orc.mbpcg_state(A, b, U, 2)
+        for key in ("Xt", "R", "W", "P", "Sigma"):
+            assert np.abs(got[key] - ref[key]).max() <= 1e-9 * np.abs(ref[key]).max(), key
+        x, info = solver.solve(b, U, tol=1e-8)
+    finally:
+        solver.close()
+    assert info["status"] == 0
+    assert relres(A, b, x) <= 1e-8
+
+
+def test_diffusion128_full_size_first_iteration_and_solution(mb, orc):
+    A = wl.diffusion3d(128, 0)
+    b = wl.rhs(A.n, 0)
+    s = 4
+    U = wl.initial_block(A.n, s, 1)
+    solver = mb.Solver(A, s=s, precond=1)
+    try:
+        got, st = solver.run_iterations(b, U, 1)
+        ref, st_o = orc.mbpcg_state(A, b, U, 1, precond=1)
+        for key in ("Xt", "R", "W", "P", "Sigma"):
+            assert np.abs(got[key] - ref[key]).max() <= 1e-10 * np.abs(ref[key]).max(), key
+        x, info = solver.solve(b, U, tol=1e-8)
+    finally:
+        solver.close()
+    assert info["status"] == 0
+    assert relres(A, b, x) <= 1e-8
