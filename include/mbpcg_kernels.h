@@ -35,6 +35,22 @@ int mbpcg_k_spmm_gram(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                       int32_t s, const double* P, double* AP, double* G, void* scratch,
                       size_t scratch_bytes, void* stream);
 
+/*
+ * mbpcg_k_spmm_gram without any device allocation. The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc (a host framework or plugin that owns all device memory,
+ * a real-time loop that cannot afford cudaMalloc's device synchronisation, a process with no
+ * device memory left to give). Its scratch is a fixed array of about 400 KB compiled into the
+ * library, which every GPU that loads the library holds until the process exits; nothing is
+ * allocated or freed. Limits: s <= 16 and at most 320 CTAs of partial sums (a GB300 uses 304);
+ * larger requests return MBPCG_ERR_INVALID with a message. The first call on each device looks up
+ * the array's device address, so make that first call before any stream capture. All calls share
+ * the one array: calls whose work overlaps on the GPU (e.g. on two streams) race and give wrong
+ * results; serialise them. Inputs, outputs and errors are those of mbpcg_k_spmm_gram.
+ */
+int mbpcg_k_spmm_gram_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                              const double* vals, int32_t s, const double* P, double* AP,
+                              double* G, void* stream);
+
 /* Same for dense symmetric A (column-major n x n; row i is read as column i). */
 int mbpcg_k_dense_gram(int32_t n, const double* A, int32_t s, const double* P, double* AP,
                        double* G, void* scratch, size_t scratch_bytes, void* stream);

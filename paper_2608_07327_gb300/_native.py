@@ -73,6 +73,7 @@ _SIGS = {
     "mbpcg_k_spmm_gram": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_dense_gram": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_cholesky": (ctypes.c_int, [_I32, _P, _P, _P, _P]),
+    "mbpcg_k_spmm_gram_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "mbpcg_k_spmm": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
     "mbpcg_k_dense_product": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P]),
 }
@@ -182,6 +183,11 @@ def mbpcg_k_scratch_bytes(n, s) -> int:
 def mbpcg_k_spmm_gram(n, row_ptr, col_idx, vals, s, P, AP, G, scratch, scratch_bytes, stream=None):
     return lib().mbpcg_k_spmm_gram(n, ptr(row_ptr), ptr(col_idx), ptr(vals), s, ptr(P), ptr(AP), ptr(G),
                                    ptr(scratch), scratch_bytes, stream)
+
+
+def mbpcg_k_spmm_gram_noalloc(n, row_ptr, col_idx, vals, s, P, AP, G, stream=None):
+    return lib().mbpcg_k_spmm_gram_noalloc(n, ptr(row_ptr), ptr(col_idx), ptr(vals), s, ptr(P), ptr(AP), ptr(G),
+                                           stream)
 
 
 def mbpcg_k_dense_gram(n, A, s, P, AP, G, scratch, scratch_bytes, stream=None):

@@ -754,6 +754,16 @@ int mbpcg_k_cholesky(int32_t s, const double* G, double* Z, int32_t* status_dev,
 
 namespace mbpcg {
 
+// Launch shape of the CSR product + Gram entry points (padded width, CTA count, slot stride).
+void product_gram_shape(int n, int s, int* kp, int* nb, int* pstride) {
+  const Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
+  *kp = dm.kp;
+  *nb = dm.nb;
+  *pstride = dm.pstride;
+}
+
+int set_last_error(int code, const char* msg) { return set_err(code, "%s", msg); }
+
 // G (s x s column-major, ld s) = the full symmetric matrix of a packed upper triangle.
 __global__ void k_unpack_full(const double* __restrict__ packed, int kp, int s, double* __restrict__ G) {
   for (int q = threadIdx.x; q < s * s; q += blockDim.x) {

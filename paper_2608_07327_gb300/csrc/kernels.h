@@ -86,6 +86,10 @@ __global__ void k_cg_update(int n, double* r, const double* w, double* x, double
                             const SolveState* st);
 __global__ void k_cg_finish(int n, const double* xbar, const double* d, double* x);
 
+// launch shape of the CSR product + Gram entry points, and the thread-local error message (api.cu)
+void product_gram_shape(int n, int s, int* kp, int* nb, int* pstride);
+int set_last_error(int code, const char* msg);
+
 // kernel-level helpers for the component entry points (api.cu)
 __global__ void k_unpack_full(const double* packed, int kp, int s, double* G);
 __global__ void k_chol_only(const double* G, int s, double* Z, int* status);

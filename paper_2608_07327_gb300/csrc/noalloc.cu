@@ -1,0 +1,87 @@
+// mbpcg_k_spmm_gram_noalloc: the A P + P^T(A P) component entry point for callers that cannot
+// allocate device memory.
+//
+// Who needs it: code that must not call cudaMalloc -- a host framework or plugin that owns every
+// device allocation and hands out only input/output buffers, a real-time loop where cudaMalloc's
+// implicit device synchronisation is not acceptable, or a process whose device memory is already
+// committed. mbpcg_k_spmm_gram needs a scratch buffer for its per-CTA partial sums; this variant
+// keeps that scratch in a fixed array compiled into the library instead.
+//
+// The array below is a host-side stand-in in host code, not a device address. Its device address is
+// looked up once per device (cudaGetSymbolAddress, with that device current) on the first call
+// from that device and cached; only that address is passed to kernels.
+#include <mutex>
+
+#include "../../include/mbpcg.h"
+#include "../../include/mbpcg_kernels.h"
+#include "kernels.h"
+
+namespace {
+
+// Capacity: s <= 16 (partial-slot stride npack(16) + 16 + 1 = 153 -> 156 doubles) and up to 320
+// CTAs (2 per SM on a 152-SM GB300 needs 304), plus one slot for the reduced sums:
+// 321 * 156 doubles = 400 608 bytes, held by every GPU that loads the library until exit.
+constexpr int kMaxS = 16;
+constexpr int kMaxCtas = 320;
+constexpr int kSlot = 156;
+constexpr size_t kScratchDoubles = (size_t)(kMaxCtas + 1) * kSlot;
+
+static __device__ __align__(256) double g_spmm_gram_scratch[kScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+double* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of the static scratch on the current device (set up on first use).
+int scratch_address(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return mbpcg::set_last_error(MBPCG_ERR_CUDA, "mbpcg_k_spmm_gram_noalloc: no usable current device");
+  }
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (g_scratch_addr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_spmm_gram_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return mbpcg::set_last_error(MBPCG_ERR_CUDA, "mbpcg_k_spmm_gram_noalloc: cudaGetSymbolAddress failed");
+    }
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return MBPCG_OK;
+}
+
+}  // namespace
+
+extern "C" int mbpcg_k_spmm_gram_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                         const double* vals, int32_t s, const double* P, double* AP, double* G,
+                                         void* stream) {
+  if (n < 1 || s < 1 || !row_ptr || !P || !AP || !G)
+    return mbpcg::set_last_error(MBPCG_ERR_INVALID, "mbpcg_k_spmm_gram_noalloc: bad arguments");
+  if (s > kMaxS)
+    return mbpcg::set_last_error(MBPCG_ERR_INVALID,
+                                 "mbpcg_k_spmm_gram_noalloc: s exceeds 16, the limit of its static scratch "
+                                 "(use mbpcg_k_spmm_gram with caller-provided scratch)");
+  int kp = 0, nb = 0, pstride = 0;
+  mbpcg::product_gram_shape(n, s, &kp, &nb, &pstride);
+  if (nb > kMaxCtas || pstride > kSlot)
+    return mbpcg::set_last_error(MBPCG_ERR_INVALID,
+                                 "mbpcg_k_spmm_gram_noalloc: launch needs more partial slots than its static "
+                                 "scratch holds (more than 320 CTAs)");
+  double* scratch = nullptr;
+  const int rc = scratch_address(&scratch);
+  if (rc != MBPCG_OK) return rc;
+  // Every partial slot the reduction reads (nb of them) is fully written by this call's product
+  // kernel first, so nothing in the array has to start at zero.
+  double* red = scratch + (size_t)kMaxCtas * kSlot;
+  cudaStream_t st = (cudaStream_t)stream;
+  mbpcg::row_ops(kp)->spmm(st, nb, n, row_ptr, col_idx, vals, P, AP, scratch, kSlot, nullptr, 1);
+  mbpcg::k_reduce<<<mbpcg::npack(kp), 128, 0, st>>>(scratch, nb, kSlot, red, nullptr);
+  mbpcg::k_unpack_full<<<1, 256, 0, st>>>(red, kp, s, G);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return mbpcg::set_last_error(MBPCG_ERR_CUDA, cudaGetErrorString(e));
+  return MBPCG_OK;
+}
