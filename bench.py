@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--kernel-launches", type=int, default=20, help="launches of the dominant kernel timed alone")
     p.add_argument("--cpu-sample-iters", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--launch-mode", default="graph", choices=["graph", "eager"],
+                   help="eager: host-launched loop (for profilers; same kernels and results)")
     return p.parse_args()
 
 
@@ -173,8 +175,9 @@ def run_ours(args, world, rank, local):
     b = wl.rhs(n, 0)
     U = wl.initial_block(n, s, 1)
     dev = torch.device("cuda", local)
-    solver = mb.Solver(A, s=s, precond=cfg["precond"])
-    cg = mb.Solver(A, algo=mb.MBPCG_ALGO_CG, precond=cfg["precond"])
+    mode = mb.MBPCG_LAUNCH_EAGER if args.launch_mode == "eager" else mb.MBPCG_LAUNCH_GRAPH
+    solver = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode)
+    cg = mb.Solver(A, algo=mb.MBPCG_ALGO_CG, precond=cfg["precond"], launch_mode=mode)
     stream = solver.stream
     bd = torch.as_tensor(b, device=dev)
     Ud = torch.as_tensor(np.asfortranarray(U).ravel(order="F"), device=dev)
@@ -286,6 +289,7 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["desc"], "n": n, "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
                        "tol": cfg["tol"], "l2": "flushed before every step (256 MB write)",
+                       "launch_mode": args.launch_mode,
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "iterations": info["iterations"], "restarts": info["restarts"], "relres_true": relres_check,
             "cg_ms": round(cg_ms, 4), "cg_iterations": cg_infos[-1]["iterations"],

@@ -47,7 +47,7 @@ typedef enum {
   MBPCG_ERR_NOT_SPD = 4,   /* a diagonal entry is missing, not positive or not finite */
   MBPCG_NOT_CONVERGED = 5, /* maxit reached; x_out holds the best iterate */
   MBPCG_BREAKDOWN = 6,     /* a k x k Cholesky pivot was not positive; x_out holds the best iterate */
-  MBPCG_ERR_TIMEOUT = 7    /* reserved: a device-side wait exceeded its limit */
+  MBPCG_ERR_TIMEOUT = 7    /* a bounded device-side wait (TMA/mbarrier) ran out of time */
 } mbpcg_status;
 
 /* Symmetric diagonal scaling of Section 1: D = diag(sqrt(A_jj)), the solver runs on
@@ -128,6 +128,13 @@ int mbpcg_solve_dev(mbpcg_handle h, const double* b, const double* U, double tol
 int mbpcg_run_iterations_dev(mbpcg_handle h, const double* b, const double* U, int32_t iters,
                              double* X0, double* Xt, double* R, double* W, double* P,
                              double* Sigma);
+
+/* How a solve drives its iteration loop. GRAPH (default): one CUDA graph launch per inner solve,
+ * the loop being a device-side WHILE node. EAGER: the same kernels launched one by one from the
+ * host, which checks the solve state every 16 iterations; meant for profilers (they do not see
+ * kernel nodes of graphs with conditional nodes) and per-kernel timing. Results are identical. */
+typedef enum { MBPCG_LAUNCH_GRAPH = 0, MBPCG_LAUNCH_EAGER = 1 } mbpcg_launch_mode;
+int mbpcg_set_launch_mode(mbpcg_handle h, int32_t mode);
 
 /* Release a handle (NULL is ignored). */
 void mbpcg_destroy(mbpcg_handle h);

@@ -13,9 +13,9 @@ from . import _native
 from ._native import (  # noqa: F401  (re-exported C ABI names)
     Info, MBPCGError, lib, lib_path, mbpcg_create_csr, mbpcg_create_dense, mbpcg_destroy, mbpcg_k_cholesky,
     mbpcg_k_dense_gram, mbpcg_k_dense_product, mbpcg_k_spmm, mbpcg_k_spmm_gram_noalloc, mbpcg_k_padded_width, mbpcg_k_scratch_bytes, mbpcg_k_spmm_gram, mbpcg_run_iterations_dev,
-    mbpcg_solve, mbpcg_solve_dev, mbpcg_workspace_size_csr, mbpcg_workspace_size_dense, status_string, last_error,
+    mbpcg_set_launch_mode, mbpcg_solve, mbpcg_solve_dev, mbpcg_workspace_size_csr, mbpcg_workspace_size_dense, status_string, last_error,
     MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,
-    MBPCG_ALGO_CG, MBPCG_FP64)
+    MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER)
 
 __all__ = ["Solver", "Info", "MBPCGError", "lib", "lib_path"]
 
@@ -28,7 +28,8 @@ class Solver:
     The workspace is a torch uint8 CUDA tensor; calls run on a dedicated torch stream that first
     waits for the caller's current stream."""
 
-    def __init__(self, A, s: int = 4, precond: int = 0, algo: int = 0, seed: int = 0):
+    def __init__(self, A, s: int = 4, precond: int = 0, algo: int = 0, seed: int = 0,
+                 launch_mode: int = MBPCG_LAUNCH_GRAPH):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("MBPCG needs a CUDA device (GB300, sm_103a); no CPU path exists")
@@ -53,6 +54,10 @@ class Solver:
             v = np.ascontiguousarray(A.val, dtype=np.float64)
             self.h = mbpcg_create_csr(self.n, int(rp[-1]), rp, ci, v, self.s, precond, algo, 0, seed, 0,
                                       self.workspace, nbytes, self.stream.cuda_stream)
+        if launch_mode != MBPCG_LAUNCH_GRAPH:
+            st = mbpcg_set_launch_mode(self.h, launch_mode)
+            if st != MBPCG_OK:
+                raise MBPCGError(st, "mbpcg_set_launch_mode")
 
     def solve(self, b, U=None, tol: float = 1e-8, maxit: int = 100000):
         """Solve A x = b. b (and U, n x s column-major) are numpy arrays (host path, mbpcg_solve)

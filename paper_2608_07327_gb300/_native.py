@@ -22,6 +22,8 @@ MBPCG_PRECOND_JACOBI = 1
 MBPCG_ALGO_MBPCG = 0
 MBPCG_ALGO_CG = 1
 MBPCG_FP64 = 0
+MBPCG_LAUNCH_GRAPH = 0
+MBPCG_LAUNCH_EAGER = 1
 
 
 class Info(ctypes.Structure):
@@ -66,6 +68,7 @@ _SIGS = {
     "mbpcg_solve_dev": (ctypes.c_int, [_P, _P, _P, _D, _I32, _P, ctypes.POINTER(Info)]),
     "mbpcg_run_iterations_dev": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P]),
     "mbpcg_destroy": (None, [_P]),
+    "mbpcg_set_launch_mode": (ctypes.c_int, [_P, _I32]),
     "mbpcg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mbpcg_last_error": (ctypes.c_char_p, []),
     "mbpcg_k_padded_width": (_I32, [_I32]),
@@ -165,6 +168,10 @@ def mbpcg_solve_dev(h, b, U, tol, maxit, x_out):
 def mbpcg_run_iterations_dev(h, b, U, iters, X0=None, Xt=None, R=None, W=None, P=None, Sigma=None):
     return lib().mbpcg_run_iterations_dev(h, ptr(b), ptr(U), iters, ptr(X0), ptr(Xt), ptr(R), ptr(W), ptr(P),
                                           ptr(Sigma))
+
+
+def mbpcg_set_launch_mode(h, mode):
+    return lib().mbpcg_set_launch_mode(h, mode)
 
 
 def mbpcg_destroy(h):

@@ -154,6 +154,8 @@ struct mbpcg_ctx {
   cudaGraphExec_t exec;
   cudaGraphConditionalHandle cond;
   int graph_ready;
+  int launch_mode;  // MBPCG_LAUNCH_GRAPH or MBPCG_LAUNCH_EAGER
+  int use_cond;     // 1 while the loop body is captured into the WHILE node
   cudaEvent_t e0, e1;
 };
 
@@ -320,7 +322,7 @@ int finish_create(mbpcg_ctx* h) {
 void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y, int gram, const SolveState* st) {
   const Dims& dm = h->dm;
   if (dm.dense) {
-    ops->dense(h->stream, dm.nb_dense, dm.n, h->A, X, Y, st);
+    ops->dense(h->stream, dm.nb_dense, dm.n, h->A, X, Y, st, &h->st->kerr);
     if (gram) ops->gram(h->stream, dm.nb, dm.n, X, Y, h->part, dm.pstride, st);
   } else {
     ops->spmm(h->stream, dm.nb, dm.n, h->rp, h->ci, h->av, X, Y, h->part, dm.pstride, st, gram);
@@ -367,7 +369,8 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
   ops->axpy(h->stream, dm.nb, n, h->P, h->Q, h->W, h->R, h->Xt, h->V, h->T, h->Xi, h->wdiag, h->part, dm.pstride,
             h->st);
   enqueue_reduce(h, npack(kp) + kp, h->st);
-  k_small_zeta<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->Sigma, h->Zeta, h->ZetaInv, h->cond);
+  k_small_zeta<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->Sigma, h->Zeta, h->ZetaInv, h->cond,
+                                                    h->use_cond);
   ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0);
 }
 
@@ -395,7 +398,7 @@ void enqueue_cg_body(mbpcg_ctx* h) {
   enqueue_product(h, ops, h->r, h->w, 0, h->st);  // w = A u, u = r
   k_cg_dots<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->r, h->w, h->wdiag, h->part, dm.pstride, h->st);
   enqueue_reduce(h, 3, h->st);
-  k_small_cg<<<1, 1, 0, h->stream>>>(h->st, h->red, h->cond);
+  k_small_cg<<<1, 1, 0, h->stream>>>(h->st, h->red, h->cond, h->use_cond);
   k_cg_update<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->r, h->w, h->xb, h->p, h->sv, h->st);
 }
 
@@ -444,8 +447,10 @@ int build_graph(mbpcg_ctx* h) {
     if (e == cudaSuccess) {
       e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
+        h->use_cond = 1;
         if (cg) enqueue_cg_body(h);
         else enqueue_mbpcg_body(h);
+        h->use_cond = 0;
         cudaGraph_t b2 = nullptr;
         e = cudaStreamEndCapture(h->stream, &b2);
       }
@@ -461,6 +466,31 @@ int build_graph(mbpcg_ctx* h) {
   return MBPCG_OK;
 }
 
+// One inner solve with ordinary launches (no graph): set-up, the loop body until the state says
+// done (checked every 16 iterations), exit. Same kernels as the graph; used for profiling, since
+// profilers do not see kernel nodes inside graphs that have conditional nodes.
+int run_eager(mbpcg_ctx* h, int maxit_inner) {
+  const bool cg = h->algo == MBPCG_ALGO_CG;
+  h->use_cond = 0;
+  if (cg) enqueue_cg_setup(h);
+  else enqueue_mbpcg_setup(h);
+  CUDA_TRY(cudaGetLastError());
+  for (int i = 0; i < maxit_inner + 1; ++i) {
+    if (cg) enqueue_cg_body(h);
+    else enqueue_mbpcg_body(h);
+    CUDA_TRY(cudaGetLastError());
+    if ((i & 15) == 15 || i == maxit_inner) {
+      CUDA_TRY(cudaMemcpyAsync(h->st_host, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
+      if (h->st_host->done) break;
+    }
+  }
+  if (cg) enqueue_cg_exit(h);
+  else enqueue_mbpcg_exit(h);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
 // Copies b and U in (host or device memory), runs the inner solves with true-residual restarts,
 // and copies x out. mem: 0 host, 1 device for b, U and x.
 int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int maxit, double* x_out,
@@ -473,7 +503,7 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
   const size_t nb = (size_t)n * sizeof(double);
   const cudaMemcpyKind in_kind = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind out_kind = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (!h->graph_ready) {
+  if (!h->graph_ready && h->launch_mode == MBPCG_LAUNCH_GRAPH) {
     int rc = build_graph(h);
     if (rc) return rc;
   }
@@ -499,10 +529,16 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
     const int maxit_inner = no_test ? maxit : (maxit - total);
     k_params<<<1, 1, 0, h->stream>>>(h->st, tol_rel, maxit_inner, no_test, restarts, h->s);
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaGraphLaunch(h->exec, h->stream));
+    if (h->launch_mode == MBPCG_LAUNCH_EAGER) {
+      int rc = run_eager(h, maxit_inner);
+      if (rc) return rc;
+    } else {
+      CUDA_TRY(cudaGraphLaunch(h->exec, h->stream));
+    }
     CUDA_TRY(cudaMemcpyAsync(h->st_host, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     std::memcpy(&s, h->st_host, sizeof(s));
+    if (s.kerr) return set_err(MBPCG_ERR_TIMEOUT, "a bounded device-side wait timed out");
     total += s.it;
     if (no_test) {
       status = s.status;
@@ -664,6 +700,13 @@ int mbpcg_run_iterations_dev(mbpcg_handle h, const double* b, const double* U, i
   return rc;
 }
 
+int mbpcg_set_launch_mode(mbpcg_handle h, int32_t mode) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (mode != MBPCG_LAUNCH_GRAPH && mode != MBPCG_LAUNCH_EAGER) return set_err(MBPCG_ERR_INVALID, "unknown mode");
+  h->launch_mode = mode;
+  return MBPCG_OK;
+}
+
 void mbpcg_destroy(mbpcg_handle h) { release(h); }
 
 const char* mbpcg_status_string(int status) {
@@ -703,7 +746,7 @@ static int k_product_gram(int dense, int32_t n, const int32_t* rp, const int32_t
   double* part = static_cast<double*>(scratch);
   double* red = part + (size_t)dm.nbmax * dm.pstride;
   if (dense) {
-    ops->dense(st, dm.nb_dense, n, A, P, AP, nullptr);
+    ops->dense(st, dm.nb_dense, n, A, P, AP, nullptr, nullptr);
     ops->gram(st, dm.nb, n, P, AP, part, dm.pstride, nullptr);
   } else {
     ops->spmm(st, dm.nb, n, rp, ci, av, P, AP, part, dm.pstride, nullptr, 1);
@@ -738,7 +781,7 @@ int mbpcg_k_spmm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, cons
 int mbpcg_k_dense_product(int32_t n, const double* A, int32_t s, const double* P, double* AP, void* stream) {
   if (n < 1 || s < 1 || s > 32 || !A || !P || !AP) return set_err(MBPCG_ERR_INVALID, "bad arguments");
   const Dims dm = make_dims(n, (long long)n * n, s, MBPCG_ALGO_MBPCG, 1, num_sms());
-  row_ops(dm.kp)->dense((cudaStream_t)stream, dm.nb_dense, n, A, P, AP, nullptr);
+  row_ops(dm.kp)->dense((cudaStream_t)stream, dm.nb_dense, n, A, P, AP, nullptr, nullptr);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

@@ -11,7 +11,8 @@ struct RowOps {
   int kp;
   void (*spmm)(cudaStream_t, int nb, int n, const int* rp, const int* ci, const double* av, const double* P,
                double* Q, double* part, int pstride, const SolveState* st, int gram);
-  void (*dense)(cudaStream_t, int nb, int n, const double* A, const double* P, double* Q, const SolveState* st);
+  void (*dense)(cudaStream_t, int nb, int n, const double* A, const double* P, double* Q, const SolveState* st,
+                int* err);
   void (*gram)(cudaStream_t, int nb, int n, const double* X, const double* Y, double* part, int pstride,
                const SolveState* st);
   void (*axpy)(cudaStream_t, int nb, int n, const double* P, const double* Q, const double* W, double* R,
@@ -63,11 +64,11 @@ __global__ void k_small_setup(SolveState* st, const double* red);
 __global__ void k_small_sigma(SolveState* st, const double* Gp, int kp, double* Sigma, double* SigmaInv);
 __global__ void k_small_xi(SolveState* st, const double* G1p, int kp, const double* Sigma, double* Xi, double* T);
 __global__ void k_small_zeta(SolveState* st, const double* G2nu, int kp, double* Sigma, double* Zeta,
-                             double* ZetaInv, cudaGraphConditionalHandle cond);
+                             double* ZetaInv, cudaGraphConditionalHandle cond, int use_cond);
 __global__ void k_small_ls(SolveState* st, const double* Mg, int kp, double* c_out);
 __global__ void k_small_true(SolveState* st, const double* rr);
 __global__ void k_small_cg_setup(SolveState* st, const double* red);
-__global__ void k_small_cg(SolveState* st, const double* red, cudaGraphConditionalHandle cond);
+__global__ void k_small_cg(SolveState* st, const double* red, cudaGraphConditionalHandle cond, int use_cond);
 __global__ void k_validate_csr(int n, long long nnz, const int* rp, const int* ci, int* flag);
 __global__ void k_diag_csr(int n, const int* rp, const int* ci, const double* av, double* diag, int* flag);
 __global__ void k_diag_dense(int n, const double* A, double* diag, int* flag);

@@ -36,7 +36,7 @@ struct SolveState {
   int32_t no_test;     // diagnostic mode: run exactly maxit iterations
   int32_t s;           // number of copies
   int32_t restart;     // index of the current inner solve (0 = the user's right-hand side)
-  int32_t pad1;
+  int32_t kerr;        // 1: a kernel's bounded wait timed out (the solve returns MBPCG_ERR_TIMEOUT)
   double tol_rel;      // tolerance of the current inner solve, relative to ||rhs||
   double tol_abs;      // tol_rel * ||rhs||
   double rhs_norm;     // ||rhs|| of the current inner solve (original metric)

@@ -7,6 +7,7 @@
 // after convergence.
 #pragma once
 #include "mbpcg_device.cuh"
+#include "tma.cuh"
 
 namespace mbpcg {
 
@@ -66,69 +67,151 @@ k_spmm(int n, const int* __restrict__ rp, const int* __restrict__ ci, const doub
 }
 
 // ------------------------------------------------------------------------------------------------
-// Q = A P for dense symmetric A stored column-major (row i of A is column i, contiguous). One CTA
-// per SM walks its rows in groups; warp w takes rows w, w+8, w+16, ... of a group (RW of them in
-// registers), its lanes split the reduction index l (LL lanes) and the KP columns. P is staged
-// through shared memory in chunks of LC rows, A streams from HBM/L2 with coalesced loads.
+// Q = A P for dense symmetric A stored column-major (row i of A is column i, contiguous).
+// One CTA per SM owns a balanced range of rows and walks it in passes of G rows. The reduction index
+// l is split into chunks of LC: for each chunk the A rows (G x LC) and the P rows (LC x KP) are
+// copied into shared memory by 1-D TMA bulk copies (cp.async.bulk) that complete on an mbarrier,
+// STAGES chunks in flight, so HBM latency is hidden behind the FP64 FMAs. Each thread owns a
+// TR x TC register tile of the output and a residue class of l (LS classes, summed at the end in a
+// fixed order). Rows of odd length (n odd) break the 16-byte rule of bulk copies; then the same
+// pipeline is filled with ordinary loads. Every mbarrier wait is bounded: on a timeout the CTA sets
+// *err (if given), waits (bounded) for the copies it still has in flight, and returns.
 template <int KP>
 struct DenseCfg {
-  static constexpr int LL = 32 / KP;
-  static constexpr int RW = 4;
-  static constexpr int WARPS = kThreads / 32;
-  static constexpr int GROUP = WARPS * RW;
-  static constexpr int LC = (4096 / KP) < 512 ? (4096 / KP) : 512;
+  static constexpr int G = 32;
+  static constexpr int LC = 128;
+  static constexpr int LDA = LC + 2;  // shared-memory row stride of the A tile (keeps 16-byte rows)
+  static constexpr int STAGES = 3;
+  static constexpr int TR = (KP <= 2) ? 1 : 2;
+  static constexpr int TC = (KP == 1) ? 1 : 2;
+  static constexpr int RT = G / TR;
+  static constexpr int CT = KP / TC;
+  static constexpr int LS = kThreads / (RT * CT);
+  static constexpr int A_ELEMS = G * LDA;
+  static constexpr int STAGE_ELEMS = A_ELEMS + LC * KP;
+  static constexpr int RED_ELEMS = (LS > 1) ? LS * G * KP : 1;
+  static constexpr size_t SMEM = (size_t)(STAGES * STAGE_ELEMS + RED_ELEMS) * sizeof(double) + STAGES * 8;
 };
 
 template <int KP>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
 k_dense(int n, const double* __restrict__ A, const double* __restrict__ P, double* __restrict__ Q,
-        const SolveState* __restrict__ st) {
+        const SolveState* __restrict__ st, int* __restrict__ err) {
   using D = DenseCfg<KP>;
   if (st != nullptr && st->done) return;
-  __shared__ __align__(16) double Ps[D::LC * KP];
+  extern __shared__ __align__(128) double dsm[];
+  double* red = dsm + D::STAGES * D::STAGE_ELEMS;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(red + D::RED_ELEMS);
+  __shared__ int abort_flag;
   int r0, r1;
   row_range(n, r0, r1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ll = lane / KP, j = lane % KP;
-  for (int base = r0; base < r1; base += D::GROUP) {
-    int nv = 0;  // rows of this warp in this group (warp-uniform)
-    const double* arow[D::RW];
-    int rows[D::RW];
-#pragma unroll
-    for (int w = 0; w < D::RW; ++w) {
-      const int i = base + warp + w * D::WARPS;
-      rows[w] = i;
-      if (i < r1) ++nv;
-      arow[w] = A + (size_t)(i < r1 ? i : r0) * n;
-    }
-    double acc[D::RW];
-#pragma unroll
-    for (int w = 0; w < D::RW; ++w) acc[w] = 0.0;
-    for (int l0 = 0; l0 < n; l0 += D::LC) {
-      const int lc = min(D::LC, n - l0);
-      __syncthreads();
-      for (int q = threadIdx.x; q < lc * KP; q += kThreads) Ps[q] = __ldg(P + (size_t)l0 * KP + q);
-      __syncthreads();
-      if (nv == D::RW) {
-        for (int l = ll; l < lc; l += D::LL) {
-          const double pj = Ps[l * KP + j];
-#pragma unroll
-          for (int w = 0; w < D::RW; ++w) acc[w] = fma(__ldg(arow[w] + l0 + l), pj, acc[w]);
+  const int tid = threadIdx.x;
+  const int q = tid % D::LS, tile = tid / D::LS, ct = tile % D::CT, rt = tile / D::CT;
+  const bool tma = (n % 2) == 0;
+  if (tid == 0) {
+    for (int s = 0; s < D::STAGES; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  const int nchunks = (n + D::LC - 1) / D::LC;
+  int g_next = 0;  // global index of the next chunk to consume (stage = g % STAGES)
+  for (int base = r0; base < r1; base += D::G) {
+    const int rows = min(D::G, r1 - base);
+    const int g0 = g_next;
+    auto issue = [&](int c) {
+      const int g = g0 + c, stage = g % D::STAGES, l0 = c * D::LC, lc = min(D::LC, n - l0);
+      double* As = dsm + stage * D::STAGE_ELEMS;
+      double* Ps = As + D::A_ELEMS;
+      if (tma) {
+        if (tid < 32) {
+          if (tid == 0) mbar_arrive_expect_tx(&bars[stage], (uint32_t)((rows + KP) * lc * sizeof(double)));
+          __syncwarp();
+          for (int r = tid; r < rows; r += 32)
+            tma_load_1d(As + r * D::LDA, A + (size_t)(base + r) * n + l0, (uint32_t)(lc * sizeof(double)),
+                        &bars[stage]);
+          if (tid == 0)
+            tma_load_1d(Ps, P + (size_t)l0 * KP, (uint32_t)(lc * KP * sizeof(double)), &bars[stage]);
         }
       } else {
-        for (int l = ll; l < lc; l += D::LL) {
-          const double pj = Ps[l * KP + j];
+        for (int e = tid; e < rows * lc; e += kThreads) {
+          const int r = e / lc, l = e - r * lc;
+          As[r * D::LDA + l] = A[(size_t)(base + r) * n + l0 + l];
+        }
+        for (int e = tid; e < lc * KP; e += kThreads) Ps[e] = P[(size_t)l0 * KP + e];
+      }
+    };
+    double acc[D::TR][D::TC];
 #pragma unroll
-          for (int w = 0; w < D::RW; ++w)
-            if (w < nv) acc[w] = fma(__ldg(arow[w] + l0 + l), pj, acc[w]);
+    for (int r = 0; r < D::TR; ++r)
+#pragma unroll
+      for (int c = 0; c < D::TC; ++c) acc[r][c] = 0.0;
+    const int pre = min(D::STAGES - 1, nchunks);
+    for (int c = 0; c < pre; ++c) issue(c);
+    int issued = pre;
+    __syncthreads();
+    for (int c = 0; c < nchunks; ++c) {
+      if (c + D::STAGES - 1 < nchunks) {
+        issue(c + D::STAGES - 1);
+        issued = c + D::STAGES;
+      }
+      const int g = g0 + c, stage = g % D::STAGES;
+      bool ok = true;
+      if (tma) ok = mbar_wait_bounded(&bars[stage], (uint32_t)((g / D::STAGES) & 1));
+      if (!ok) abort_flag = 1;
+      if (ok && rt * D::TR < rows) {
+        const double* As = dsm + stage * D::STAGE_ELEMS;
+        const double* Ps = As + D::A_ELEMS;
+        const int lc = min(D::LC, n - c * D::LC);
+        for (int l = q; l < lc; l += D::LS) {
+          double a[D::TR], p[D::TC];
+#pragma unroll
+          for (int r = 0; r < D::TR; ++r) a[r] = As[(rt * D::TR + r) * D::LDA + l];
+          if constexpr (D::TC == 2) {
+            const double2 t = *reinterpret_cast<const double2*>(Ps + l * KP + ct * 2);
+            p[0] = t.x;
+            p[1] = t.y;
+          } else {
+            p[0] = Ps[l * KP + ct];
+          }
+#pragma unroll
+          for (int r = 0; r < D::TR; ++r)
+#pragma unroll
+            for (int cc = 0; cc < D::TC; ++cc) acc[r][cc] = fma(a[r], p[cc], acc[r][cc]);
         }
       }
+      __syncthreads();
+      if (abort_flag) {
+        if (tid == 0) {
+          if (err != nullptr) atomicExch(err, 1);
+          for (int c2 = c; c2 < issued; ++c2) {  // drain the copies still in flight (bounded)
+            const int g2 = g0 + c2;
+            mbar_wait_bounded(&bars[g2 % D::STAGES], (uint32_t)((g2 / D::STAGES) & 1));
+          }
+        }
+        __syncthreads();
+        return;
+      }
     }
+    g_next = g0 + nchunks;
+    // sum the LS residue classes in a fixed order, then store the valid rows
+    if constexpr (D::LS > 1) {
 #pragma unroll
-    for (int w = 0; w < D::RW; ++w) {
-      double v = acc[w];
-      for (int off = KP; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (ll == 0 && w < nv) Q[(size_t)rows[w] * KP + j] = v;
+      for (int r = 0; r < D::TR; ++r)
+#pragma unroll
+        for (int cc = 0; cc < D::TC; ++cc) red[(q * D::G + rt * D::TR + r) * KP + ct * D::TC + cc] = acc[r][cc];
+      cta_tree_sum(red, D::LS, D::G * KP);
+      for (int e = tid; e < rows * KP; e += kThreads) Q[(size_t)base * KP + e] = red[e];
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int r = 0; r < D::TR; ++r) {
+        const int row = rt * D::TR + r;
+        if (row < rows) {
+#pragma unroll
+          for (int cc = 0; cc < D::TC; ++cc) Q[(size_t)(base + row) * KP + ct * D::TC + cc] = acc[r][cc];
+        }
+      }
     }
   }
 }

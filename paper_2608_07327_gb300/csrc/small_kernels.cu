@@ -23,6 +23,7 @@ __global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test,
   st->no_test = no_test;
   st->restart = restart;
   st->s = s;
+  st->kerr = 0;
 }
 
 // Set-up scalars: ||rhs||, X0 = (||B||_F / ||A U||_F) U with ||B||_F = sqrt(s) ||D^{-1} rhs||.
@@ -113,15 +114,15 @@ k_small_xi(SolveState* st, const double* __restrict__ G1p, int kp, const double*
 // Best-basis test and the Cholesky QR factor of V = W - A P Xi:
 //   h = argmin_j nu_j (lowest index on ties); stop when sqrt(nu_h) < tol ||rhs|| (Section 2,
 //   initial tolerance = convergence tolerance); else zeta = chol(V^T V), Sigma = zeta Sigma.
-// Sets the WHILE condition of the graph loop.
+// Sets the WHILE condition of the graph loop (use_cond = 0 when launched outside a graph).
 __global__ void __launch_bounds__(kSmallThreads)
 k_small_zeta(SolveState* st, const double* __restrict__ G2nu, int kp, double* __restrict__ Sigma,
-             double* __restrict__ Zeta, double* __restrict__ ZetaInv, cudaGraphConditionalHandle cond) {
+             double* __restrict__ Zeta, double* __restrict__ ZetaInv, cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double A[kMaxKP * kMaxKP], Zi[kMaxKP * kMaxKP], S[kMaxKP * kMaxKP], rd[kMaxKP];
   __shared__ int flag, stop;
   const int s = st->s;
   if (st->done) {
-    if (threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    if (threadIdx.x == 0) if (use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
   if (threadIdx.x == 0) {
@@ -143,7 +144,7 @@ k_small_zeta(SolveState* st, const double* __restrict__ G2nu, int kp, double* __
   }
   __syncthreads();
   if (stop) {
-    if (threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    if (threadIdx.x == 0) if (use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
   cta_unpack_sym(s, kp, G2nu, A);
@@ -152,7 +153,7 @@ k_small_zeta(SolveState* st, const double* __restrict__ G2nu, int kp, double* __
       st->done = 1;
       st->pw_skip = 1;
       st->status = 6;
-      cudaGraphSetConditional(cond, 0);
+      if (use_cond) cudaGraphSetConditional(cond, 0);
     }
     return;
   }
@@ -176,7 +177,7 @@ k_small_zeta(SolveState* st, const double* __restrict__ G2nu, int kp, double* __
       st->pw_skip = 0;  // the last iteration still completes its W, P update
       st->status = st->no_test ? 0 : 5;
     }
-    cudaGraphSetConditional(cond, done ? 0u : 1u);
+    if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
   }
 }
 
@@ -302,10 +303,11 @@ __global__ void k_small_cg_setup(SolveState* st, const double* __restrict__ red)
 
 // gamma = (r, u), delta = (w, u) with u = r and w = A u; test ||D r|| < tol ||rhs||; then
 // beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old) (first step:
-// beta = 0, alpha = gamma / delta). Sets the WHILE condition.
-__global__ void k_small_cg(SolveState* st, const double* __restrict__ red, cudaGraphConditionalHandle cond) {
+// beta = 0, alpha = gamma / delta). Sets the WHILE condition (use_cond = 0 outside a graph).
+__global__ void k_small_cg(SolveState* st, const double* __restrict__ red, cudaGraphConditionalHandle cond,
+                           int use_cond) {
   if (st->done) {
-    cudaGraphSetConditional(cond, 0);
+    if (use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
   const double gamma = red[0], delta = red[1], nu = sqrt(red[2]);
@@ -315,13 +317,13 @@ __global__ void k_small_cg(SolveState* st, const double* __restrict__ red, cudaG
     st->converged = 1;
     st->done = 1;
     st->status = 0;
-    cudaGraphSetConditional(cond, 0);
+    if (use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
   if (st->it >= st->maxit) {
     st->done = 1;
     st->status = 5;
-    cudaGraphSetConditional(cond, 0);
+    if (use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
   double alpha, beta;
@@ -335,7 +337,7 @@ __global__ void k_small_cg(SolveState* st, const double* __restrict__ red, cudaG
   if (!isfinite(alpha) || !(alpha > 0.0)) {
     st->done = 1;
     st->status = 6;
-    cudaGraphSetConditional(cond, 0);
+    if (use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
   st->cg_alpha = alpha;
@@ -343,7 +345,7 @@ __global__ void k_small_cg(SolveState* st, const double* __restrict__ red, cudaG
   st->cg_gamma_old = gamma;
   st->cg_alpha_old = alpha;
   st->it += 1;
-  cudaGraphSetConditional(cond, 1);
+  if (use_cond) cudaGraphSetConditional(cond, 1);
 }
 
 // ------------------------------------------------------------------ vector kernels
