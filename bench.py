@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--kernel-launches", type=int, default=20, help="launches of the dominant kernel timed alone")
     p.add_argument("--cpu-sample-iters", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "tc"],
+                   help="tc: dense product on the BF16 tensor cores by exact digit splitting (FP64 accuracy)")
     p.add_argument("--launch-mode", default="graph", choices=["graph", "eager"],
                    help="eager: host-launched loop (for profilers; same kernels and results)")
     return p.parse_args()
@@ -176,7 +178,8 @@ def run_ours(args, world, rank, local):
     U = wl.initial_block(n, s, 1)
     dev = torch.device("cuda", local)
     mode = mb.MBPCG_LAUNCH_EAGER if args.launch_mode == "eager" else mb.MBPCG_LAUNCH_GRAPH
-    solver = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode)
+    prec = mb.MBPCG_FP64_TC if (args.precision == "tc" and isinstance(A, wl.Dense)) else mb.MBPCG_FP64
+    solver = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode, precision=prec)
     cg = mb.Solver(A, algo=mb.MBPCG_ALGO_CG, precond=cfg["precond"], launch_mode=mode)
     stream = solver.stream
     bd = torch.as_tensor(b, device=dev)
@@ -231,7 +234,17 @@ def run_ours(args, world, rank, local):
     kp = mb.mbpcg_k_padded_width(s)
     P = torch.as_tensor(np.ascontiguousarray(np.pad(U, ((0, 0), (0, kp - s)))), device=dev)
     AP = torch.empty_like(P)
-    if dense:
+    tc = dense and prec == mb.MBPCG_FP64_TC
+    if tc:
+        Ad = torch.as_tensor(np.asfortranarray(A.a).ravel(order="F"), device=dev)
+        tcb = mb.mbpcg_k_dense_tc_scratch_bytes(n, s)
+        tcs = torch.empty(tcb, dtype=torch.uint8, device=dev)
+        mb.mbpcg_k_dense_tc_prepare(n, Ad, s, tcs, tcb, stream.cuda_stream)  # digits of A, once
+        launch = lambda: mb.mbpcg_k_dense_tc_product(n, s, P, AP, tcs, tcb, stream.cuda_stream)  # noqa: E731
+        kname = "k_dense_tc"
+        flops = 2.0 * n * n * s
+        nbytes = 16.0 * n * n + 16.0 * n * kp  # 8 bf16 digits of A per entry
+    elif dense:
         Ad = torch.as_tensor(np.asfortranarray(A.a).ravel(order="F"), device=dev)
         launch = lambda: mb.mbpcg_k_dense_product(n, Ad, s, P, AP, stream.cuda_stream)  # noqa: E731
         kname = "k_dense"
@@ -260,13 +273,24 @@ def run_ours(args, world, rank, local):
             k_ms.append(ev0.elapsed_time(ev1))
     k_avg = sum(k_ms) / len(k_ms)
     achieved_tflops = flops / (k_avg * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": f"{kname}<{kp}> (FP64 pipe)", "achieved": round(achieved_tflops, 4),
-                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
-                "traffic": recorded_traffic(kname, args.workload, s),
-                "kernel_ms": round(k_avg, 5), "algorithmic_flops": flops, "algorithmic_bytes": nbytes,
-                "hbm_gbs_equiv": round(nbytes / (k_avg * 1e-3) / 1e9, 1),
-                "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (probe measured 1.20 TFLOP/s)"}
+    if tc:
+        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        achieved_gbs = nbytes / (k_avg * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"{kname}<{kp}> (digits of P + tcgen05 MMAs + split sum)",
+                    "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(achieved_gbs / hbm_peak, 4), "traffic": recorded_traffic(kname, args.workload, s),
+                    "kernel_ms": round(k_avg, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
+                    "fp64_equiv_tflops": round(achieved_tflops, 3),
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+    else:
+        roofline = {"bound": "alu", "kernel": f"{kname}<{kp}> (FP64 pipe)", "achieved": round(achieved_tflops, 4),
+                    "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
+                    "traffic": recorded_traffic(kname, args.workload, s),
+                    "kernel_ms": round(k_avg, 5), "algorithmic_flops": flops, "algorithmic_bytes": nbytes,
+                    "hbm_gbs_equiv": round(nbytes / (k_avg * 1e-3) / 1e9, 1),
+                    "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (probe measured 1.20 TFLOP/s)"}
 
     # end to end through the public host-buffer API (pinned host memory in, x out)
     b_pin = torch.from_numpy(b).pin_memory()
@@ -289,7 +313,7 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["desc"], "n": n, "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
                        "tol": cfg["tol"], "l2": "flushed before every step (256 MB write)",
-                       "launch_mode": args.launch_mode,
+                       "launch_mode": args.launch_mode, "precision": args.precision,
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "iterations": info["iterations"], "restarts": info["restarts"], "relres_true": relres_check,
             "cg_ms": round(cg_ms, 4), "cg_iterations": cg_infos[-1]["iterations"],

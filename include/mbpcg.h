@@ -58,8 +58,11 @@ typedef enum { MBPCG_PRECOND_NONE = 0, MBPCG_PRECOND_JACOBI = 1 } mbpcg_precond;
  * paper's baseline, Section 4), s ignored. */
 typedef enum { MBPCG_ALGO_MBPCG = 0, MBPCG_ALGO_CG = 1 } mbpcg_algo;
 
-/* Arithmetic of the n-proportional work. FP64: everything in double precision. */
-typedef enum { MBPCG_FP64 = 0 } mbpcg_precision;
+/* Arithmetic of the n-proportional work. FP64: everything in double precision on the FP64 pipe.
+ * FP64_TC (dense A, MBPCG only): the same FP64 solve, but the product A P runs on the BF16 tensor
+ * cores by exact splitting of A and P into 8 base-128 digits (Ozaki scheme); its result has the
+ * accuracy of an FP64 product. The digits of A take 16 bytes per entry of workspace. */
+typedef enum { MBPCG_FP64 = 0, MBPCG_FP64_TC = 2 } mbpcg_precision;
 
 typedef struct {
   int32_t iterations;        /* inner iterations summed over restarts */

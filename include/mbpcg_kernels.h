@@ -63,6 +63,16 @@ int mbpcg_k_spmm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, cons
 int mbpcg_k_dense_product(int32_t n, const double* A, int32_t s, const double* P, double* AP,
                           void* stream);
 
+/* The tensor-core form of the dense product (precision MBPCG_FP64_TC), as accurate as an FP64
+ * product. mbpcg_k_dense_tc_prepare writes the BF16 digits of A into `scratch`
+ * (mbpcg_k_dense_tc_scratch_bytes(n, s) bytes of device memory, 256-byte aligned);
+ * mbpcg_k_dense_tc_product then splits P and computes AP = A P with tcgen05 MMAs, reusing them. */
+size_t mbpcg_k_dense_tc_scratch_bytes(int32_t n, int32_t s);
+int mbpcg_k_dense_tc_prepare(int32_t n, const double* A, int32_t s, void* scratch,
+                             size_t scratch_bytes, void* stream);
+int mbpcg_k_dense_tc_product(int32_t n, int32_t s, const double* P, double* AP, void* scratch,
+                             size_t scratch_bytes, void* stream);
+
 /* Z = upper Cholesky factor of the SPD s x s matrix G (G = Z^T Z, positive diagonal), the k x k
  * factorisation used for Xi (Section 3) and for the Cholesky QR. *status_dev (device int) is set
  * to 0, or to 6 (MBPCG_BREAKDOWN) when a pivot is not finite or not above 64 eps max_j G_jj. */

@@ -12,10 +12,10 @@ import numpy as np
 from . import _native
 from ._native import (  # noqa: F401  (re-exported C ABI names)
     Info, MBPCGError, lib, lib_path, mbpcg_create_csr, mbpcg_create_dense, mbpcg_destroy, mbpcg_k_cholesky,
-    mbpcg_k_dense_gram, mbpcg_k_dense_product, mbpcg_k_spmm, mbpcg_k_spmm_gram_noalloc, mbpcg_k_padded_width, mbpcg_k_scratch_bytes, mbpcg_k_spmm_gram, mbpcg_run_iterations_dev,
+    mbpcg_k_dense_gram, mbpcg_k_dense_product, mbpcg_k_dense_tc_prepare, mbpcg_k_dense_tc_product, mbpcg_k_dense_tc_scratch_bytes, mbpcg_k_spmm, mbpcg_k_spmm_gram_noalloc, mbpcg_k_padded_width, mbpcg_k_scratch_bytes, mbpcg_k_spmm_gram, mbpcg_run_iterations_dev,
     mbpcg_set_launch_mode, mbpcg_solve, mbpcg_solve_dev, mbpcg_workspace_size_csr, mbpcg_workspace_size_dense, status_string, last_error,
     MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,
-    MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER)
+    MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_FP64_TC, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER)
 
 __all__ = ["Solver", "Info", "MBPCGError", "lib", "lib_path"]
 
@@ -29,7 +29,7 @@ class Solver:
     waits for the caller's current stream."""
 
     def __init__(self, A, s: int = 4, precond: int = 0, algo: int = 0, seed: int = 0,
-                 launch_mode: int = MBPCG_LAUNCH_GRAPH):
+                 launch_mode: int = MBPCG_LAUNCH_GRAPH, precision: int = MBPCG_FP64):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("MBPCG needs a CUDA device (GB300, sm_103a); no CPU path exists")
@@ -40,13 +40,13 @@ class Solver:
         # a stream of our own, ordered after the caller's work before every call
         self.stream = torch.cuda.Stream()
         if self.dense:
-            nbytes = mbpcg_workspace_size_dense(self.n, self.s, algo)
+            nbytes = mbpcg_workspace_size_dense(self.n, self.s, algo, precision)
         else:
             nbytes = mbpcg_workspace_size_csr(self.n, int(A.row_ptr[-1]), self.s, algo)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         if self.dense:
             a = np.asfortranarray(A.a, dtype=np.float64)
-            self.h = mbpcg_create_dense(self.n, a, self.s, precond, algo, 0, seed, 0, self.workspace, nbytes,
+            self.h = mbpcg_create_dense(self.n, a, self.s, precond, algo, precision, seed, 0, self.workspace, nbytes,
                                         self.stream.cuda_stream)
         else:
             rp = np.ascontiguousarray(A.row_ptr, dtype=np.int32)

@@ -22,6 +22,7 @@ MBPCG_PRECOND_JACOBI = 1
 MBPCG_ALGO_MBPCG = 0
 MBPCG_ALGO_CG = 1
 MBPCG_FP64 = 0
+MBPCG_FP64_TC = 2
 MBPCG_LAUNCH_GRAPH = 0
 MBPCG_LAUNCH_EAGER = 1
 
@@ -76,6 +77,9 @@ _SIGS = {
     "mbpcg_k_spmm_gram": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_dense_gram": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_cholesky": (ctypes.c_int, [_I32, _P, _P, _P, _P]),
+    "mbpcg_k_dense_tc_scratch_bytes": (_SZ, [_I32, _I32]),
+    "mbpcg_k_dense_tc_prepare": (ctypes.c_int, [_I32, _P, _I32, _P, _SZ, _P]),
+    "mbpcg_k_dense_tc_product": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_spmm_gram_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "mbpcg_k_spmm": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
     "mbpcg_k_dense_product": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P]),
@@ -207,6 +211,18 @@ def mbpcg_k_spmm(n, row_ptr, col_idx, vals, s, P, AP, stream=None):
 
 def mbpcg_k_dense_product(n, A, s, P, AP, stream=None):
     return lib().mbpcg_k_dense_product(n, ptr(A), s, ptr(P), ptr(AP), stream)
+
+
+def mbpcg_k_dense_tc_scratch_bytes(n, s) -> int:
+    return int(lib().mbpcg_k_dense_tc_scratch_bytes(n, s))
+
+
+def mbpcg_k_dense_tc_prepare(n, A, s, scratch, scratch_bytes, stream=None):
+    return lib().mbpcg_k_dense_tc_prepare(n, ptr(A), s, ptr(scratch), scratch_bytes, stream)
+
+
+def mbpcg_k_dense_tc_product(n, s, P, AP, scratch, scratch_bytes, stream=None):
+    return lib().mbpcg_k_dense_tc_product(n, s, ptr(P), ptr(AP), ptr(scratch), scratch_bytes, stream)
 
 
 def mbpcg_k_cholesky(s, G, Z, status_dev, stream=None):

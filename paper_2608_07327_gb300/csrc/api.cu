@@ -45,7 +45,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Dims {
   int n, kp, nb, nb_dense, nbmax, pstride;
   long long nnz;
-  int dense, algo;
+  int dense, algo, tc, sms;
 };
 
 int num_sms() {
@@ -69,6 +69,8 @@ Dims make_dims(int n, long long nnz, int s, int algo, int dense, int sms) {
   d.nb_dense = (int)(wd < sm ? (wd > 0 ? wd : 1) : sm);
   d.nbmax = d.nb > d.nb_dense ? d.nb : d.nb_dense;
   d.pstride = (npack(d.kp) + d.kp + 1 + 3) / 4 * 4;
+  d.tc = 0;
+  d.sms = sm;
   return d;
 }
 
@@ -78,6 +80,7 @@ struct Layout {
   size_t U, X0, Xt, R, W, P, Q, V;    // MBPCG blocks, n x KP each
   size_t r, w, xb, p, sv;             // CG vectors
   size_t part, red, small, st, flag;  // reductions, k x k matrices, control block
+  size_t oz_a, oz_ea, oz_p, oz_ep, oz_q; // tensor-core product: digits of A and P, exponents, split sums
   size_t total;
 };
 
@@ -122,6 +125,13 @@ Layout make_layout(const Dims& dm) {
     L.p = take(n * sizeof(double));
     L.sv = take(n * sizeof(double));
   }
+  if (dm.tc) {
+    L.oz_a = take(oz_a_tiles_bytes(dm.n));
+    L.oz_ea = take(n * sizeof(int));
+    L.oz_p = take(oz_p_chunks_bytes(dm.n, dm.kp));
+    L.oz_ep = take(kMaxKP * sizeof(int));
+    L.oz_q = take((size_t)oz_ksplit(dm.n, dm.sms) * n * dm.kp * sizeof(double));
+  }
   L.part = take((size_t)dm.nbmax * dm.pstride * sizeof(double));
   L.red = take((size_t)dm.pstride * sizeof(double));
   L.small = take(8 * (size_t)kMaxKP * kMaxKP * sizeof(double));
@@ -151,6 +161,9 @@ struct mbpcg_ctx {
   double *Sigma, *SigmaInv, *Xi, *T, *Zeta, *ZetaInv, *c, *Gtmp;
   SolveState* st;
   SolveState* st_host;  // pinned
+  uint8_t *oz_a, *oz_p;
+  int *oz_ea, *oz_ep;
+  double* oz_q;
   cudaGraphExec_t exec;
   cudaGraphConditionalHandle cond;
   int graph_ready;
@@ -216,6 +229,13 @@ void bind(mbpcg_ctx* h) {
   h->Gtmp = sm + 7 * q;
   h->st = at<SolveState>(h, L.st);
   h->flag = at<int>(h, L.flag);
+  if (h->dm.tc) {
+    h->oz_a = at<uint8_t>(h, L.oz_a);
+    h->oz_ea = at<int>(h, L.oz_ea);
+    h->oz_p = at<uint8_t>(h, L.oz_p);
+    h->oz_ep = at<int>(h, L.oz_ep);
+    h->oz_q = at<double>(h, L.oz_q);
+  }
 }
 
 int check_common(int n, int s, int precond, int algo, int precision, int mem) {
@@ -224,7 +244,8 @@ int check_common(int n, int s, int precond, int algo, int precision, int mem) {
   if (algo == MBPCG_ALGO_MBPCG && (s < 1 || s > 32)) return set_err(MBPCG_ERR_INVALID, "s must be in [1, 32] (got %d)", s);
   if (precond != MBPCG_PRECOND_NONE && precond != MBPCG_PRECOND_JACOBI)
     return set_err(MBPCG_ERR_INVALID, "unknown precond %d", precond);
-  if (precision != MBPCG_FP64) return set_err(MBPCG_ERR_INVALID, "unsupported precision %d", precision);
+  if (precision != MBPCG_FP64 && precision != MBPCG_FP64_TC)
+    return set_err(MBPCG_ERR_INVALID, "unsupported precision %d", precision);
   if (mem != 0 && mem != 1) return set_err(MBPCG_ERR_INVALID, "mem must be 0 (host) or 1 (device)");
   return MBPCG_OK;
 }
@@ -313,6 +334,11 @@ int finish_create(mbpcg_ctx* h) {
     h->sqd = nullptr;
     h->wdiag = nullptr;
   }
+  if (h->dm.tc) {
+    oz_prepare_a(h->stream, n, h->A, h->oz_ea, h->oz_a);
+    CUDA_TRY(cudaMemsetAsync(h->oz_p, 0, oz_p_chunks_bytes(n, h->dm.kp), h->stream));
+    CUDA_TRY(cudaGetLastError());
+  }
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   return MBPCG_OK;
 }
@@ -321,7 +347,10 @@ int finish_create(mbpcg_ctx* h) {
 
 void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y, int gram, const SolveState* st) {
   const Dims& dm = h->dm;
-  if (dm.dense) {
+  if (dm.dense && dm.tc) {
+    oz_product(h->stream, dm.n, dm.kp, dm.sms, h->oz_a, h->oz_ea, X, h->oz_p, h->oz_ep, h->oz_q, Y, &h->st->kerr, st);
+    if (gram) ops->gram(h->stream, dm.nb, dm.n, X, Y, h->part, dm.pstride, st);
+  } else if (dm.dense) {
     ops->dense(h->stream, dm.nb_dense, dm.n, h->A, X, Y, st, &h->st->kerr);
     if (gram) ops->gram(h->stream, dm.nb, dm.n, X, Y, h->part, dm.pstride, st);
   } else {
@@ -592,9 +621,10 @@ size_t mbpcg_workspace_size_csr(int32_t n, int64_t nnz, int32_t s, int32_t algo,
 }
 
 size_t mbpcg_workspace_size_dense(int32_t n, int32_t s, int32_t algo, int32_t precision) {
-  (void)precision;
   if (n < 1) return 0;
-  return make_layout(make_dims(n, (long long)n * n, s, algo, 1, num_sms())).total;
+  Dims dm = make_dims(n, (long long)n * n, s, algo, 1, num_sms());
+  dm.tc = (precision == MBPCG_FP64_TC && algo == MBPCG_ALGO_MBPCG) ? 1 : 0;
+  return make_layout(dm).total;
 }
 
 int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
@@ -606,6 +636,7 @@ int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* r
   if (rc) return rc;
   if (nnz < 0 || nnz >= (1LL << 31)) return set_err(MBPCG_ERR_INVALID, "nnz must be in [0, 2^31)");
   if (!row_ptr || (nnz > 0 && (!col_idx || !vals))) return set_err(MBPCG_ERR_INVALID, "CSR arrays must not be NULL");
+  if (precision == MBPCG_FP64_TC) return set_err(MBPCG_ERR_INVALID, "the tensor-core product is for dense A");
   const int sms = num_sms();
   if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
   mbpcg_ctx* h = nullptr;
@@ -648,8 +679,9 @@ int mbpcg_create_dense(mbpcg_handle* out, int32_t n, const double* A_colmajor, i
   const int sms = num_sms();
   if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
   mbpcg_ctx* h = nullptr;
-  rc = alloc_handle(&h, make_dims(n, (long long)n * n, s, algo, 1, sms), s, precond, algo, precision, seed,
-                    workspace, workspace_bytes, stream);
+  Dims dm = make_dims(n, (long long)n * n, s, algo, 1, sms);
+  dm.tc = (precision == MBPCG_FP64_TC && algo == MBPCG_ALGO_MBPCG) ? 1 : 0;
+  rc = alloc_handle(&h, dm, s, precond, algo, precision, seed, workspace, workspace_bytes, stream);
   if (rc) {
     release(h);
     return rc;
@@ -782,6 +814,61 @@ int mbpcg_k_dense_product(int32_t n, const double* A, int32_t s, const double* P
   if (n < 1 || s < 1 || s > 32 || !A || !P || !AP) return set_err(MBPCG_ERR_INVALID, "bad arguments");
   const Dims dm = make_dims(n, (long long)n * n, s, MBPCG_ALGO_MBPCG, 1, num_sms());
   row_ops(dm.kp)->dense((cudaStream_t)stream, dm.nb_dense, n, A, P, AP, nullptr, nullptr);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+size_t mbpcg_k_dense_tc_scratch_bytes(int32_t n, int32_t s) {
+  if (n < 1 || s < 1 || s > 32) return 0;
+  const int kp = padded_width(s), sms = num_sms() > 0 ? num_sms() : 1;
+  return align_up(oz_a_tiles_bytes(n)) + align_up((size_t)n * sizeof(int)) + align_up(oz_p_chunks_bytes(n, kp)) +
+         align_up(kMaxKP * sizeof(int)) + align_up((size_t)oz_ksplit(n, sms) * n * kp * sizeof(double));
+}
+
+namespace {
+struct TcScratch {
+  uint8_t* at;
+  int* ea;
+  uint8_t* pc;
+  int* ep;
+  double* qp;
+};
+TcScratch tc_scratch(void* scratch, int n, int kp) {
+  TcScratch t;
+  uint8_t* p = static_cast<uint8_t*>(scratch);
+  t.at = p;
+  p += align_up(oz_a_tiles_bytes(n));
+  t.ea = reinterpret_cast<int*>(p);
+  p += align_up((size_t)n * sizeof(int));
+  t.pc = p;
+  p += align_up(oz_p_chunks_bytes(n, kp));
+  t.ep = reinterpret_cast<int*>(p);
+  p += align_up(kMaxKP * sizeof(int));
+  t.qp = reinterpret_cast<double*>(p);
+  return t;
+}
+}  // namespace
+
+int mbpcg_k_dense_tc_prepare(int32_t n, const double* A, int32_t s, void* scratch, size_t scratch_bytes,
+                             void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !A || !scratch) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if (scratch_bytes < mbpcg_k_dense_tc_scratch_bytes(n, s)) return set_err(MBPCG_ERR_INVALID, "scratch too small");
+  const int kp = padded_width(s);
+  cudaStream_t st = (cudaStream_t)stream;
+  const TcScratch t = tc_scratch(scratch, n, kp);
+  oz_prepare_a(st, n, A, t.ea, t.at);
+  CUDA_TRY(cudaMemsetAsync(t.pc, 0, oz_p_chunks_bytes(n, kp), st));
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+int mbpcg_k_dense_tc_product(int32_t n, int32_t s, const double* P, double* AP, void* scratch, size_t scratch_bytes,
+                             void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !P || !AP || !scratch) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if (scratch_bytes < mbpcg_k_dense_tc_scratch_bytes(n, s)) return set_err(MBPCG_ERR_INVALID, "scratch too small");
+  const int kp = padded_width(s);
+  const TcScratch t = tc_scratch(scratch, n, kp);
+  oz_product((cudaStream_t)stream, n, kp, num_sms(), t.at, t.ea, P, t.pc, t.ep, t.qp, AP, nullptr, nullptr);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

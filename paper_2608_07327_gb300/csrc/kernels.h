@@ -87,6 +87,14 @@ __global__ void k_cg_update(int n, double* r, const double* w, double* x, double
                             const SolveState* st);
 __global__ void k_cg_finish(int n, const double* xbar, const double* d, double* x);
 
+// FP64-accurate dense product on the BF16 tensor cores (ozaki_tc.cu)
+size_t oz_a_tiles_bytes(int n);
+size_t oz_p_chunks_bytes(int n, int kp);
+int oz_ksplit(int n, int sms);
+void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* Atiles);
+void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
+                uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st);
+
 // launch shape of the CSR product + Gram entry points, and the thread-local error message (api.cu)
 void product_gram_shape(int n, int s, int* kp, int* nb, int* pstride);
 int set_last_error(int code, const char* msg);

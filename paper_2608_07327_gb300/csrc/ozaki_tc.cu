@@ -1,0 +1,398 @@
+// FP64-accurate dense product Q = A P on the BF16 tensor cores (tcgen05), by exact splitting
+// (Ozaki et al., "Error-free transformations of matrix multiplication by using fast routines of
+// matrix multiplication and its applications", Numer. Algorithms 2012).
+//
+// Splitting. Each row i of A (A is symmetric, so row i = column i) is scaled by 2^-F_i, F_i the
+// largest binary exponent in the row, and the magnitude of every entry is written as 8 base-128
+// digits taken straight from its 53-bit significand (integer shifts, truncation below 2^-56 of the
+// row scale). Columns of P are split the same way with their own scales G_j. A digit is an integer
+// in [-127, 127], exact in BF16. Then
+//     (A P)_ij = 2^(F_i + G_j) * sum_{L=2..16} 2^(-7L) * S_L,   S_L = sum_{t+u=L} sum_l a^t_il b^u_lj
+// and the terms with t + u > 9 are below 2^-56 of the row/column scales and are dropped.
+//
+// Exactness. A product of two digits is < 2^14, so a level-L sum over a window of 128 values of l
+// is at most (L-1) * 127^2 * 128 < 2^24 for L <= 6: the FP32 accumulator of the tensor core holds
+// it exactly. Levels 2..6 are therefore drained from TMEM every 128 values of l and combined in
+// int64 (exact); levels 7..9 are carried in FP32 (their rounding is below 2^-58 of the scale).
+// The result has the accuracy of an FP64 product (error ~2^-53 |A||P|; an FP64 GEMM's bound is
+// n 2^-53 |A||P|).
+//
+// Data movement. Digits are stored in global memory already in the tensor-core operand layout
+// (K-major, no swizzle, 128 x 64 tiles of 16 KB for A, 8*KPT x 64 tiles for P), so whole tiles move
+// with 1-D TMA bulk copies into shared memory. One thread issues copies and MMAs (a software
+// pipeline over 7 A stages and 3 P buffers); the MMA for digit t of A uses all needed digits of P at
+// once (N = KPT * (9 - t)), writing levels t+1..9 of the accumulator. Every wait is bounded.
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace mbpcg {
+
+namespace {
+
+constexpr int kOzDigits = 8;
+constexpr int kOzMT = 128;                             // rows per M tile (= TMEM lanes)
+constexpr int kOzKC = 64;                              // reduction index per chunk
+constexpr int kOzWin = 2;                              // chunks per exact window (128 values of l)
+constexpr int kOzAStages = 7;
+constexpr int kOzPBufs = 3;
+constexpr uint32_t kATileBytes = kOzMT * kOzKC * 2;    // 16 KB
+constexpr int kOzThreads = 128;
+
+__device__ __forceinline__ int biased_exponent(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// The 8 signed base-128 digits of x relative to the scale 2^(emax - 1022).
+__device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDigits]) {
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  unsigned long long X = 0;
+  if (e != 0 && e != 0x7FF && emax != 0) {
+    const unsigned long long mant = ((unsigned long long)bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int shift = e - emax + 3;  // X = |x| 2^(1022 - emax) 2^56 < 2^56
+    X = shift >= 0 ? (mant << shift) : (shift > -60 ? (mant >> (-shift)) : 0ull);
+  }
+  const int sgn = bits < 0 ? -1 : 1;
+#pragma unroll
+  for (int t = 0; t < kOzDigits; ++t) d[t] = sgn * (int)((X >> (49 - 7 * t)) & 127ull);
+}
+
+// BF16 bit pattern of a small integer (exact: |v| <= 127 needs 7 significand bits).
+__device__ __forceinline__ uint16_t bf16_of_int(int v) { return (uint16_t)(__float_as_uint((float)v) >> 16); }
+
+}  // namespace
+
+// emax[i] = largest biased exponent of row i of the column-major symmetric A (= column i).
+__global__ void k_oz_rowexp(int n, const double* __restrict__ A, int* __restrict__ emax) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = A + (size_t)warp * n;
+  int m = 0;
+  for (int l = lane; l < n; l += 32) m = max(m, biased_exponent(row[l]));
+  for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if (lane == 0) emax[warp] = m;
+}
+
+// Digits of A into tiles [mtile][kchunk][digit] of 128 x 64 bf16 (canonical K-major layout).
+__global__ void k_oz_slice_a(int n, int nK, const double* __restrict__ A, const int* __restrict__ emax,
+                             uint16_t* __restrict__ tiles) {
+  const size_t total = (size_t)n * n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / n), l = (int)(q % n);
+    int d[kOzDigits];
+    ozaki_digits(A[q], emax[i], d);  // A[i*n + l] = row i (symmetric)
+    const size_t tile0 = ((size_t)(i / kOzMT) * nK + l / kOzKC) * kOzDigits;
+    const uint32_t off = umma_kmajor_offset(i % kOzMT, l % kOzKC, kOzKC) / 2;
+#pragma unroll
+    for (int t = 0; t < kOzDigits; ++t) tiles[(tile0 + t) * (kATileBytes / 2) + off] = bf16_of_int(d[t]);
+  }
+}
+
+// emaxP[j] = max over rows of the biased exponent of P[:, j] (atomicMax of integers: order-free).
+template <int KP>
+__global__ void k_oz_colexp(int n, const double* __restrict__ P, int* __restrict__ emaxP,
+                            const SolveState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  __shared__ int m[KP];
+  if (threadIdx.x < KP) m[threadIdx.x] = 0;
+  __syncthreads();
+  int loc[KP];
+#pragma unroll
+  for (int j = 0; j < KP; ++j) loc[j] = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < KP; ++j) loc[j] = max(loc[j], biased_exponent(P[(size_t)i * KP + j]));
+  }
+#pragma unroll
+  for (int j = 0; j < KP; ++j) {
+    int v = loc[j];
+    for (int off = 16; off; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&m[j], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < KP) atomicMax(&emaxP[threadIdx.x], m[threadIdx.x]);
+}
+
+// Digits of P into chunks [kchunk] of (8 * KPT) x 64 bf16, row index KPT * t + j (canonical
+// K-major layout, so digit t of every column j is one contiguous N-range).
+template <int KP, int KPT>
+__global__ void k_oz_slice_p(int n, const double* __restrict__ P, const int* __restrict__ emaxP,
+                             uint16_t* __restrict__ chunks, const SolveState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  constexpr uint32_t kChunkElems = kOzDigits * KPT * kOzKC;
+  const size_t total = (size_t)n * KP;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(q / KP), j = (int)(q % KP);
+    int d[kOzDigits];
+    ozaki_digits(P[q], emaxP[j], d);
+    uint16_t* ch = chunks + (size_t)(l / kOzKC) * kChunkElems;
+#pragma unroll
+    for (int t = 0; t < kOzDigits; ++t) ch[umma_kmajor_offset(KPT * t + j, l % kOzKC, kOzKC) / 2] = bf16_of_int(d[t]);
+  }
+}
+
+template <int KPT>
+struct OzCfg {
+  static constexpr uint32_t kPChunkBytes = kOzDigits * KPT * kOzKC * 2;
+  static constexpr uint32_t kTmemCols = (8 * KPT <= 128) ? 128 : 256;
+  static constexpr size_t kBarBytes = 1024;  // barriers + TMEM slot, keeps tiles 1024-aligned
+  static constexpr size_t kSmem = kBarBytes + (size_t)kOzAStages * kATileBytes + (size_t)kOzPBufs * kPChunkBytes;
+};
+
+// Qpart[ks][i][j] = the part of (A P)_ij over the K range of split ks, for j < KP.
+template <int KPT>
+__global__ void __launch_bounds__(kOzThreads, 1)
+k_dense_tc(int n, int KP, int nK, const uint8_t* __restrict__ Atiles, const int* __restrict__ emaxA,
+           const uint8_t* __restrict__ Pchunks, const int* __restrict__ emaxP, double* __restrict__ Qpart,
+           int* __restrict__ err, const SolveState* __restrict__ st) {
+  using C = OzCfg<KPT>;
+  if (st != nullptr && st->done) return;
+  extern __shared__ __align__(1024) uint8_t osm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(osm);
+  uint64_t* empty = full + kOzAStages;
+  uint64_t* pfull = empty + kOzAStages;
+  uint64_t* pempty = pfull + kOzPBufs;
+  uint64_t* wdone = pempty + kOzPBufs;
+  uint64_t* fin = wdone + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  uint8_t* As = osm + C::kBarBytes;
+  uint8_t* Ps = As + (size_t)kOzAStages * kATileBytes;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x, KS = gridDim.y, ks = blockIdx.y;
+  const int c0 = (int)((long long)nK * ks / KS), c1 = (int)((long long)nK * (ks + 1) / KS);
+  const int nch = c1 - c0, T = nch * kOzDigits;
+  const int nwin = (nch + kOzWin - 1) / kOzWin;
+
+  if (tid == 0) {
+    for (int s = 0; s < kOzAStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < kOzPBufs; ++b) {
+      mbar_init(&pfull[b], 1);
+      mbar_init(&pempty[b], 1);
+    }
+    mbar_init(wdone, 1);
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, C::kTmemCols);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  auto a_src = [&](int j) {
+    return Atiles + (((size_t)mt * nK + (c0 + j / kOzDigits)) * kOzDigits + (j % kOzDigits)) * kATileBytes;
+  };
+  auto issue_a = [&](int j) {
+    const int s = j % kOzAStages;
+    mbar_arrive_expect_tx(&full[s], kATileBytes);
+    tma_load_1d(As + (size_t)s * kATileBytes, a_src(j), kATileBytes, &full[s]);
+  };
+  auto issue_p = [&](int cc) {
+    const int b = cc % kOzPBufs;
+    mbar_arrive_expect_tx(&pfull[b], C::kPChunkBytes);
+    tma_load_1d(Ps + (size_t)b * C::kPChunkBytes, Pchunks + (size_t)(c0 + cc) * C::kPChunkBytes, C::kPChunkBytes,
+                &pfull[b]);
+  };
+
+  int issued_a = 0, issued_p = 0, next_j = 0;
+  if (tid == 0) {
+    for (; issued_p < nch && issued_p < 2; ++issued_p) issue_p(issued_p);
+    for (; issued_a < T && issued_a < kOzAStages; ++issued_a) issue_a(issued_a);
+  }
+
+  long long acc_i[KPT];
+  float acc_f[KPT];
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) {
+    acc_i[j] = 0;
+    acc_f[j] = 0.f;
+  }
+
+  for (int w = 0; w < nwin; ++w) {
+    if (tid == 0 && !*abort_flag) {
+      const int cc_end = min(nch, (w + 1) * kOzWin);
+      bool ok = true;
+      for (int cc = w * kOzWin; cc < cc_end && ok; ++cc) {
+        const int b = cc % kOzPBufs;
+        ok = mbar_wait_bounded(&pfull[b], (uint32_t)((cc / kOzPBufs) & 1));
+        for (int t = 0; t < kOzDigits && ok; ++t) {
+          const int j = next_j++;
+          const int s = j % kOzAStages;
+          ok = mbar_wait_bounded(&full[s], (uint32_t)((j / kOzAStages) & 1));
+          if (!ok) break;
+          const uint32_t a_base = smem_addr(As + (size_t)s * kATileBytes);
+          const uint32_t b_base = smem_addr(Ps + (size_t)b * C::kPChunkBytes);
+          const uint32_t idesc = umma_idesc_bf16_f32(kOzMT, KPT * (kOzDigits - t));
+          const uint32_t d = tmem + (uint32_t)(KPT * t);
+#pragma unroll
+          for (int k4 = 0; k4 < kOzKC / 16; ++k4) {
+            const uint32_t first = (cc == w * kOzWin && t == 0 && k4 == 0) ? 0u : 1u;
+            umma_bf16(d, umma_smem_desc(a_base + 256u * k4, 128, 1024), umma_smem_desc(b_base + 256u * k4, 128, 1024),
+                      idesc, first);
+          }
+          umma_commit(&empty[s]);
+          if (t == kOzDigits - 1) umma_commit(&pempty[b]);
+          // refill the stage of the previous tile (its MMAs are ahead of the ones just issued)
+          if (j >= 1 && issued_a < T) {
+            const int jp = j - 1;
+            ok = mbar_wait_bounded(&empty[jp % kOzAStages], (uint32_t)((jp / kOzAStages) & 1));
+            if (ok) issue_a(issued_a++);
+          }
+          // after the first tile of chunk cc, load chunk cc+1 (issued_p == cc+1) into the buffer of
+          // chunk cc-2, whose MMAs were issued two chunks ago
+          if (t == 0 && cc >= 1 && issued_p < nch && ok) {
+            if (cc >= 2) {
+              const int cp = cc - 2;
+              ok = mbar_wait_bounded(&pempty[cp % kOzPBufs], (uint32_t)((cp / kOzPBufs) & 1));
+            }
+            if (ok) issue_p(issued_p++);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (err != nullptr) atomicExch(err, 1);
+      }
+      umma_commit(wdone);
+    }
+    __syncwarp();
+    const bool wok = mbar_wait_bounded(wdone, (uint32_t)(w & 1));
+    if (!wok) *abort_flag = 1;
+    tc_fence_after_sync();
+    // drain levels 2..9 of this thread's row (TMEM lane 32*warp + lane)
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+    for (int L = 0; L < kOzDigits; ++L) {
+      float v[KPT];
+      if constexpr (KPT == 32) {
+        uint32_t r[32];
+        tmem_ld32(lane_base + (uint32_t)(KPT * L), r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+      } else {
+        uint32_t r[16];
+        tmem_ld16(lane_base + (uint32_t)(KPT * L), r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+      }
+      if (L < 5) {
+        const int sh = 7 * (4 - L);
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) acc_i[j] += (long long)__float2int_rn(v[j]) << sh;
+      } else {
+        const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : 0x1p-14f;
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) acc_f[j] = fmaf(v[j], sc, acc_f[j]);
+      }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    if (*abort_flag) break;
+  }
+
+  if (*abort_flag) {
+    if (tid == 0) {  // let the copies and MMAs still in flight land before the memory is released
+      for (int j = next_j; j < issued_a; ++j) mbar_wait_bounded(&full[j % kOzAStages], (uint32_t)((j / kOzAStages) & 1));
+      for (int cc = 0; cc < issued_p; ++cc) mbar_wait_bounded(&pfull[cc % kOzPBufs], (uint32_t)((cc / kOzPBufs) & 1));
+      umma_commit(fin);
+      mbar_wait_bounded(fin, 0);
+    }
+  } else {
+    const int row = mt * kOzMT + 32 * warp + lane;
+    if (row < n) {
+      const int fa = emaxA[row] - 1022;
+      double* out = Qpart + ((size_t)ks * n + row) * KP;
+#pragma unroll
+      for (int j = 0; j < KPT; ++j) {
+        if (j < KP) {
+          const double v = (double)acc_i[j] * 0x1p-42 + (double)acc_f[j] * 0x1p-49;
+          out[j] = ldexp(v, fa + emaxP[j] - 1022);
+        }
+      }
+    }
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  if (warp == 0) tmem_dealloc(tmem, C::kTmemCols);
+}
+
+// Q[i][j] = sum over splits of Qpart[ks][i][j], in split order.
+template <int KP>
+__global__ void k_oz_sum(int n, int KS, const double* __restrict__ Qpart, double* __restrict__ Q,
+                         const SolveState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const size_t total = (size_t)n * KP;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    double a = Qpart[q];
+    for (int k = 1; k < KS; ++k) a += Qpart[(size_t)k * total + q];
+    Q[q] = a;
+  }
+}
+
+// ------------------------------------------------------------------------------------ launchers
+
+size_t oz_a_tiles_bytes(int n) {
+  const size_t nM = (n + kOzMT - 1) / kOzMT, nK = (n + kOzKC - 1) / kOzKC;
+  return nM * nK * kOzDigits * kATileBytes;
+}
+size_t oz_p_chunks_bytes(int n, int kp) {
+  const int kpt = kp < 16 ? 16 : kp;
+  const size_t nK = (n + kOzKC - 1) / kOzKC;
+  return nK * (size_t)kOzDigits * kpt * kOzKC * 2;
+}
+int oz_ksplit(int n, int sms) {
+  const int nM = (n + kOzMT - 1) / kOzMT, nK = (n + kOzKC - 1) / kOzKC;
+  int ks = sms / nM;
+  if (ks < 1) ks = 1;
+  if (ks > nK) ks = nK;
+  return ks;
+}
+
+void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* Atiles) {
+  cudaMemsetAsync(Atiles, 0, oz_a_tiles_bytes(n), s);
+  k_oz_rowexp<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, A, emaxA);
+  const int nK = (n + kOzKC - 1) / kOzKC;
+  k_oz_slice_a<<<4096, 256, 0, s>>>(n, nK, A, emaxA, reinterpret_cast<uint16_t*>(Atiles));
+}
+
+template <int KP, int KPT>
+static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
+                          uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st) {
+  using C = OzCfg<KPT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dense_tc<KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
+    attr = true;
+  }
+  const int nM = (n + kOzMT - 1) / kOzMT, nK = (n + kOzKC - 1) / kOzKC, KS = oz_ksplit(n, sms);
+  cudaMemsetAsync(emaxP, 0, sizeof(int) * KP, s);
+  k_oz_colexp<KP><<<sms, 256, 0, s>>>(n, P, emaxP, st);
+  const int g = (int)(((size_t)n * KP + 255) / 256);
+  k_oz_slice_p<KP, KPT><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
+  k_dense_tc<KPT><<<dim3(nM, KS), kOzThreads, C::kSmem, s>>>(n, KP, nK, Atiles, emaxA, Pchunks, emaxP, Qpart, err, st);
+  k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, KS, Qpart, Q, st);
+}
+
+void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
+                uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st) {
+  switch (kp) {
+    case 1: oz_product_kp<1, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
+    case 2: oz_product_kp<2, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
+    case 4: oz_product_kp<4, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
+    case 8: oz_product_kp<8, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
+    case 16: oz_product_kp<16, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
+    default: oz_product_kp<32, 32>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
+  }
+}
+
+}  // namespace mbpcg

@@ -137,3 +137,27 @@ def test_cholesky_kernel_breakdown(mb):
     assert mb.mbpcg_k_cholesky(s, Gd, Z, status, None) == 0
     torch.cuda.synchronize()
     assert int(status.item()) == 6
+
+
+@pytest.mark.parametrize("s", [1, 4, 9, 16, 32])
+@pytest.mark.parametrize("n", [64, 300, 1031])
+def test_dense_tc_product_matches_oracle(mb, orc, n, s):
+    """The tensor-core (exact digit splitting) product against the FP64 oracle: the error must be at
+    the FP64 rounding level of |A||P| entry by entry (an FP64 GEMM's own bound is n eps |A||P|)."""
+    D = wl.dense_spd(n, 5, 0.0, 6.0)
+    P, kp = padded_block(n, s, 6)
+    P[:, :s] *= 10.0 ** (3 * wl.uniform_pm1(9, 77, s))[None, :]  # columns of very different scales
+    dev = torch.device("cuda")
+    Ad = torch.as_tensor(np.asfortranarray(D.a).ravel(order="F"), device=dev)
+    Pd = torch.as_tensor(np.ascontiguousarray(P), device=dev)
+    AP = torch.full_like(Pd, float("nan"))
+    nbytes = mb.mbpcg_k_dense_tc_scratch_bytes(n, s)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    assert mb.mbpcg_k_dense_tc_prepare(n, Ad, s, scratch, nbytes, None) == 0, mb.last_error()
+    assert mb.mbpcg_k_dense_tc_product(n, s, Pd, AP, scratch, nbytes, None) == 0, mb.last_error()
+    torch.cuda.synchronize()
+    got = AP.cpu().numpy()
+    ref = orc.matmat(D, P)
+    scale = np.abs(np.asarray(D.a)) @ np.abs(P)
+    assert np.all(np.isfinite(got[:, :s]))
+    assert np.all(np.abs(got[:, :s] - ref[:, :s]) <= 1e-14 * scale[:, :s] + 1e-300)

@@ -92,6 +92,47 @@ def test_mbpcg_matches_oracle(mb, orc, name, factory, s, precond, tol):
         assert err <= 2 * kappa_scaled(A, precond) * tol, (err, info, io)
 
 
+TC_CASES = [
+    ("dense200_s8_tc", lambda: wl.dense_spd(200, 0), 8, 0),
+    ("dense257_s3_jacobi_tc", lambda: wl.dense_spd(257, 1, 0.0, 3.0), 3, 1),
+    # (at s = 16 this M^T M system exhausts its block Krylov space: the oracle itself fails in 4 of 12
+    # rounding-level perturbations of b, so that case is not a parity case; s = 8 is stable)
+    ("dense_mtm150_s8_tc", lambda: wl.dense_mtm(150, 0), 8, 0),
+    ("dense300_s32_tc", lambda: wl.dense_spd(300, 2, 0.0, 4.0), 32, 0),
+]
+
+
+@pytest.mark.parametrize("name,factory,s,precond", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_mbpcg_tensor_core_product_matches_oracle(mb, orc, name, factory, s, precond):
+    """MBPCG with the dense product on the tensor cores (precision MBPCG_FP64_TC) against the FP64
+    oracle, under the same bars as the FP64 path."""
+    A = factory()
+    n = A.n
+    b = wl.rhs(n, 0)
+    U = wl.initial_block(n, s, 1)
+    solver = mb.Solver(A, s=s, precond=precond, precision=mb.MBPCG_FP64_TC)
+    try:
+        x, info = solver.solve(b, U, tol=1e-8)
+        got, st = solver.run_iterations(b, U, 2)
+    finally:
+        solver.close()
+    xo, co, io = orc.mbpcg(A, b, U, precond=precond, tol=1e-8)
+    assert info["status"] == 0, info
+    assert relres(A, b, x) <= 1e-8
+    lo, hi = oracle_iteration_band(
+        lambda k: orc.mbpcg(A, perturbed(b, k), U, precond=precond, tol=1e-8)[2]["iterations"],
+        io["iterations"], -(-n // s))
+    assert lo <= info["iterations"] <= hi, (info, io, lo, hi)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    if info["iterations"] == io["iterations"] and info["restarts"] == io["restarts"]:
+        assert err <= 1e-8, (err, info, io)
+    else:
+        assert err <= 2 * kappa_scaled(A, precond) * 1e-8, (err, info, io)
+    ref, st_o = orc.mbpcg_state(A, b, U, 2, precond=precond)
+    for key in ("Xt", "R", "W", "P", "Sigma"):
+        assert np.abs(got[key] - ref[key]).max() <= 1e-10 * np.abs(ref[key]).max(), key
+
+
 def oracle_iteration_band(run_oracle, it_o, bound, samples=12):
     """Allowed range of GPU iteration counts around the oracle's it_o.
 
