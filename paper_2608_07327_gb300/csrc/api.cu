@@ -384,7 +384,7 @@ void enqueue_mbpcg_setup(mbpcg_ctx* h) {
   k_small_setup<<<1, 1, 0, h->stream>>>(h->st, h->red);
   ops->init(h->stream, dm.nb, n, h->s, h->U, h->Q, h->bs, h->X0, h->Xt, h->R, h->part, dm.pstride, h->st);
   enqueue_reduce(h, npack(kp), nullptr);
-  k_small_sigma<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->Sigma, h->SigmaInv);
+  launch_small_sigma(h->stream, kp, h->st, h->red, h->Sigma, h->SigmaInv);
   ops->pw(h->stream, dm.nb, n, h->R, h->W, h->P, h->SigmaInv, nullptr, nullptr, 1);
 }
 
@@ -394,12 +394,11 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
   const int kp = dm.kp, n = dm.n;
   enqueue_product(h, ops, h->P, h->Q, 1, h->st);
   enqueue_reduce(h, npack(kp), h->st);
-  k_small_xi<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->Sigma, h->Xi, h->T);
+  launch_small_xi(h->stream, kp, h->st, h->red, h->Sigma, h->Xi, h->T);
   ops->axpy(h->stream, dm.nb, n, h->P, h->Q, h->W, h->R, h->Xt, h->V, h->T, h->Xi, h->wdiag, h->part, dm.pstride,
             h->st);
   enqueue_reduce(h, npack(kp) + kp, h->st);
-  k_small_zeta<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->Sigma, h->Zeta, h->ZetaInv, h->cond,
-                                                    h->use_cond);
+  launch_small_zeta(h->stream, kp, h->st, h->red, h->Sigma, h->Zeta, h->ZetaInv, h->cond, h->use_cond);
   ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0);
 }
 

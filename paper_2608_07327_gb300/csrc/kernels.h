@@ -61,10 +61,6 @@ inline const RowOps* row_ops(int kp) {
 __global__ void k_reduce(const double* part, int nparts, int pstride, double* out, const SolveState* st);
 __global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s);
 __global__ void k_small_setup(SolveState* st, const double* red);
-__global__ void k_small_sigma(SolveState* st, const double* Gp, int kp, double* Sigma, double* SigmaInv);
-__global__ void k_small_xi(SolveState* st, const double* G1p, int kp, const double* Sigma, double* Xi, double* T);
-__global__ void k_small_zeta(SolveState* st, const double* G2nu, int kp, double* Sigma, double* Zeta,
-                             double* ZetaInv, cudaGraphConditionalHandle cond, int use_cond);
 __global__ void k_small_ls(SolveState* st, const double* Mg, int kp, double* c_out);
 __global__ void k_small_true(SolveState* st, const double* rr);
 __global__ void k_small_cg_setup(SolveState* st, const double* red);
@@ -94,6 +90,13 @@ int oz_ksplit(int n, int sms);
 void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* Atiles);
 void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
                 uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st);
+
+// single-warp k x k steps of the loop (small_warp.cu)
+void launch_small_sigma(cudaStream_t s, int kp, SolveState* st, const double* Gp, double* Sigma, double* SigmaInv);
+void launch_small_xi(cudaStream_t s, int kp, SolveState* st, const double* G1p, const double* Sigma, double* Xi,
+                     double* T);
+void launch_small_zeta(cudaStream_t s, int kp, SolveState* st, const double* G2nu, double* Sigma, double* Zeta,
+                       double* ZetaInv, cudaGraphConditionalHandle cond, int use_cond);
 
 // launch shape of the CSR product + Gram entry points, and the thread-local error message (api.cu)
 void product_gram_shape(int n, int s, int* kp, int* nb, int* pstride);

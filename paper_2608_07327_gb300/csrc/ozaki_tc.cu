@@ -89,6 +89,7 @@ __global__ void k_oz_slice_a(int n, int nK, const double* __restrict__ A, const 
 }
 
 // emaxP[j] = max over rows of the biased exponent of P[:, j] (atomicMax of integers: order-free).
+// Element-parallel: the thread stride is a multiple of KP, so each thread stays on one column.
 template <int KP>
 __global__ void k_oz_colexp(int n, const double* __restrict__ P, int* __restrict__ emaxP,
                             const SolveState* __restrict__ st) {
@@ -96,19 +97,11 @@ __global__ void k_oz_colexp(int n, const double* __restrict__ P, int* __restrict
   __shared__ int m[KP];
   if (threadIdx.x < KP) m[threadIdx.x] = 0;
   __syncthreads();
-  int loc[KP];
-#pragma unroll
-  for (int j = 0; j < KP; ++j) loc[j] = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int j = 0; j < KP; ++j) loc[j] = max(loc[j], biased_exponent(P[(size_t)i * KP + j]));
-  }
-#pragma unroll
-  for (int j = 0; j < KP; ++j) {
-    int v = loc[j];
-    for (int off = 16; off; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(&m[j], v);
-  }
+  const size_t total = (size_t)n * KP, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  int loc = 0;
+  for (size_t q = q0; q < total; q += stride) loc = max(loc, biased_exponent(P[q]));
+  atomicMax(&m[q0 % KP], loc);
   __syncthreads();
   if (threadIdx.x < KP) atomicMax(&emaxP[threadIdx.x], m[threadIdx.x]);
 }
@@ -376,8 +369,8 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
   }
   const int nM = (n + kOzMT - 1) / kOzMT, nK = (n + kOzKC - 1) / kOzKC, KS = oz_ksplit(n, sms);
   cudaMemsetAsync(emaxP, 0, sizeof(int) * KP, s);
-  k_oz_colexp<KP><<<sms, 256, 0, s>>>(n, P, emaxP, st);
   const int g = (int)(((size_t)n * KP + 255) / 256);
+  k_oz_colexp<KP><<<g < 1024 ? g : 1024, 256, 0, s>>>(n, P, emaxP, st);
   k_oz_slice_p<KP, KPT><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
   k_dense_tc<KPT><<<dim3(nM, KS), kOzThreads, C::kSmem, s>>>(n, KP, nK, Atiles, emaxA, Pchunks, emaxP, Qpart, err, st);
   k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, KS, Qpart, Q, st);

@@ -44,143 +44,6 @@ __global__ void k_small_setup(SolveState* st, const double* __restrict__ red) {
   st->ls_res = 0.0;
 }
 
-// W^0, Sigma^0 = qr(R^0) (Cholesky QR): Sigma = chol(R^T R) upper, SigmaInv = Sigma^{-1}.
-__global__ void __launch_bounds__(kSmallThreads)
-k_small_sigma(SolveState* st, const double* __restrict__ Gp, int kp, double* __restrict__ Sigma,
-              double* __restrict__ SigmaInv) {
-  __shared__ double A[kMaxKP * kMaxKP], Zi[kMaxKP * kMaxKP], rd[kMaxKP];
-  __shared__ int flag;
-  const int s = st->s;
-  cta_unpack_sym(s, kp, Gp, A);
-  const int fail = cta_cholesky(s, kp, A, &flag);
-  if (fail) {
-    if (threadIdx.x == 0) {
-      st->done = 1;
-      st->pw_skip = 1;
-      st->status = 6;
-    }
-    for (int q = threadIdx.x; q < kp * kp; q += blockDim.x) Sigma[q] = SigmaInv[q] = 0.0;
-    return;
-  }
-  cta_tri_inv_upper(s, kp, A, Zi, rd);
-  for (int q = threadIdx.x; q < kp * kp; q += blockDim.x) {
-    Sigma[q] = A[q];
-    SigmaInv[q] = Zi[q];
-  }
-  if (threadIdx.x == 0 && st->maxit <= 0) {
-    st->done = 1;
-    st->pw_skip = 1;
-  }
-}
-
-// Xi = (P^T A P)^{-1} through the Cholesky factor of P^T A P (Section 3): G1 = Z^T Z,
-// Xi = Z^{-1} Z^{-T};  T = Xi Sigma.  Starts iteration it+1.
-__global__ void __launch_bounds__(kSmallThreads)
-k_small_xi(SolveState* st, const double* __restrict__ G1p, int kp, const double* __restrict__ Sigma,
-           double* __restrict__ Xi, double* __restrict__ T) {
-  if (st->done) return;
-  __shared__ double A[kMaxKP * kMaxKP], Zi[kMaxKP * kMaxKP], X[kMaxKP * kMaxKP], rd[kMaxKP];
-  __shared__ int flag;
-  const int s = st->s;
-  cta_unpack_sym(s, kp, G1p, A);
-  if (cta_cholesky(s, kp, A, &flag)) {
-    if (threadIdx.x == 0) {
-      st->done = 1;
-      st->pw_skip = 1;
-      st->status = 6;
-    }
-    return;
-  }
-  cta_tri_inv_upper(s, kp, A, Zi, rd);
-  for (int q = threadIdx.x; q < kp * kp; q += blockDim.x) {
-    const int a = q % kp, b = q / kp;
-    double v = 0.0;
-    if (a < s && b < s)
-      for (int l = (a > b ? a : b); l < s; ++l) v = fma(Zi[a + l * kp], Zi[b + l * kp], v);
-    X[q] = v;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < kp * kp; q += blockDim.x) {
-    const int a = q % kp, b = q / kp;
-    double v = 0.0;
-    if (a < s && b < s)
-      for (int l = 0; l <= b; ++l) v = fma(X[a + l * kp], Sigma[l + b * kp], v);
-    Xi[q] = X[q];
-    T[q] = v;
-  }
-  if (threadIdx.x == 0) st->it += 1;
-}
-
-// Best-basis test and the Cholesky QR factor of V = W - A P Xi:
-//   h = argmin_j nu_j (lowest index on ties); stop when sqrt(nu_h) < tol ||rhs|| (Section 2,
-//   initial tolerance = convergence tolerance); else zeta = chol(V^T V), Sigma = zeta Sigma.
-// Sets the WHILE condition of the graph loop (use_cond = 0 when launched outside a graph).
-__global__ void __launch_bounds__(kSmallThreads)
-k_small_zeta(SolveState* st, const double* __restrict__ G2nu, int kp, double* __restrict__ Sigma,
-             double* __restrict__ Zeta, double* __restrict__ ZetaInv, cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double A[kMaxKP * kMaxKP], Zi[kMaxKP * kMaxKP], S[kMaxKP * kMaxKP], rd[kMaxKP];
-  __shared__ int flag, stop;
-  const int s = st->s;
-  if (st->done) {
-    if (threadIdx.x == 0) if (use_cond) cudaGraphSetConditional(cond, 0);
-    return;
-  }
-  if (threadIdx.x == 0) {
-    const double* nu = G2nu + npack(kp);
-    int h = 0;
-    for (int j = 1; j < s; ++j)
-      if (nu[j] < nu[h]) h = j;
-    const double nh = sqrt(nu[h]);
-    st->best_col = h;
-    st->nu_h = nh;
-    stop = 0;
-    if (!st->no_test && nh < st->tol_abs) {
-      st->converged = 1;
-      st->done = 1;
-      st->pw_skip = 1;
-      st->status = 0;
-      stop = 1;
-    }
-  }
-  __syncthreads();
-  if (stop) {
-    if (threadIdx.x == 0) if (use_cond) cudaGraphSetConditional(cond, 0);
-    return;
-  }
-  cta_unpack_sym(s, kp, G2nu, A);
-  if (cta_cholesky(s, kp, A, &flag)) {
-    if (threadIdx.x == 0) {
-      st->done = 1;
-      st->pw_skip = 1;
-      st->status = 6;
-      if (use_cond) cudaGraphSetConditional(cond, 0);
-    }
-    return;
-  }
-  cta_tri_inv_upper(s, kp, A, Zi, rd);
-  for (int q = threadIdx.x; q < kp * kp; q += blockDim.x) S[q] = Sigma[q];
-  __syncthreads();
-  for (int q = threadIdx.x; q < kp * kp; q += blockDim.x) {
-    const int a = q % kp, b = q / kp;
-    double v = 0.0;
-    if (a < s && b < s)
-      for (int l = a; l <= b; ++l) v = fma(A[a + l * kp], S[l + b * kp], v);
-    Sigma[q] = v;
-    Zeta[q] = A[q];
-    ZetaInv[q] = Zi[q];
-  }
-  if (threadIdx.x == 0) {
-    int done = 0;
-    if (st->it >= st->maxit) {
-      done = 1;
-      st->done = 1;
-      st->pw_skip = 0;  // the last iteration still completes its W, P update
-      st->status = st->no_test ? 0 : 5;
-    }
-    if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
-  }
-}
-
 // Exit combination (Section 2): c = argmin ||rhs - Bhat c||, Bhat = B - R (Proposition 1), in the
 // original metric. Written as min ||[rhs | D R] y|| subject to sum(y) = 1 with y = (1 - 1^T c, c)
 // (the same minimiser), solved on the column-equilibrated (s+1) x (s+1) Gram:
