@@ -19,9 +19,9 @@
 //
 // Data movement. Digits are stored in global memory already in the tensor-core operand layout
 // (K-major, no swizzle, 128 x 64 tiles of 16 KB for A, 8*KPT x 64 tiles for P), so whole tiles move
-// with 1-D TMA bulk copies into shared memory. One thread issues copies and MMAs (a software
-// pipeline over 7 A stages and 3 P buffers); the MMA for digit t of A uses all needed digits of P at
-// once (N = KPT * (9 - t)), writing levels t+1..9 of the accumulator. Every wait is bounded.
+// with 1-D TMA bulk copies into shared memory (7 A stages, 3 P buffers). The MMA for digit t of A
+// uses all needed digits of P at once (N = KPT * (9 - t)), writing levels t+1..9 of the
+// accumulator. Producer, MMA issuer and drain run in separate warps; every wait is bounded.
 #include "kernels.h"
 #include "tcgen05.cuh"
 
@@ -36,7 +36,6 @@ constexpr int kOzWin = 2;                              // chunks per exact windo
 constexpr int kOzAStages = 7;
 constexpr int kOzPBufs = 3;
 constexpr uint32_t kATileBytes = kOzMT * kOzKC * 2;    // 16 KB
-constexpr int kOzThreads = 128;
 
 __device__ __forceinline__ int biased_exponent(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
@@ -127,14 +126,24 @@ __global__ void k_oz_slice_p(int n, const double* __restrict__ P, const int* __r
 template <int KPT>
 struct OzCfg {
   static constexpr uint32_t kPChunkBytes = kOzDigits * KPT * kOzKC * 2;
-  static constexpr uint32_t kTmemCols = (8 * KPT <= 128) ? 128 : 256;
+  static constexpr uint32_t kAccCols = 8 * KPT;                         // one accumulator set
+  static constexpr uint32_t kTmemCols = (2 * kAccCols <= 256) ? 256 : 512;  // two sets (double buffer)
   static constexpr size_t kBarBytes = 1024;  // barriers + TMEM slot, keeps tiles 1024-aligned
   static constexpr size_t kSmem = kBarBytes + (size_t)kOzAStages * kATileBytes + (size_t)kOzPBufs * kPChunkBytes;
 };
 
+constexpr int kOzDrainWarps = 4;                      // warps 0..3: TMEM lane quarters 0..3
+constexpr int kOzProducerWarp = 4;                    // TMA issue
+constexpr int kOzMmaWarp = 5;                         // MMA issue
+constexpr int kOzTcThreads = 32 * 6;
+
 // Qpart[ks][i][j] = the part of (A P)_ij over the K range of split ks, for j < KP.
+// Warp-specialised: a producer thread streams A-digit tiles and P-digit chunks into shared memory
+// (empty/full mbarriers), an MMA thread issues tcgen05.mma into one of two TMEM accumulator sets,
+// alternating per window of 128 values of l, and four drain warps read a finished set (levels
+// 2..6 exact in int64, 7..9 in FP32) while the MMA thread fills the other.
 template <int KPT>
-__global__ void __launch_bounds__(kOzThreads, 1)
+__global__ void __launch_bounds__(kOzTcThreads, 1)
 k_dense_tc(int n, int KP, int nK, const uint8_t* __restrict__ Atiles, const int* __restrict__ emaxA,
            const uint8_t* __restrict__ Pchunks, const int* __restrict__ emaxP, double* __restrict__ Qpart,
            int* __restrict__ err, const SolveState* __restrict__ st) {
@@ -145,29 +154,33 @@ k_dense_tc(int n, int KP, int nK, const uint8_t* __restrict__ Atiles, const int*
   uint64_t* empty = full + kOzAStages;
   uint64_t* pfull = empty + kOzAStages;
   uint64_t* pempty = pfull + kOzPBufs;
-  uint64_t* wdone = pempty + kOzPBufs;
-  uint64_t* fin = wdone + 1;
+  uint64_t* accf = pempty + kOzPBufs;  // [2] accumulator set ready for draining
+  uint64_t* acce = accf + 2;           // [2] accumulator set drained
+  uint64_t* fin = acce + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
-  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint8_t* As = osm + C::kBarBytes;
   uint8_t* Ps = As + (size_t)kOzAStages * kATileBytes;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mt = blockIdx.x, KS = gridDim.y, ks = blockIdx.y;
   const int c0 = (int)((long long)nK * ks / KS), c1 = (int)((long long)nK * (ks + 1) / KS);
-  const int nch = c1 - c0, T = nch * kOzDigits;
+  const int nch = c1 - c0;
   const int nwin = (nch + kOzWin - 1) / kOzWin;
 
   if (tid == 0) {
-    for (int s = 0; s < kOzAStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int q = 0; q < kOzAStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
     }
-    for (int b = 0; b < kOzPBufs; ++b) {
-      mbar_init(&pfull[b], 1);
-      mbar_init(&pempty[b], 1);
+    for (int q = 0; q < kOzPBufs; ++q) {
+      mbar_init(&pfull[q], 1);
+      mbar_init(&pempty[q], 1);
     }
-    mbar_init(wdone, 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&accf[q], 1);
+      mbar_init(&acce[q], kOzDrainWarps);
+    }
     mbar_init(fin, 1);
     *abort_flag = 0;
     mbar_fence_init();
@@ -177,141 +190,150 @@ k_dense_tc(int n, int KP, int nK, const uint8_t* __restrict__ Atiles, const int*
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  int issued_a = 0, issued_p = 0;  // copies issued (producer thread only)
 
-  auto a_src = [&](int j) {
-    return Atiles + (((size_t)mt * nK + (c0 + j / kOzDigits)) * kOzDigits + (j % kOzDigits)) * kATileBytes;
-  };
-  auto issue_a = [&](int j) {
-    const int s = j % kOzAStages;
-    mbar_arrive_expect_tx(&full[s], kATileBytes);
-    tma_load_1d(As + (size_t)s * kATileBytes, a_src(j), kATileBytes, &full[s]);
-  };
-  auto issue_p = [&](int cc) {
-    const int b = cc % kOzPBufs;
-    mbar_arrive_expect_tx(&pfull[b], C::kPChunkBytes);
-    tma_load_1d(Ps + (size_t)b * C::kPChunkBytes, Pchunks + (size_t)(c0 + cc) * C::kPChunkBytes, C::kPChunkBytes,
-                &pfull[b]);
-  };
-
-  int issued_a = 0, issued_p = 0, next_j = 0;
-  if (tid == 0) {
-    for (; issued_p < nch && issued_p < 2; ++issued_p) issue_p(issued_p);
-    for (; issued_a < T && issued_a < kOzAStages; ++issued_a) issue_a(issued_a);
-  }
-
-  long long acc_i[KPT];
-  float acc_f[KPT];
-#pragma unroll
-  for (int j = 0; j < KPT; ++j) {
-    acc_i[j] = 0;
-    acc_f[j] = 0.f;
-  }
-
-  for (int w = 0; w < nwin; ++w) {
-    if (tid == 0 && !*abort_flag) {
-      const int cc_end = min(nch, (w + 1) * kOzWin);
+  if (warp == kOzProducerWarp) {
+    if (lane == 0) {
       bool ok = true;
-      for (int cc = w * kOzWin; cc < cc_end && ok; ++cc) {
+      for (int cc = 0; cc < nch && ok; ++cc) {
         const int b = cc % kOzPBufs;
-        ok = mbar_wait_bounded(&pfull[b], (uint32_t)((cc / kOzPBufs) & 1));
+        if (cc >= kOzPBufs) ok = mbar_wait_bounded(&pempty[b], (uint32_t)((cc / kOzPBufs - 1) & 1));
+        if (!ok) break;
+        mbar_arrive_expect_tx(&pfull[b], C::kPChunkBytes);
+        tma_load_1d(Ps + (size_t)b * C::kPChunkBytes, Pchunks + (size_t)(c0 + cc) * C::kPChunkBytes,
+                    C::kPChunkBytes, &pfull[b]);
+        issued_p = cc + 1;
         for (int t = 0; t < kOzDigits && ok; ++t) {
-          const int j = next_j++;
-          const int s = j % kOzAStages;
-          ok = mbar_wait_bounded(&full[s], (uint32_t)((j / kOzAStages) & 1));
+          const int j = cc * kOzDigits + t, q = j % kOzAStages;
+          if (j >= kOzAStages) ok = mbar_wait_bounded(&empty[q], (uint32_t)((j / kOzAStages - 1) & 1));
           if (!ok) break;
-          const uint32_t a_base = smem_addr(As + (size_t)s * kATileBytes);
-          const uint32_t b_base = smem_addr(Ps + (size_t)b * C::kPChunkBytes);
-          const uint32_t idesc = umma_idesc_bf16_f32(kOzMT, KPT * (kOzDigits - t));
-          const uint32_t d = tmem + (uint32_t)(KPT * t);
-#pragma unroll
-          for (int k4 = 0; k4 < kOzKC / 16; ++k4) {
-            const uint32_t first = (cc == w * kOzWin && t == 0 && k4 == 0) ? 0u : 1u;
-            umma_bf16(d, umma_smem_desc(a_base + 256u * k4, 128, 1024), umma_smem_desc(b_base + 256u * k4, 128, 1024),
-                      idesc, first);
-          }
-          umma_commit(&empty[s]);
-          if (t == kOzDigits - 1) umma_commit(&pempty[b]);
-          // refill the stage of the previous tile (its MMAs are ahead of the ones just issued)
-          if (j >= 1 && issued_a < T) {
-            const int jp = j - 1;
-            ok = mbar_wait_bounded(&empty[jp % kOzAStages], (uint32_t)((jp / kOzAStages) & 1));
-            if (ok) issue_a(issued_a++);
-          }
-          // after the first tile of chunk cc, load chunk cc+1 (issued_p == cc+1) into the buffer of
-          // chunk cc-2, whose MMAs were issued two chunks ago
-          if (t == 0 && cc >= 1 && issued_p < nch && ok) {
-            if (cc >= 2) {
-              const int cp = cc - 2;
-              ok = mbar_wait_bounded(&pempty[cp % kOzPBufs], (uint32_t)((cp / kOzPBufs) & 1));
-            }
-            if (ok) issue_p(issued_p++);
-          }
+          mbar_arrive_expect_tx(&full[q], kATileBytes);
+          tma_load_1d(As + (size_t)q * kATileBytes,
+                      Atiles + (((size_t)mt * nK + c0 + cc) * kOzDigits + t) * kATileBytes, kATileBytes, &full[q]);
+          issued_a = j + 1;
+          if (*abort_flag) ok = false;
         }
       }
       if (!ok) {
         *abort_flag = 1;
         if (err != nullptr) atomicExch(err, 1);
       }
-      umma_commit(wdone);
     }
-    __syncwarp();
-    const bool wok = mbar_wait_bounded(wdone, (uint32_t)(w & 1));
-    if (!wok) *abort_flag = 1;
-    tc_fence_after_sync();
-    // drain levels 2..9 of this thread's row (TMEM lane 32*warp + lane)
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+  } else if (warp == kOzMmaWarp) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int w = 0; w < nwin && ok; ++w) {
+        const int ab = w & 1;
+        if (w >= 2) ok = mbar_wait_bounded(&acce[ab], (uint32_t)((w / 2 - 1) & 1));
+        tc_fence_after_sync();
+        const int cc_end = min(nch, (w + 1) * kOzWin);
+        for (int cc = w * kOzWin; cc < cc_end && ok; ++cc) {
+          const int b = cc % kOzPBufs;
+          ok = mbar_wait_bounded(&pfull[b], (uint32_t)((cc / kOzPBufs) & 1));
+          for (int t = 0; t < kOzDigits && ok; ++t) {
+            const int j = cc * kOzDigits + t, q = j % kOzAStages;
+            ok = mbar_wait_bounded(&full[q], (uint32_t)((j / kOzAStages) & 1));
+            if (!ok) break;
+            const uint32_t a_base = smem_addr(As + (size_t)q * kATileBytes);
+            const uint32_t b_base = smem_addr(Ps + (size_t)b * C::kPChunkBytes);
+            const uint32_t idesc = umma_idesc_bf16_f32(kOzMT, KPT * (kOzDigits - t));
+            const uint32_t d = tmem + (uint32_t)(ab * C::kAccCols + KPT * t);
 #pragma unroll
-    for (int L = 0; L < kOzDigits; ++L) {
-      float v[KPT];
-      if constexpr (KPT == 32) {
-        uint32_t r[32];
-        tmem_ld32(lane_base + (uint32_t)(KPT * L), r);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-      } else {
-        uint32_t r[16];
-        tmem_ld16(lane_base + (uint32_t)(KPT * L), r);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+            for (int k4 = 0; k4 < kOzKC / 16; ++k4) {
+              const uint32_t first = (cc == w * kOzWin && t == 0 && k4 == 0) ? 0u : 1u;
+              umma_bf16(d, umma_smem_desc(a_base + 256u * k4, 128, 1024),
+                        umma_smem_desc(b_base + 256u * k4, 128, 1024), idesc, first);
+            }
+            umma_commit(&empty[q]);
+            if (t == kOzDigits - 1) umma_commit(&pempty[b]);
+            if (*abort_flag) ok = false;
+          }
+        }
+        if (!ok) *abort_flag = 1;  // before the commit, so the drain warps see it
+        umma_commit(&accf[ab]);
       }
-      if (L < 5) {
-        const int sh = 7 * (4 - L);
-#pragma unroll
-        for (int j = 0; j < KPT; ++j) acc_i[j] += (long long)__float2int_rn(v[j]) << sh;
-      } else {
-        const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : 0x1p-14f;
-#pragma unroll
-        for (int j = 0; j < KPT; ++j) acc_f[j] = fmaf(v[j], sc, acc_f[j]);
+      if (!ok) {
+        *abort_flag = 1;
+        if (err != nullptr) atomicExch(err, 1);
       }
-    }
-    tc_fence_before_sync();
-    __syncthreads();
-    tc_fence_after_sync();
-    if (*abort_flag) break;
-  }
-
-  if (*abort_flag) {
-    if (tid == 0) {  // let the copies and MMAs still in flight land before the memory is released
-      for (int j = next_j; j < issued_a; ++j) mbar_wait_bounded(&full[j % kOzAStages], (uint32_t)((j / kOzAStages) & 1));
-      for (int cc = 0; cc < issued_p; ++cc) mbar_wait_bounded(&pfull[cc % kOzPBufs], (uint32_t)((cc / kOzPBufs) & 1));
       umma_commit(fin);
       mbar_wait_bounded(fin, 0);
     }
   } else {
-    const int row = mt * kOzMT + 32 * warp + lane;
-    if (row < n) {
-      const int fa = emaxA[row] - 1022;
-      double* out = Qpart + ((size_t)ks * n + row) * KP;
+    // drain warps 0..3: warp w reads TMEM lanes 32w..32w+31 = rows of this M tile
+    long long acc_i[KPT];
+    float acc_f[KPT];
 #pragma unroll
-      for (int j = 0; j < KPT; ++j) {
-        if (j < KP) {
-          const double v = (double)acc_i[j] * 0x1p-42 + (double)acc_f[j] * 0x1p-49;
-          out[j] = ldexp(v, fa + emaxP[j] - 1022);
+    for (int j = 0; j < KPT; ++j) {
+      acc_i[j] = 0;
+      acc_f[j] = 0.f;
+    }
+    bool ok = true;
+    for (int w = 0; w < nwin; ++w) {
+      const int ab = w & 1;
+      if (!mbar_wait_bounded(&accf[ab], (uint32_t)((w / 2) & 1))) ok = false;
+      tc_fence_after_sync();
+      if (!ok || *abort_flag) {
+        ok = false;
+        break;
+      }
+      const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * C::kAccCols);
+#pragma unroll
+      for (int L = 0; L < kOzDigits; ++L) {
+        float v[KPT];
+        if constexpr (KPT == 32) {
+          uint32_t r[32];
+          tmem_ld32(lane_base + (uint32_t)(KPT * L), r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+        } else {
+          uint32_t r[16];
+          tmem_ld16(lane_base + (uint32_t)(KPT * L), r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+        }
+        if (L < 5) {
+          const int sh = 7 * (4 - L);
+#pragma unroll
+          for (int j = 0; j < KPT; ++j) acc_i[j] += (long long)__float2int_rn(v[j]) << sh;
+        } else {
+          const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : 0x1p-14f;
+#pragma unroll
+          for (int j = 0; j < KPT; ++j) acc_f[j] = fmaf(v[j], sc, acc_f[j]);
         }
       }
+      tc_fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[ab]);
     }
+    if (ok && !*abort_flag) {
+      const int row = mt * kOzMT + 32 * warp + lane;
+      if (row < n) {
+        const int fa = emaxA[row] - 1022;
+        double* out = Qpart + ((size_t)ks * n + row) * KP;
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+          if (j < KP) {
+            const double v = (double)acc_i[j] * 0x1p-42 + (double)acc_f[j] * 0x1p-49;
+            out[j] = ldexp(v, fa + emaxP[j] - 1022);
+          }
+        }
+      }
+    } else {
+      *abort_flag = 1;
+      if (err != nullptr) atomicExch(err, 1);
+    }
+  }
+  __syncthreads();
+  if (*abort_flag && tid == 32 * kOzProducerWarp) {
+    // let the copies still in flight land before the shared memory is released (bounded waits);
+    // only the last issue into each stage or buffer can still be pending
+    for (int j = max(0, issued_a - kOzAStages); j < issued_a; ++j)
+      mbar_wait_bounded(&full[j % kOzAStages], (uint32_t)((j / kOzAStages) & 1));
+    for (int cc = max(0, issued_p - kOzPBufs); cc < issued_p; ++cc)
+      mbar_wait_bounded(&pfull[cc % kOzPBufs], (uint32_t)((cc / kOzPBufs) & 1));
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -372,7 +394,7 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
   const int g = (int)(((size_t)n * KP + 255) / 256);
   k_oz_colexp<KP><<<g < 1024 ? g : 1024, 256, 0, s>>>(n, P, emaxP, st);
   k_oz_slice_p<KP, KPT><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
-  k_dense_tc<KPT><<<dim3(nM, KS), kOzThreads, C::kSmem, s>>>(n, KP, nK, Atiles, emaxA, Pchunks, emaxP, Qpart, err, st);
+  k_dense_tc<KPT><<<dim3(nM, KS), kOzTcThreads, C::kSmem, s>>>(n, KP, nK, Atiles, emaxA, Pchunks, emaxP, Qpart, err, st);
   k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, KS, Qpart, Q, st);
 }
 
