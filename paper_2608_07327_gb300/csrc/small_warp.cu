@@ -8,12 +8,15 @@
 // kernels keep the padded columns of every block at exactly zero.
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace mbpcg {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+namespace cg = cooperative_groups;
 
 // Loads the symmetric s x s matrix whose upper triangle is packed in `packed` into column j = lane:
 // a[i] = G[i][j] (i <= j), identity outside the leading s x s block.
@@ -312,13 +315,14 @@ __device__ __forceinline__ void unpack_upper(int q, int& l, int& m) {
 // unit for ~16 cycles), so each pivot's square root and reciprocal is computed once, by the thread
 // that finishes updating that pivot one step earlier (look-ahead), and read by all from shared
 // memory: one barrier per column.
-template <int KP>
-__device__ bool cta_chol(double* A, double* Z, int s) {
+template <int KP, int NT = kCtaSmall>
+__device__ bool cta_chol(double* A, double* Z, int s, const double** rz_out = nullptr) {
   constexpr int LD = SmallLd<KP>::LD;
   __shared__ double maxd, zd[KP], rzd[KP], ipd[KP];  // sqrt(pivot), 1/sqrt(pivot), 1/pivot
+  if (rz_out != nullptr) *rz_out = rzd;
   __shared__ int bad;
   const int tid = threadIdx.x;
-  for (int q = tid; q < KP * LD; q += kCtaSmall) Z[q] = 0.0;
+  for (int q = tid; q < KP * LD; q += NT) Z[q] = 0.0;
   if (tid == 0) {
     double m = 0.0;
     for (int j = 0; j < s; ++j) m = fmax(m, A[j * LD + j]);
@@ -334,7 +338,7 @@ __device__ bool cta_chol(double* A, double* Z, int s) {
   for (int k = 0; k < KP; ++k) {
     const double zkk = zd[k], rz = rzd[k], ip = ipd[k];
     const int t = KP - k, cnt = t * (t + 1) / 2;
-    for (int q = tid; q < cnt; q += kCtaSmall) {
+    for (int q = tid; q < cnt; q += NT) {
       int l, m;
       unpack_upper(q, l, m);
       l += k;
@@ -388,10 +392,10 @@ __device__ void cta_tri_inv(const double* Z, double* Zi, double* Tmp) {
   }
 }
 
-template <int KP>
+template <int KP, int NT = kCtaSmall>
 __device__ void cta_load_packed(const double* __restrict__ packed, int s, double* A) {
   constexpr int LD = SmallLd<KP>::LD;
-  for (int q = threadIdx.x; q < KP * KP; q += kCtaSmall) {
+  for (int q = threadIdx.x; q < KP * KP; q += NT) {
     const int i = q / KP, j = q % KP;
     double v;
     if (i < s && j < s) v = (i <= j) ? packed[pidx(i, j)] : packed[pidx(j, i)];
@@ -438,110 +442,318 @@ k_small_sigma_c(SolveState* st, const double* __restrict__ Gp, double* __restric
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// KP >= 16 inside the loop: a cluster of CS CTAs of 128 threads.
+//
+// Cost model of this part: an FP64 instruction holds its SM sub-partition's FP64 unit for 64 cycles
+// whatever the number of active lanes, and its result is ready 64 cycles later (four independent
+// chains in one warp take four times as long as one). So the factorisation is organised around its
+// serial chain of pivots, and every other FP64 operation is packed into full warps and spread over
+// the sub-partitions and the CTAs of the cluster.
+//
+// Factorisation (every CTA of the cluster, redundantly): symmetric Gaussian elimination
+// G = L D L^T that builds L^{-1} alongside (the row operations applied to the identity). Warp 0 (the
+// pivot warp) carries the chain: pivot d_k -> 1/d_k -> row k+1 updated by step k -> d_{k+1}; warps
+// 1-3 and, at KP = 32, 5-7 (two per sub-partition, so that one hides the other's latencies; warp 4
+// stays idle to leave the pivot warp's sub-partition to it) apply step k to the rest of the trailing matrix and
+// to L^{-1} while the pivot warp already works on step k+1 (two named barriers per step hand rows
+// over). The Cholesky factor and the
+// inverses follow without further serial steps: Z = D^{1/2} L^T, Z^{-1} = L^{-T} D^{-1/2},
+// Xi = G^{-1} = L^{-T} D^{-1} L^{-1}.
+//
+// After it, each CTA owns CPC = 128 / KP columns b = c + CS r (r < CPC; c = rank in the cluster) of
+// every result; columns computed elsewhere are read from the owner's shared memory (distributed
+// shared memory) after a cluster barrier.
+
 template <int KP>
-__global__ void __launch_bounds__(kCtaSmall)
-k_small_xi_c(SolveState* st, const double* __restrict__ G1p, const double* __restrict__ Sigma,
+struct ClusterCfg {
+  static constexpr int NT = 128;       // threads of the column phases (thread = (column r, row a))
+  static constexpr int NF = KP >= 32 ? 256 : 128;  // threads of the CTA (all take part in the factorisation)
+  static constexpr int NB = NF > 128 ? NF - 64 : NF - 32;  // bulk threads (warp 0 and, if present, 4 excluded)
+  static constexpr int IDLE = NF > 128 ? 4 : 3;             // warp free before the factorisation's bulk work
+  static constexpr int CPC = NT / KP;  // columns per CTA: 4 (KP = 32), 8 (KP = 16)
+  static constexpr int CS = KP / CPC;  // CTAs per cluster: 8, 2
+};
+
+// 1/d for a positive normal d below 2^1000, within about an ulp: the hardware approximation
+// (rcp.approx.f32) of d's leading 23 significand bits, rescaled by d's exponent with integer
+// operations, then one third-order Newton step y = y0 (1 + e + e^2), e = 1 - d y0 (the truncated
+// series of 1 / (1 - e)); the seed's relative error is below 2^-22, so e^3 is below 2^-66.
+__device__ __forceinline__ double rcp_pos(double d) {
+  const long long bits = __double_as_longlong(d);
+  const int e = (int)(bits >> 52) & 0x7FF;
+  const float f = __int_as_float(0x3F800000 | (int)((bits >> 29) & 0x7FFFFF));  // in [1, 2)
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));  // in (0.5, 1]
+  const int rb = __float_as_int(r);
+  const long long ex = (long long)(((rb >> 23) & 0xFF) - 127 + 2046 - e);
+  const double y0 = __longlong_as_double((ex << 52) | ((long long)(rb & 0x7FFFFF) << 29));
+  const double eps = fma(-d, y0, 1.0);
+  const double e2 = fma(eps, eps, eps);
+  return fma(y0, e2, y0);
+}
+
+// 1/sqrt(d) for a positive normal d, within about an ulp: rsqrt.approx.f32 of the leading
+// significand bits with the exponent's parity folded in (argument in [1, 4)), then one third-order
+// Newton step y = y0 (1 + e/2 + 3 e^2/8), e = 1 - d y0^2 (the series of (1 - e)^{-1/2}).
+__device__ __forceinline__ double rsqrt_pos(double d) {
+  const long long bits = __double_as_longlong(d);
+  const int E = ((int)(bits >> 52) & 0x7FF) - 1023;
+  const int odd = E & 1;
+  const float f = __int_as_float(((127 + odd) << 23) | (int)((bits >> 29) & 0x7FFFFF));  // in [1, 4)
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));  // in (0.5, 1]
+  const int rb = __float_as_int(r);
+  const int half = (E - odd) / 2;
+  const long long ex = (long long)(((rb >> 23) & 0xFF) - 127 - half + 1023);
+  const double y0 = __longlong_as_double((ex << 52) | ((long long)(rb & 0x7FFFFF) << 29));
+  const double t = d * y0;
+  const double eps = fma(-t, y0, 1.0);
+  const double q = eps * fma(eps, 0.375, 0.5);
+  return fma(y0, q, y0);
+}
+
+__device__ __forceinline__ void named_bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Shared working set of the factorisation (matrices row-major with ld KP+1).
+template <int KP>
+struct LdlWork {
+  static constexpr int LD = KP + 1;
+  static constexpr int OU = KP * LD, OL = 2 * KP * LD, OR = 3 * KP * LD;  // offsets of U, Lt, R from S
+  double S[KP * LD];   // in: G (identity outside s x s); then the trailing matrices; later reused
+  double U[KP * LD];   // row k of D L^T: U[k][m] = d_k L[m][k] (m >= k)
+  double Lt[KP * LD];  // Lt[k][m] = L[m][k] (m > k)
+  double R[KP * LD];   // L^{-1}, unit lower triangular
+  double d[KP], inv[KP];
+  unsigned short tri[KP * (KP + 1) / 2];  // packed index q = m (m+1)/2 + l (l <= m) -> l | m << 8
+  int bad;
+};
+
+template <int KP>
+__device__ void ldl_init(LdlWork<KP>& W, const double* __restrict__ packed, int s) {
+  constexpr int LD = LdlWork<KP>::LD, NT = ClusterCfg<KP>::NF, NI = KP * KP / NT;
+  double v[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {  // all loads in flight at once
+    const int q = threadIdx.x + NT * i, r = q / KP, c = q % KP;
+    v[i] = (r < s && c < s) ? ((r <= c) ? packed[pidx(r, c)] : packed[pidx(c, r)]) : (r == c ? 1.0 : 0.0);
+  }
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int q = threadIdx.x + NT * i, r = q / KP, c = q % KP;
+    W.S[r * LD + c] = v[i];
+    W.R[r * LD + c] = (r == c) ? 1.0 : 0.0;
+    if (r >= s) W.U[r * LD + c] = (r == c) ? 1.0 : 0.0;
+  }
+  for (int m = 0, q0 = 0; m < KP; q0 += ++m)
+    for (int l = threadIdx.x; l <= m; l += NT) W.tri[q0 + l] = (unsigned short)(l | (m << 8));
+  if (threadIdx.x < KP && threadIdx.x >= s) W.d[threadIdx.x] = W.inv[threadIdx.x] = 1.0;
+  __syncthreads();
+}
+
+// G = L D L^T and L^{-1} (see above). Sets W.bad when a pivot of the leading s x s block is not a
+// finite number above 64 eps max_j G_jj (or not below 2^1000). All NF threads call it; it ends with
+// a block-wide barrier.
+template <int KP>
+__device__ void ldl_factor(LdlWork<KP>& W, int s) {
+  using LW = LdlWork<KP>;
+  constexpr int LD = LW::LD, NB = ClusterCfg<KP>::NB, NBAR = 32 + NB;  // threads on the named barriers
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {  // pivot warp; lane j holds column j of the current pivot row
+    const int j = tid;
+    long long mb = (j < s) ? __double_as_longlong(W.S[j * LD + j]) : 0;  // bit order = value order for x >= 0
+#pragma unroll
+    for (int off = 16; off; off >>= 1) mb = max(mb, __shfl_xor_sync(kFull, mb, off));
+    const long long thr_b = __double_as_longlong(64.0 * DBL_EPSILON * __longlong_as_double(mb));
+    double row = (j < KP) ? W.S[j] : 0.0;
+    bool bad = false;
+    for (int k = 0; k < s; ++k) {
+      const double dk = __shfl_sync(kFull, row, k);
+      const double a = __shfl_sync(kFull, row, (k + 1 < KP) ? k + 1 : k);
+      const long long db = __double_as_longlong(dk);
+      bad |= !(db > thr_b && db < 0x7E70000000000000LL);  // thr < d_k < 2^1000 (NaN fails)
+      const double inv = rcp_pos(dk);
+      const double w = row * inv;
+      if (j >= k && j < KP) W.U[k * LD + j] = row;
+      if (j > k && j < KP) W.Lt[k * LD + j] = w;
+      if (j == 0) {
+        W.d[k] = dk;
+        W.inv[k] = inv;
+      }
+      // The bulk warps must have finished step k-1 before step k is published: otherwise their
+      // step-k arrivals on barrier 2 could complete the phase meant for step k-1 without this warp.
+      if (k >= 1) named_bar_sync(2, NBAR);  // the bulk warps finished step k-1
+      named_bar_arrive(1, NBAR);            // step k published
+      if (k + 1 < s) {
+        const double nxt = (j < KP) ? W.S[(k + 1) * LD + j] : 0.0;  // row k+1 after step k-1
+        row = fma(-a, w, nxt);
+      }
+    }
+    named_bar_sync(2, NBAR);
+    if (j == 0) W.bad = bad ? 1 : 0;
+  } else if (warp != 4) {  // bulk: step k on rows k+2.. of the trailing matrix and rows k+1.. of L^{-1}
+    static_assert(ClusterCfg<KP>::NF == 128 || ClusterCfg<KP>::NF == 256, "bulk thread numbering");
+    const int bt = tid - (warp < 4 ? 32 : 64);
+    double* base = W.S;
+    for (int k = 0; k < s; ++k) {
+      named_bar_sync(1, NBAR);
+      const int t = s - k - 2, cntS = t > 0 ? t * (t + 1) / 2 : 0;
+      const int rows = s - k - 1, cnt = cntS + rows * (k + 1);
+      const unsigned long long magic = rows > 0 ? ((1ull << 32) + rows - 1) / rows : 0;  // q / rows = q magic >> 32 (q < 2^10)
+      for (int q = bt; q < cnt; q += NB) {
+        int zo, xo, yo;
+        if (q < cntS) {  // S[l][m] -= S[k][l] S[k][m] / d_k
+          const int pk = W.tri[q], l = k + 2 + (pk & 0xFF), m = k + 2 + (pk >> 8);
+          zo = l * LD + m;
+          xo = LW::OU + k * LD + l;
+          yo = LW::OL + k * LD + m;
+        } else {  // R[l][j] -= L[l][k] R[k][j]
+          const int q2 = q - cntS, jj = (int)(((unsigned long long)q2 * magic) >> 32), l = k + 1 + (q2 - jj * rows);
+          zo = LW::OR + l * LD + jj;
+          xo = LW::OL + k * LD + l;
+          yo = LW::OR + k * LD + jj;
+        }
+        base[zo] = fma(-base[xo], base[yo], base[zo]);
+      }
+      named_bar_arrive(2, NBAR);
+    }
+  }
+  __syncthreads();
+}
+
+// Copies the columns of M (ld KP+1) owned by the other CTAs of the cluster into this CTA's M
+// (upper triangle a <= b only when upper is set).
+template <int KP>
+__device__ void cluster_gather_columns(double* M, int c, bool upper) {
+  using CC = ClusterCfg<KP>;
+  constexpr int LD = KP + 1;
+  cg::cluster_group cluster = cg::this_cluster();
+  for (int q = threadIdx.x; q < KP * KP; q += CC::NF) {
+    const int a = q / KP, b = q % KP, owner = b % CC::CS;
+    if (owner != c && (!upper || a <= b)) {
+      const double* rm = cluster.map_shared_rank(M, owner);
+      M[a * LD + b] = rm[a * LD + b];
+    }
+  }
+}
+
+// Xi = (P^T A P)^{-1} from the packed Gram G1p and T = Xi Sigma, both column-major KP x KP with zeros
+// outside s x s; the step counter advances.
+template <int KP>
+__global__ void __launch_bounds__(ClusterCfg<KP>::NF) __cluster_dims__(ClusterCfg<KP>::CS, 1, 1)
+k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __restrict__ Sigma,
              double* __restrict__ Xi, double* __restrict__ T) {
-  constexpr int LD = SmallLd<KP>::LD;
+  using CC = ClusterCfg<KP>;
+  constexpr int LD = KP + 1;
+  __shared__ LdlWork<KP> W;
+  __shared__ double Sg[KP * CC::CPC], V[KP * CC::CPC];
+  cg::cluster_group cluster = cg::this_cluster();
   if (st->done) return;
-  __shared__ double A[KP * LD], Z[KP * LD], Zi[KP * LD], Tmp[KP * LD];
-  const int s = st->s, tid = threadIdx.x;
-  cta_load_packed<KP>(G1p, s, A);
-  if (!cta_chol<KP>(A, Z, s)) {
-    if (tid == 0) {
+  const int s = st->s, tid = threadIdx.x, c = (int)cluster.block_rank();
+  const bool ct = tid < CC::NT;  // column-phase thread: column b = c + CS r, row a
+  const int r = tid / KP, a = tid % KP, b = c + CC::CS * r;
+  if (ct) Sg[a * CC::CPC + r] = Sigma[a + b * KP];  // own columns of Sigma (upper, zero outside s x s)
+  ldl_init<KP>(W, G1p, s);
+  ldl_factor<KP>(W, s);
+  if (W.bad) {  // every CTA reaches the same verdict
+    if (c == 0 && tid == 0) {
       st->done = 1;
       st->pw_skip = 1;
       st->status = 6;
     }
     return;
   }
-  cta_tri_inv<KP>(Z, Zi, Tmp);
-  // Xi = Zi Zi^T (into A; upper half computed, mirrored), Sigma (into Tmp)
-  for (int q = tid; q < KP * (KP + 1) / 2; q += kCtaSmall) {
-    int a, b;
-    unpack_upper(q, a, b);  // a <= b
+  // Xi[a][b] = sum_{j >= b} L^{-1}[j][a] (L^{-1}[j][b] / d_j) for a <= b, into W.S (upper part)
+  double* X = W.S;
+  if (ct) {
+    V[a * CC::CPC + r] = W.inv[a] * W.R[a * LD + b];
+    __syncwarp();
     double v = 0.0;
-    for (int l = b; l < KP; ++l) v = fma(Zi[a * LD + l], Zi[b * LD + l], v);
-    v = (b < s) ? v : 0.0;
-    A[a * LD + b] = v;
-    A[b * LD + a] = v;
+    for (int j = b; j < s; ++j) v = fma(W.R[j * LD + a], V[j * CC::CPC + r], v);
+    if (a <= b) X[a * LD + b] = v;
   }
-  for (int q = tid; q < KP * KP; q += kCtaSmall) {
-    const int a = q / KP, b = q % KP;
-    Tmp[a * LD + b] = Sigma[a + b * KP];
-  }
+  cluster.sync();
+  cluster_gather_columns<KP>(X, c, true);
   __syncthreads();
-  cta_store<KP>(Xi, A, s);
-  {  // T = Xi Sigma (Sigma upper: l <= b); each thread interleaves its R outputs
-    constexpr int R = KP * KP / kCtaSmall > 0 ? KP * KP / kCtaSmall : 1;
-    const int a = tid % KP;
-    int b[R];
-    double v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      b[r] = (tid + r * kCtaSmall) / KP;
-      v[r] = 0.0;
-    }
-    if (tid + (R - 1) * kCtaSmall < KP * KP) {
-      for (int l = 0; l <= b[R - 1]; ++l) {
-        const double xa = A[a * LD + l];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (l <= b[r]) v[r] = fma(xa, Tmp[l * LD + b[r]], v[r]);
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) T[a + b[r] * KP] = (a < s && b[r] < s) ? v[r] : 0.0;
-    }
+  if (ct) {
+    const bool in = (a < s && b < s);
+    Xi[a + b * KP] = in ? X[min(a, b) * LD + max(a, b)] : 0.0;
+    double v = 0.0;  // T[a][b] = sum_{l <= b} Xi[a][l] Sigma[l][b]
+    for (int l = 0; l <= b; ++l) v = fma(X[min(a, l) * LD + max(a, l)], Sg[l * CC::CPC + r], v);
+    T[a + b * KP] = in ? v : 0.0;
   }
-  if (tid == 0) st->it += 1;
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+  if (c == 0 && tid == 0) st->it += 1;
 }
 
+// zeta from the packed Gram V^T V (Z = D^{1/2} L^T), zeta^{-1}, Sigma <- zeta Sigma, after the
+// stopping test on nu (argmin over the columns, lowest index on ties); sets the loop's conditional.
+// The factorisation starts before the stopping test is decided and is discarded if it stops.
 template <int KP>
-__global__ void __launch_bounds__(kCtaSmall)
-k_small_zeta_c(SolveState* st, const double* __restrict__ G2nu, double* __restrict__ Sigma,
+__global__ void __launch_bounds__(ClusterCfg<KP>::NF) __cluster_dims__(ClusterCfg<KP>::CS, 1, 1)
+k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restrict__ Sigma,
                double* __restrict__ Zeta, double* __restrict__ ZetaInv, cudaGraphConditionalHandle cond,
                int use_cond) {
-  constexpr int LD = SmallLd<KP>::LD;
-  __shared__ double A[KP * LD], Z[KP * LD], Zi[KP * LD], Tmp[KP * LD];
-  __shared__ int stop;
-  const int s = st->s, tid = threadIdx.x;
+  using CC = ClusterCfg<KP>;
+  constexpr int LD = KP + 1;
+  __shared__ LdlWork<KP> W;
+  __shared__ double Sg[KP * CC::CPC];
+  __shared__ double nh_s;
+  __shared__ int h_s, stop_s;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int s = st->s, tid = threadIdx.x, c = (int)cluster.block_rank();
+  const bool lead = (c == 0 && tid == 0);
   if (st->done) {
-    if (tid == 0 && use_cond) cudaGraphSetConditional(cond, 0);
+    if (lead && use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
-  if (tid < 32) {  // h = argmin_j nu_j, lowest index on ties
-    const int j = tid;
-    double nv = (j < s) ? G2nu[npack(KP) + j] : __longlong_as_double(0x7ff0000000000000ll);
+  const bool ct = tid < CC::NT;
+  const int r = tid / KP, a = tid % KP, b = c + CC::CS * r;
+  if (ct) Sg[a * CC::CPC + r] = Sigma[a + b * KP];
+  ldl_init<KP>(W, G2nu, s);
+  if ((tid >> 5) == CC::IDLE) {  // a warp without early factorisation work decides the stopping test
+    const int j = tid & 31;  // h = argmin_j nu_j, lowest index on ties (nu >= 0: bit order = value order)
+    long long nv = (j < s) ? __double_as_longlong(G2nu[npack(KP) + j]) : 0x7FF0000000000000LL;
     int h = j;
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
-      const double ov = __shfl_xor_sync(kFull, nv, off);
+      const long long ov = __shfl_xor_sync(kFull, nv, off);
       const int oh = __shfl_xor_sync(kFull, h, off);
       if (ov < nv || (ov == nv && oh < h)) {
         nv = ov;
         h = oh;
       }
     }
-    if (tid == 0) {
-      const double nh = sqrt(nv);
-      st->best_col = h;
-      st->nu_h = nh;
-      stop = 0;
-      if (!st->no_test && nh < st->tol_abs) {
-        st->converged = 1;
-        st->done = 1;
-        st->pw_skip = 1;
-        st->status = 0;
-        stop = 1;
-        if (use_cond) cudaGraphSetConditional(cond, 0);
-      }
+    if (j == 0) {
+      nh_s = sqrt(__longlong_as_double(nv));
+      h_s = h;
+      stop_s = (!st->no_test && nh_s < st->tol_abs) ? 1 : 0;
     }
   }
-  __syncthreads();
-  if (stop) return;
-  cta_load_packed<KP>(G2nu, s, A);
-  if (!cta_chol<KP>(A, Z, s)) {
-    if (tid == 0) {
+  ldl_factor<KP>(W, s);
+  const double nh = nh_s;
+  const int h = h_s;
+  if (stop_s) {  // late CTAs may then find done set and return early: nothing of theirs is used
+    if (lead) {
+      st->best_col = h;
+      st->nu_h = nh;
+      st->converged = 1;
+      st->done = 1;
+      st->pw_skip = 1;
+      st->status = 0;
+      if (use_cond) cudaGraphSetConditional(cond, 0);
+    }
+    return;
+  }
+  if (W.bad) {
+    if (lead) {
+      st->best_col = h;
+      st->nu_h = nh;
       st->done = 1;
       st->pw_skip = 1;
       st->status = 6;
@@ -549,36 +761,20 @@ k_small_zeta_c(SolveState* st, const double* __restrict__ G2nu, double* __restri
     }
     return;
   }
-  cta_tri_inv<KP>(Z, Zi, Tmp);
-  for (int q = tid; q < KP * KP; q += kCtaSmall) {
-    const int a = q / KP, b = q % KP;
-    Tmp[a * LD + b] = Sigma[a + b * KP];
+  if (ct) {
+    const double ra = rsqrt_pos(W.d[a]);              // d_a^{-1/2}
+    const double rb = __shfl_sync(kFull, ra, b, KP);  // d_b^{-1/2} (lane b of this column's segment)
+    double v = 0.0;  // (zeta Sigma)[a][b] = d_a^{-1/2} sum_{l = a..b} U[a][l] Sigma[l][b]
+    for (int l = a; l <= b; ++l) v = fma(W.U[a * LD + l], Sg[l * CC::CPC + r], v);
+    const bool in = (a < s && b < s), up = in && a <= b;
+    Sigma[a + b * KP] = in ? v * ra : 0.0;
+    Zeta[a + b * KP] = up ? W.U[a * LD + b] * ra : 0.0;
+    ZetaInv[a + b * KP] = up ? W.R[b * LD + a] * rb : 0.0;
   }
-  __syncthreads();
-  {  // Sigma = zeta Sigma (both upper: a <= l <= b); R interleaved outputs per thread
-    constexpr int R = KP * KP / kCtaSmall > 0 ? KP * KP / kCtaSmall : 1;
-    const int a = tid % KP;
-    int b[R];
-    double v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      b[r] = (tid + r * kCtaSmall) / KP;
-      v[r] = 0.0;
-    }
-    if (tid + (R - 1) * kCtaSmall < KP * KP) {
-      for (int l = a; l <= b[R - 1]; ++l) {
-        const double za = Z[a * LD + l];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (l <= b[r]) v[r] = fma(za, Tmp[l * LD + b[r]], v[r]);
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) Sigma[a + b[r] * KP] = (a < s && b[r] < s) ? v[r] : 0.0;
-    }
-  }
-  cta_store<KP>(Zeta, Z, s);
-  cta_store<KP>(ZetaInv, Zi, s);
-  if (tid == 0) {
+  cluster.sync();  // every CTA has read the state before the leader updates it
+  if (lead) {
+    st->best_col = h;
+    st->nu_h = nh;
     int done = 0;
     if (st->it >= st->maxit) {
       done = 1;
@@ -592,7 +788,7 @@ k_small_zeta_c(SolveState* st, const double* __restrict__ G2nu, double* __restri
 
 // ------------------------------------------------------------------------------------ launchers
 
-// KP <= 8: one warp; KP >= 16: one CTA of 256 threads.
+// KP <= 8: one warp; KP >= 16: one CTA of 256 threads (setup) or a cluster of CTAs (loop).
 #define MBPCG_SMALL_SWITCH(kp, WARP, CTA) \
   switch (kp) {                           \
     case 1: WARP(1); break;               \
@@ -613,7 +809,7 @@ void launch_small_sigma(cudaStream_t s, int kp, SolveState* st, const double* Gp
 void launch_small_xi(cudaStream_t s, int kp, SolveState* st, const double* G1p, const double* Sigma, double* Xi,
                      double* T) {
 #define WARP(K) k_small_xi_w<K><<<1, 32, 0, s>>>(st, G1p, Sigma, Xi, T)
-#define CTA(K) k_small_xi_c<K><<<1, kCtaSmall, 0, s>>>(st, G1p, Sigma, Xi, T)
+#define CTA(K) k_small_xi_x<K><<<ClusterCfg<K>::CS, ClusterCfg<K>::NF, 0, s>>>(st, G1p, Sigma, Xi, T)
   MBPCG_SMALL_SWITCH(kp, WARP, CTA)
 #undef WARP
 #undef CTA
@@ -621,7 +817,8 @@ void launch_small_xi(cudaStream_t s, int kp, SolveState* st, const double* G1p, 
 void launch_small_zeta(cudaStream_t s, int kp, SolveState* st, const double* G2nu, double* Sigma, double* Zeta,
                        double* ZetaInv, cudaGraphConditionalHandle cond, int use_cond) {
 #define WARP(K) k_small_zeta_w<K><<<1, 32, 0, s>>>(st, G2nu, Sigma, Zeta, ZetaInv, cond, use_cond)
-#define CTA(K) k_small_zeta_c<K><<<1, kCtaSmall, 0, s>>>(st, G2nu, Sigma, Zeta, ZetaInv, cond, use_cond)
+#define CTA(K) \
+  k_small_zeta_x<K><<<ClusterCfg<K>::CS, ClusterCfg<K>::NF, 0, s>>>(st, G2nu, Sigma, Zeta, ZetaInv, cond, use_cond)
   MBPCG_SMALL_SWITCH(kp, WARP, CTA)
 #undef WARP
 #undef CTA
