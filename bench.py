@@ -39,7 +39,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 WORKLOADS = {
     "dense4096": dict(desc="dense SPD n=4096, A=Q diag(lambda) Q^T, lambda=10^U[0,6], b,U~U(-1,1), FP64, tol 1e-8",
-                      precond=0, tol=1e-8, s=16),
+                      precond=0, tol=1e-8, s=32),
     "poisson64": dict(desc="2D 5-point Poisson 64x64 (n=4096, nnz=20224), CSR int32/FP64, tol 1e-8",
                       precond=0, tol=1e-8, s=4),
     "diffusion128": dict(desc="3D 7-point variable-coefficient diffusion 128^3 (n=2097152, nnz=14581760), "
@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--kernel-launches", type=int, default=20, help="launches of the dominant kernel timed alone")
     p.add_argument("--cpu-sample-iters", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "tc"],
+    p.add_argument("--precision", default="tc", choices=["fp64", "tc"],
                    help="tc: dense product on the BF16 tensor cores by exact digit splitting (FP64 accuracy)")
     p.add_argument("--launch-mode", default="graph", choices=["graph", "eager"],
                    help="eager: host-launched loop (for profilers; same kernels and results)")
@@ -133,9 +133,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {
+    "k_dense": ("row_kernels.cuh", "mbpcg_device.cuh"),
+    "k_spmm": ("row_kernels.cuh", "mbpcg_device.cuh"),
+    "k_dense_tc": ("ozaki_tc.cu", "tcgen05.cuh", "tma.cuh", "mbpcg_device.cuh"),
+}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the sources a recorded ncu traffic figure was taken from (stale figures are dropped)."""
     h = hashlib.sha256()
-    for f in ("row_kernels.cuh", "mbpcg_device.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2608_07327_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -146,18 +154,21 @@ def recorded_traffic(kernel, workload, s):
     except (OSError, ValueError):
         return None
     rec = data.get(f"{kernel}:{workload}:s{s}")
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != kernel_source_hash(kernel):
         return None
     return rec.get("dram_bytes_per_launch")
 
 
-def launches_per_solve(info, dense, algo_cg):
-    """Kernels of ours launched by one solve call (the counter of the graph the library builds)."""
+def launches_per_solve(info, dense, algo_cg, tc=False):
+    """Kernels of ours launched by one solve call (the counter of the graph the library builds). The
+    tensor-core dense product is four kernels (column exponents, digits of P, MMAs, split sum)."""
     inner = info["restarts"] + 1
     if algo_cg:
         setup, exit_, body = 3, 5, 5
     else:
         setup, exit_, body = 8, 7, (8 if dense else 7)
+        if tc:
+            setup, body = setup + 3, body + 3
     return inner * (1 + setup + exit_) + body * info["iterations"] + (0 if algo_cg else 1)
 
 
@@ -325,7 +336,7 @@ def run_ours(args, world, rank, local):
             "roofline": roofline,
             "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": 8 * n + 8 * n * s,
                     "d2h_bytes_per_step": 8 * n + 200 * (info["restarts"] + 1)},
-            "gpu_launches": sum(launches_per_solve(i, dense, False) for i in infos),
+            "gpu_launches": sum(launches_per_solve(i, dense, False, prec == mb.MBPCG_FP64_TC) for i in infos),
             "clocks": clk.summary(),
         }
     solver.close()
