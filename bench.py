@@ -63,7 +63,11 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="dense4096", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="dense4096", choices=sorted(WORKLOADS) + ["serving"])
+    p.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
+    p.add_argument("--slots", type=int, default=8, help="serving: solves admitted at once")
+    p.add_argument("--compare-requests", type=int, default=400,
+                   help="serving: requests of the same stream also served one at a time (0: skip)")
     p.add_argument("--s", type=int, default=None)
     p.add_argument("--kernel-launches", type=int, default=20, help="launches of the dominant kernel timed alone")
     p.add_argument("--cpu-sample-iters", type=int, default=6)
@@ -398,10 +402,134 @@ def run_reference(args, world, rank):
             "e2e": {"value": round(ms, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+SERVING_DESC = ("stream of requests, Poisson arrivals at 0.7x the measured single-stream solve rate; each a 2D/3D "
+                "Poisson (no scaling) or 3D diffusion (Jacobi) CSR system, n log-uniform in [1e3,1e6] (24 grid sides "
+                "per kind), s uniform in {1,4,8,16}, tol 1e-8, FP64; b from SplitMix64 per request")
+
+
+class MatrixCache:
+    """Matrices of the request stream, generated once per (kind, grid side)."""
+
+    def __init__(self):
+        self.mats = {}
+
+    def get(self, kind, m):
+        key = (kind, m)
+        if key not in self.mats:
+            if kind == "poisson2d":
+                self.mats[key] = wl.poisson2d(m)
+            elif kind == "poisson3d":
+                self.mats[key] = wl.poisson3d(m)
+            else:
+                self.mats[key] = wl.diffusion3d(m, m)
+        return self.mats[key]
+
+
+def serve_stream(mb, reqs, cache, rhs, arrivals, slots):
+    """Submit every request at its arrival time (seconds from start) to a server with `slots`
+    slots; a second thread waits for the tickets. Returns per-request latency (s) and results."""
+    import threading
+    srv = mb.Server(slots=slots)
+    tickets = [None] * len(reqs)
+    results = [None] * len(reqs)
+    ready = threading.Semaphore(0)
+
+    def waiter():
+        for i in range(len(reqs)):
+            ready.acquire()
+            results[i] = srv.wait(tickets[i])
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    lag = []
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        delay = arrivals[i] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        lag.append(max(0.0, -delay))
+        A = cache.get(r["kind"], r["m"])
+        tickets[i] = srv.submit(A, rhs[i], s=r["s"], precond=r["precond"], algo=0, tol=1e-8, maxit=200000,
+                                seed=r["rhs_seed"])
+        ready.release()
+    th.join()
+    makespan = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([res["queue_s"] + res["run_s"] for res in results])
+    return lat, results, makespan, stats, float(np.max(lag))
+
+
+def run_serving(args, world, rank):
+    import torch
+    import paper_2608_07327_gb300 as mb
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    mb.lib()
+    reqs = wl.serving_requests(args.requests, 0)
+    cache = MatrixCache()
+    rhs = [wl.rhs(r["n"], r["rhs_seed"]) for r in reqs]
+    for r in reqs:
+        cache.get(r["kind"], r["m"])
+    # single-stream rate: a seeded sample of the stream served one at a time (after a warm-up)
+    rng = np.random.default_rng(1)
+    sample = sorted(rng.choice(len(reqs), size=min(60, len(reqs)), replace=False))
+    warm = [reqs[i] for i in sample[:3]]
+    serve_stream(mb, warm, cache, [rhs[i] for i in sample[:3]], [0.0] * 3, 1)
+    s_lat, s_res, s_span, _, _ = serve_stream(mb, [reqs[i] for i in sample], cache, [rhs[i] for i in sample],
+                                              [0.0] * len(sample), 1)
+    mean_service = float(np.mean([res["run_s"] for res in s_res]))
+    rate = 0.7 / mean_service
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    arrivals -= arrivals[0]
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with clk:
+        lat, res, span, stats, lag = serve_stream(mb, reqs, cache, rhs, arrivals, args.slots)
+    seq = None
+    if args.compare_requests > 0:
+        m = min(args.compare_requests, len(reqs))
+        q_lat, q_res, q_span, _, _ = serve_stream(mb, reqs[:m], cache, rhs[:m], arrivals[:m], 1)
+        b_lat = lat[:m]
+        seq = {"requests": m, "slots": 1, "p50_ms": round(float(np.percentile(q_lat, 50)) * 1e3, 3),
+               "p99_ms": round(float(np.percentile(q_lat, 99)) * 1e3, 3),
+               "batched_p50_ms_same_requests": round(float(np.percentile(b_lat, 50)) * 1e3, 3),
+               "batched_p99_ms_same_requests": round(float(np.percentile(b_lat, 99)) * 1e3, 3),
+               "identical_results": bool(all(np.array_equal(a["x"], b["x"]) for a, b in zip(q_res, res[:m])))}
+    statuses = [r["status"] for r in res]
+    relres = max(r["info"]["relres_true"] for r in res)
+    launches = sum(launches_per_solve(r["info"], False, False) for r in res)
+    h2d = float(np.mean([cache.get(q["kind"], q["m"]).nnz * 12 + (q["n"] + 1) * 4 + q["n"] * 8 for q in reqs]))
+    p99 = float(np.percentile(lat, 99)) * 1e3
+    line = {
+        "metric": "serving p99 latency (submit to result), continuous batching", "value": round(p99, 3),
+        "unit": "ms", "n_gpus": world, "steps": len(reqs), "warmup": 3, "ms_per_step": round(float(np.mean(lat)) * 1e3, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": SERVING_DESC, "requests": len(reqs), "slots": args.slots,
+                   "arrival_rate_per_s": round(rate, 3), "single_stream_mean_solve_ms": round(mean_service * 1e3, 3),
+                   "parallelism": "replicas only" if world > 1 else "single GPU",
+                   "l2": "inputs differ per request (n up to 1e6); no flush"},
+        "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3), "p99_ms": round(p99, 3),
+        "mean_ms": round(float(np.mean(lat)) * 1e3, 3), "solves_per_s": round(len(reqs) / span, 3),
+        "makespan_s": round(span, 3), "max_submit_lag_ms": round(lag * 1e3, 3),
+        "failed": int(sum(1 for x in statuses if x != 0)), "max_relres_true": relres,
+        "peak_active": stats["peak_active"], "peak_bytes": stats["peak_bytes"],
+        "sequential": seq,
+        "e2e": {"value": round(p99, 3), "unit": "ms", "h2d_bytes_per_step": round(h2d), "d2h_bytes_per_step":
+                round(float(np.mean([q["n"] * 8 for q in reqs])))},
+        "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    return line if rank == 0 else None
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
-    if args.impl == "reference":
+    if args.workload == "serving":
+        line = None if args.impl == "reference" else run_serving(args, world, rank)
+        if args.impl == "reference":
+            line = {"impl": "reference", "unavailable": "the oracle solves one system at a time; the serving "
+                    "stream has no CPU reference arm"} if rank == 0 else None
+    elif args.impl == "reference":
         line = run_reference(args, world, rank)
     else:
         line = run_ours(args, world, rank, local)
@@ -413,7 +541,8 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1 and args.impl != "reference":
         import torch.distributed as dist
-        dist.destroy_process_group()
+        if dist.is_initialized():
+            dist.destroy_process_group()
 
 
 if __name__ == "__main__":

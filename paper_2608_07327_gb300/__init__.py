@@ -17,7 +17,55 @@ from ._native import (  # noqa: F401  (re-exported C ABI names)
     MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,
     MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_FP64_TC, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER)
 
-__all__ = ["Solver", "Info", "MBPCGError", "lib", "lib_path"]
+from ._native import (  # noqa: F401,E402
+    mbpcg_server_create, mbpcg_server_destroy, mbpcg_server_get_stats, mbpcg_server_submit_csr, mbpcg_server_wait)
+
+__all__ = ["Solver", "Server", "Info", "MBPCGError", "lib", "lib_path"]
+
+
+class Server:
+    """The library's continuous-batching request server (include/mbpcg_server.h): up to `slots`
+    solves run at once, each on its own stream, admitted first come first served while a slot is
+    free and its workspace fits in `hbm_budget_bytes` (0 = 85 % of the free device memory).
+    ``submit`` returns a ticket at once; ``wait`` returns the result of a ticket. The arrays of a
+    request are kept alive here until its ticket is waited for."""
+
+    def __init__(self, slots: int = 8, hbm_budget_bytes: int = 0):
+        self._srv = _native.mbpcg_server_create(slots, hbm_budget_bytes)
+        self._keep = {}
+
+    def submit(self, A, b, s: int = 4, precond: int = 0, algo: int = 0, tol: float = 1e-8, maxit: int = 100000,
+               seed: int = 0) -> int:
+        rp = np.ascontiguousarray(A.row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+        v = np.ascontiguousarray(A.val, dtype=np.float64)
+        bb = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty(int(A.n), dtype=np.float64)
+        t = _native.mbpcg_server_submit_csr(self._srv, int(A.n), int(v.size), rp, ci, v, bb, s, precond, algo, tol,
+                                            maxit, seed, x)
+        self._keep[t] = (rp, ci, v, bb, x)
+        return t
+
+    def wait(self, ticket: int) -> dict:
+        """{status, x, info, queue_s, run_s}: blocks until the request has finished."""
+        st, info, q, r = _native.mbpcg_server_wait(self._srv, ticket)
+        x = self._keep.pop(ticket)[4]
+        return {"status": st, "x": x, "info": info.as_dict(), "queue_s": q, "run_s": r}
+
+    def stats(self) -> dict:
+        return _native.mbpcg_server_get_stats(self._srv)
+
+    def close(self):
+        if self._srv is not None:
+            _native.mbpcg_server_destroy(self._srv)
+            self._srv = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Solver:

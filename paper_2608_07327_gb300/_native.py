@@ -46,6 +46,23 @@ class Info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class ServerStats(ctypes.Structure):
+    """mbpcg_server_stats."""
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("failed", ctypes.c_int64),
+        ("active", ctypes.c_int32),
+        ("peak_active", ctypes.c_int32),
+        ("used_bytes", ctypes.c_uint64),
+        ("peak_bytes", ctypes.c_uint64),
+        ("budget_bytes", ctypes.c_uint64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class MBPCGError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -83,6 +100,12 @@ _SIGS = {
     "mbpcg_k_spmm_gram_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "mbpcg_k_spmm": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
     "mbpcg_k_dense_product": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P]),
+    "mbpcg_server_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, ctypes.c_uint64]),
+    "mbpcg_server_submit_csr": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _P, _I32, _I32, _I32, _D, _I32,
+                                               ctypes.c_uint64, _P, ctypes.POINTER(_I64)]),
+    "mbpcg_server_wait": (ctypes.c_int, [_P, _I64, ctypes.POINTER(Info), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "mbpcg_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "mbpcg_server_destroy": (None, [_P]),
 }
 
 _lock = threading.Lock()
@@ -227,3 +250,42 @@ def mbpcg_k_dense_tc_product(n, s, P, AP, scratch, scratch_bytes, stream=None):
 
 def mbpcg_k_cholesky(s, G, Z, status_dev, stream=None):
     return lib().mbpcg_k_cholesky(s, ptr(G), ptr(Z), ptr(status_dev), stream)
+
+
+def mbpcg_server_create(slots, hbm_budget_bytes=0):
+    srv = _P()
+    st = lib().mbpcg_server_create(ctypes.byref(srv), slots, hbm_budget_bytes)
+    if st != MBPCG_OK:
+        raise MBPCGError(st, "mbpcg_server_create")
+    return srv
+
+
+def mbpcg_server_submit_csr(srv, n, nnz, row_ptr, col_idx, vals, b, s, precond, algo, tol, maxit, seed, x_out):
+    """Queue one solve; the arrays (host) must stay alive and unchanged until the ticket is waited for."""
+    t = _I64()
+    st = lib().mbpcg_server_submit_csr(srv, n, nnz, ptr(row_ptr), ptr(col_idx), ptr(vals), ptr(b), s, precond, algo,
+                                       tol, maxit, seed, ptr(x_out), ctypes.byref(t))
+    if st != MBPCG_OK:
+        raise MBPCGError(st, "mbpcg_server_submit_csr")
+    return int(t.value)
+
+
+def mbpcg_server_wait(srv, ticket):
+    """(status, Info, queue_seconds, run_seconds) of a finished request; blocks until it ends."""
+    info = Info()
+    q = _D()
+    r = _D()
+    st = lib().mbpcg_server_wait(srv, ticket, ctypes.byref(info), ctypes.byref(q), ctypes.byref(r))
+    return st, info, q.value, r.value
+
+
+def mbpcg_server_get_stats(srv) -> dict:
+    out = ServerStats()
+    st = lib().mbpcg_server_get_stats(srv, ctypes.byref(out))
+    if st != MBPCG_OK:
+        raise MBPCGError(st, "mbpcg_server_get_stats")
+    return out.as_dict()
+
+
+def mbpcg_server_destroy(srv):
+    lib().mbpcg_server_destroy(srv)

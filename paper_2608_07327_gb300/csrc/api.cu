@@ -160,7 +160,7 @@ struct mbpcg_ctx {
   double *part, *red;
   double *Sigma, *SigmaInv, *Xi, *T, *Zeta, *ZetaInv, *c, *Gtmp;
   SolveState* st;
-  SolveState* st_host;  // pinned
+  SolveState* st_host;  // host copy of the solve state (pageable: no device-wide synchronisation on free)
   uint8_t *oz_a, *oz_p;
   int *oz_ea, *oz_ep;
   double* oz_q;
@@ -284,7 +284,8 @@ int alloc_handle(mbpcg_ctx** out, const Dims& dm, int s, int precond, int algo, 
     }
     h->own_ws = 1;
   }
-  CUDA_TRY(cudaMallocHost(&h->st_host, sizeof(SolveState)));
+  h->st_host = new (std::nothrow) SolveState;
+  if (!h->st_host) return set_err(MBPCG_ERR_OOM, "host allocation failed");
   CUDA_TRY(cudaEventCreate(&h->e0));
   CUDA_TRY(cudaEventCreate(&h->e1));
   bind(h);
@@ -297,7 +298,7 @@ void release(mbpcg_ctx* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph_ready) cudaGraphExecDestroy(h->exec);
   if (h->own_ws && h->ws) cudaFree(h->ws);
-  if (h->st_host) cudaFreeHost(h->st_host);
+  delete h->st_host;
   if (h->e0) cudaEventDestroy(h->e0);
   if (h->e1) cudaEventDestroy(h->e1);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

@@ -139,6 +139,42 @@ def poisson2d(m: int) -> CSR:
     return _csr_from_entries(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 
 
+def poisson3d(m: int) -> CSR:
+    """3D 7-point Poisson Laplacian on an m^3 interior grid, Dirichlet: diagonal 6, neighbours -1.
+    n = m^3, nnz = 7 m^3 - 6 m^2."""
+    n = m ** 3
+    idx = np.arange(n, dtype=np.int64)
+    z, y, x = idx // (m * m), (idx // m) % m, idx % m
+    rows, cols, vals = [idx], [idx], [np.full(n, 6.0)]
+    for dz, dy, dx in ((-1, 0, 0), (0, -1, 0), (0, 0, -1), (0, 0, 1), (0, 1, 0), (1, 0, 0)):
+        ok = ((z + dz >= 0) & (z + dz < m) & (y + dy >= 0) & (y + dy < m) & (x + dx >= 0) & (x + dx < m))
+        rows.append(idx[ok])
+        cols.append(idx[ok] + dz * m * m + dy * m + dx)
+        vals.append(np.full(int(ok.sum()), -1.0))
+    return _csr_from_entries(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def serving_requests(count: int, seed: int, n_lo: float = 1e3, n_hi: float = 1e6, sizes: int = 24):
+    """A stream of solve requests shaped like the serving workload: kind in {2D Poisson, 3D Poisson,
+    3D diffusion (Jacobi)} uniformly, n log-uniform in [n_lo, n_hi] rounded to the nearest of
+    `sizes` log-spaced grid sides per kind (so matrices can be cached), s uniform in {1, 4, 8, 16}.
+    Returns dicts (kind, m, n, s, precond, rhs_seed); draws from streams 7000-7002 of `seed`."""
+    u_kind = uniform01(seed, 7000, count)
+    u_n = uniform01(seed, 7001, count)
+    u_s = uniform01(seed, 7002, count)
+    out = []
+    for i in range(count):
+        kind = ("poisson2d", "poisson3d", "diffusion3d")[min(int(u_kind[i] * 3), 2)]
+        n = n_lo * (n_hi / n_lo) ** u_n[i]
+        dim = 2 if kind == "poisson2d" else 3
+        lo, hi = n_lo ** (1.0 / dim), n_hi ** (1.0 / dim)
+        grid = np.unique(np.round(lo * (hi / lo) ** np.linspace(0.0, 1.0, sizes)).astype(int))
+        m = int(grid[np.argmin(np.abs(np.log(grid) - np.log(n) / dim))])
+        s = (1, 4, 8, 16)[min(int(u_s[i] * 4), 3)]
+        out.append(dict(kind=kind, m=m, n=m ** dim, s=s, precond=1 if kind == "diffusion3d" else 0, rhs_seed=i + 1))
+    return out
+
+
 def conductivity(m: int, seed: int) -> np.ndarray:
     """Per-cell conductivity kappa = 10^U[-2,2] on an m^3 grid (stream 1000)."""
     return 10.0 ** (4.0 * uniform01(seed, 1000, m ** 3) - 2.0)
