@@ -39,11 +39,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 WORKLOADS = {
     "dense4096": dict(desc="dense SPD n=4096, A=Q diag(lambda) Q^T, lambda=10^U[0,6], b,U~U(-1,1), FP64, tol 1e-8",
-                      precond=0, tol=1e-8, s=32),
+                      precond=0, tol=1e-8, s=32, precision="tc"),
     "poisson64": dict(desc="2D 5-point Poisson 64x64 (n=4096, nnz=20224), CSR int32/FP64, tol 1e-8",
                       precond=0, tol=1e-8, s=4),
     "diffusion128": dict(desc="3D 7-point variable-coefficient diffusion 128^3 (n=2097152, nnz=14581760), "
                               "Jacobi scaling, tol 1e-8", precond=1, tol=1e-8, s=4),
+    "stencil27_96": dict(desc="3D 27-point stencil 96^3 (n=884736, nnz=23393656), off-diagonals -U[0,1) per edge, "
+                              "diagonal sum|off|+1e-2; FP32 blocks/SpMM with FP32 accumulation, FP64-class Grams, "
+                              "FP64 k x k and FP64 refinement to relres 1e-10", precond=0, tol=1e-10, s=16,
+                         precision="mixed"),
 }
 
 
@@ -54,6 +58,8 @@ def make_matrix(name):
         return wl.poisson2d(64)
     if name == "diffusion128":
         return wl.diffusion3d(128, 0)
+    if name == "stencil27_96":
+        return wl.stencil27(96, 0)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -72,8 +78,9 @@ def parse():
     p.add_argument("--kernel-launches", type=int, default=20, help="launches of the dominant kernel timed alone")
     p.add_argument("--cpu-sample-iters", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--precision", default="tc", choices=["fp64", "tc"],
-                   help="tc: dense product on the BF16 tensor cores by exact digit splitting (FP64 accuracy)")
+    p.add_argument("--precision", default=None, choices=["fp64", "tc", "mixed"],
+                   help="tc: dense product on the BF16 tensor cores by exact digit splitting (FP64 accuracy); "
+                        "mixed: FP32 inner solves in FP64 refinement (CSR); default: the workload's own")
     p.add_argument("--launch-mode", default="graph", choices=["graph", "eager"],
                    help="eager: host-launched loop (for profilers; same kernels and results)")
     return p.parse_args()
@@ -163,14 +170,15 @@ def recorded_traffic(kernel, workload, s):
     return rec.get("dram_bytes_per_launch")
 
 
-def launches_per_solve(info, dense, algo_cg, tc=False):
+def launches_per_solve(info, dense, algo_cg, tc=False, mixed=False):
     """Kernels of ours launched by one solve call (the counter of the graph the library builds). The
-    tensor-core dense product is four kernels (column exponents, digits of P, MMAs, split sum)."""
+    tensor-core dense product is four kernels (column exponents, digits of P, MMAs, split sum); the
+    mixed-precision loop runs its Gram as a kernel of its own."""
     inner = info["restarts"] + 1
     if algo_cg:
         setup, exit_, body = 3, 5, 5
     else:
-        setup, exit_, body = 8, 7, (8 if dense else 7)
+        setup, exit_, body = 8, 7, (8 if (dense or mixed) else 7)
         if tc:
             setup, body = setup + 3, body + 3
     return inner * (1 + setup + exit_) + body * info["iterations"] + (0 if algo_cg else 1)
@@ -193,8 +201,16 @@ def run_ours(args, world, rank, local):
     U = wl.initial_block(n, s, 1)
     dev = torch.device("cuda", local)
     mode = mb.MBPCG_LAUNCH_EAGER if args.launch_mode == "eager" else mb.MBPCG_LAUNCH_GRAPH
-    prec = mb.MBPCG_FP64_TC if (args.precision == "tc" and isinstance(A, wl.Dense)) else mb.MBPCG_FP64
+    pname = args.precision or cfg.get("precision", "fp64")
+    if pname == "tc" and dense:
+        prec = mb.MBPCG_FP64_TC
+    elif pname == "mixed" and not dense:
+        prec = mb.MBPCG_MIXED_FP32
+    else:
+        prec, pname = mb.MBPCG_FP64, "fp64"
+    mixed = prec == mb.MBPCG_MIXED_FP32
     solver = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode, precision=prec)
+    fp64 = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode) if mixed else None
     cg = mb.Solver(A, algo=mb.MBPCG_ALGO_CG, precond=cfg["precond"], launch_mode=mode)
     stream = solver.stream
     bd = torch.as_tensor(b, device=dev)
@@ -209,7 +225,7 @@ def run_ours(args, world, rank, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(sv.stream)
-            x, info = sv.solve(bd, Uarg, tol=cfg["tol"])
+            x, info = sv.solve(bd, Uarg, tol=cfg["tol"], maxit=400000)
             e1.record(sv.stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -224,6 +240,8 @@ def run_ours(args, world, rank, local):
 
     timed(solver, Ud, args.warmup)
     timed(cg, None, max(1, min(args.warmup, 2)))
+    if fp64 is not None:
+        timed(fp64, Ud, 1)
     barrier()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
@@ -232,6 +250,9 @@ def run_ours(args, world, rank, local):
         wall = time.perf_counter() - t0
         cg_times, cg_infos, xc = timed(cg, None, args.steps)
         barrier()
+        if fp64 is not None:
+            f_times, f_infos, xf = timed(fp64, Ud, max(1, min(args.steps, 2)))
+            barrier()
     total_ms = sum(times)
     cg_total = sum(cg_times)
     if world > 1:
@@ -265,6 +286,21 @@ def run_ours(args, world, rank, local):
         kname = "k_dense"
         flops = 2.0 * n * n * s
         nbytes = 8.0 * n * n + 16.0 * n * kp
+    elif mixed:
+        rp = torch.as_tensor(A.row_ptr, device=dev)
+        ci = torch.as_tensor(A.col_idx, device=dev)
+        av = torch.as_tensor(A.val.astype(np.float32), device=dev)
+        P = P.float()
+        AP = torch.empty_like(P)
+        launch = lambda: mb.mbpcg_k_spmm_f32(n, rp, ci, av, s, P, AP, stream.cuda_stream)  # noqa: E731
+        kname = "k_spmm_f"
+        flops = 2.0 * A.nnz * s
+        nbytes = 8.0 * A.nnz + 4.0 * (n + 1) + 8.0 * n * kp  # FP32 values + int32 indices, P in, AP out
+        gb = mb.mbpcg_k_scratch_bytes(n, s)
+        gscr = torch.empty(gb, dtype=torch.uint8, device=dev)
+        Gd = torch.empty((s, s), dtype=torch.float64, device=dev)
+        launch_gram = lambda: mb.mbpcg_k_spmm_gram_f32(n, rp, ci, av, s, P, AP, Gd, gscr, gb,  # noqa: E731
+                                                       stream.cuda_stream)
     else:
         rp = torch.as_tensor(A.row_ptr, device=dev)
         ci = torch.as_tensor(A.col_idx, device=dev)
@@ -288,7 +324,32 @@ def run_ours(args, world, rank, local):
             k_ms.append(ev0.elapsed_time(ev1))
     k_avg = sum(k_ms) / len(k_ms)
     achieved_tflops = flops / (k_avg * 1e-3) / 1e12
-    if tc:
+    gram_ms = None
+    if mixed:
+        with torch.cuda.stream(stream):
+            g_ms = []
+            for _ in range(max(3, args.kernel_launches // 2)):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                launch_gram()
+                ev1.record(stream)
+                ev1.synchronize()
+                g_ms.append(ev0.elapsed_time(ev1))
+        gram_ms = sum(g_ms) / len(g_ms)
+    if mixed:
+        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        achieved_gbs = nbytes / (k_avg * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"{kname}<{kp}> (FP32 SpMM, the product alone)",
+                    "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(achieved_gbs / hbm_peak, 4), "traffic": recorded_traffic(kname, args.workload, s),
+                    "kernel_ms": round(k_avg, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
+                    "with_gram_ms": round(gram_ms, 5),
+                    "with_gram_frac": round(nbytes / (gram_ms * 1e-3) / 1e9 / hbm_peak, 4),
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+    elif tc:
         peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
         hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
         achieved_gbs = nbytes / (k_avg * 1e-3) / 1e9
@@ -325,10 +386,10 @@ def run_ours(args, world, rank, local):
         line = {
             "metric": METRIC, "value": round(ms_per_step, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
             "config": {"workload": cfg["desc"], "n": n, "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
                        "tol": cfg["tol"], "l2": "flushed before every step (256 MB write)",
-                       "launch_mode": args.launch_mode, "precision": args.precision,
+                       "launch_mode": args.launch_mode, "precision": pname,
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "iterations": info["iterations"], "restarts": info["restarts"], "relres_true": relres_check,
             "cg_ms": round(cg_ms, 4), "cg_iterations": cg_infos[-1]["iterations"],
@@ -340,11 +401,20 @@ def run_ours(args, world, rank, local):
             "roofline": roofline,
             "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": 8 * n + 8 * n * s,
                     "d2h_bytes_per_step": 8 * n + 200 * (info["restarts"] + 1)},
-            "gpu_launches": sum(launches_per_solve(i, dense, False, prec == mb.MBPCG_FP64_TC) for i in infos),
+            "gpu_launches": sum(launches_per_solve(i, dense, False, prec == mb.MBPCG_FP64_TC, mixed) for i in infos),
             "clocks": clk.summary(),
         }
+        if fp64 is not None:
+            f_ms = sum(f_times) / len(f_times)
+            xfh = xf.cpu().numpy()
+            line["fp64_mbpcg"] = {"ms": round(f_ms, 4), "iterations": f_infos[-1]["iterations"],
+                                  "restarts": f_infos[-1]["restarts"], "relres_true": f_infos[-1]["relres_true"]}
+            line["speedup_vs_fp64_mbpcg"] = round(f_ms / ms_per_step, 4)
+            line["rel_diff_to_fp64_solution"] = float(np.linalg.norm(xh - xfh) / np.linalg.norm(xfh))
     solver.close()
     cg.close()
+    if fp64 is not None:
+        fp64.close()
     return line
 
 

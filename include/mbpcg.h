@@ -59,10 +59,17 @@ typedef enum { MBPCG_PRECOND_NONE = 0, MBPCG_PRECOND_JACOBI = 1 } mbpcg_precond;
 typedef enum { MBPCG_ALGO_MBPCG = 0, MBPCG_ALGO_CG = 1 } mbpcg_algo;
 
 /* Arithmetic of the n-proportional work. FP64: everything in double precision on the FP64 pipe.
+ * MIXED_FP32 (CSR A, MBPCG only): the inner solves keep the n x s blocks and the (scaled) matrix
+ * values in FP32 and do the products and block updates in FP32 with FP32 accumulation; the s x s
+ * Grams and norms are accumulated with FP64-class accuracy (compensated FP32 dot products, Ogita,
+ * Rump & Oishi 2005), the s x s Cholesky steps run in FP64, and the true residual b - A x and x
+ * itself are FP64: the true-residual restarts are an FP64 iterative refinement loop (at most 12
+ * correction solves, each asked for at most 1e-5 relative reduction). Results therefore differ from
+ * the FP64 path; the requested tol is still checked on the FP64 true residual.
  * FP64_TC (dense A, MBPCG only): the same FP64 solve, but the product A P runs on the BF16 tensor
  * cores by exact splitting of A and P into 8 base-128 digits (Ozaki scheme); its result has the
  * accuracy of an FP64 product. The digits of A take 16 bytes per entry of workspace. */
-typedef enum { MBPCG_FP64 = 0, MBPCG_FP64_TC = 2 } mbpcg_precision;
+typedef enum { MBPCG_FP64 = 0, MBPCG_MIXED_FP32 = 1, MBPCG_FP64_TC = 2 } mbpcg_precision;
 
 typedef struct {
   int32_t iterations;        /* inner iterations summed over restarts */

@@ -51,6 +51,20 @@ int mbpcg_k_spmm_gram_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* 
                               const double* vals, int32_t s, const double* P, double* AP,
                               double* G, void* stream);
 
+/*
+ * The FP32 form used by the mixed-precision inner solve (MBPCG_MIXED_FP32): vals, P and AP are
+ * FP32 (P, AP row-major n x KP as above), AP = A P with FP32 accumulation, and G = P^T (A P) (s x s
+ * FP64) accumulated from the FP32 values with compensated dot products (Ogita, Rump & Oishi 2005:
+ * as accurate as a sum in twice FP32's precision). Scratch and errors as mbpcg_k_spmm_gram.
+ * mbpcg_k_spmm_f32 is the product alone (no Gram, no scratch), in the solver's launch
+ * configuration, for timing.
+ */
+int mbpcg_k_spmm_gram_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const float* vals,
+                          int32_t s, const float* P, float* AP, double* G, void* scratch,
+                          size_t scratch_bytes, void* stream);
+int mbpcg_k_spmm_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const float* vals,
+                     int32_t s, const float* P, float* AP, void* stream);
+
 /* Same for dense symmetric A (column-major n x n; row i is read as column i). */
 int mbpcg_k_dense_gram(int32_t n, const double* A, int32_t s, const double* P, double* AP,
                        double* G, void* scratch, size_t scratch_bytes, void* stream);

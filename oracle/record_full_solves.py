@@ -5,6 +5,7 @@ the number of iterations the oracle needs for the whole solve; that number comes
 which calls only the oracle and the shared input generators, and writes full_solve_counts.json.
 
     python oracle/record_full_solves.py dense4096 8 16 32 cg
+    python oracle/record_full_solves.py stencil27_96 16 cg
 """
 from __future__ import annotations
 
@@ -27,6 +28,8 @@ def load_workload(name):
         return wl.dense_spd(4096, 0), 0, 1e-8
     if name == "poisson64":
         return wl.poisson2d(64), 0, 1e-8
+    if name == "stencil27_96":
+        return wl.stencil27(96, 0), 0, 1e-10
     raise SystemExit(f"unknown workload {name}")
 
 

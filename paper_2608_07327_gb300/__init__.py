@@ -15,7 +15,8 @@ from ._native import (  # noqa: F401  (re-exported C ABI names)
     mbpcg_k_dense_gram, mbpcg_k_dense_product, mbpcg_k_dense_tc_prepare, mbpcg_k_dense_tc_product, mbpcg_k_dense_tc_scratch_bytes, mbpcg_k_spmm, mbpcg_k_spmm_gram_noalloc, mbpcg_k_padded_width, mbpcg_k_scratch_bytes, mbpcg_k_spmm_gram, mbpcg_run_iterations_dev,
     mbpcg_set_launch_mode, mbpcg_solve, mbpcg_solve_dev, mbpcg_workspace_size_csr, mbpcg_workspace_size_dense, status_string, last_error,
     MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,
-    MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_FP64_TC, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER)
+    MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_FP64_TC, MBPCG_MIXED_FP32, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER,
+    mbpcg_k_spmm_gram_f32, mbpcg_k_spmm_f32)
 
 from ._native import (  # noqa: F401,E402
     mbpcg_server_create, mbpcg_server_destroy, mbpcg_server_get_stats, mbpcg_server_submit_csr, mbpcg_server_wait)
@@ -90,7 +91,7 @@ class Solver:
         if self.dense:
             nbytes = mbpcg_workspace_size_dense(self.n, self.s, algo, precision)
         else:
-            nbytes = mbpcg_workspace_size_csr(self.n, int(A.row_ptr[-1]), self.s, algo)
+            nbytes = mbpcg_workspace_size_csr(self.n, int(A.row_ptr[-1]), self.s, algo, precision)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         if self.dense:
             a = np.asfortranarray(A.a, dtype=np.float64)
@@ -100,7 +101,7 @@ class Solver:
             rp = np.ascontiguousarray(A.row_ptr, dtype=np.int32)
             ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
             v = np.ascontiguousarray(A.val, dtype=np.float64)
-            self.h = mbpcg_create_csr(self.n, int(rp[-1]), rp, ci, v, self.s, precond, algo, 0, seed, 0,
+            self.h = mbpcg_create_csr(self.n, int(rp[-1]), rp, ci, v, self.s, precond, algo, precision, seed, 0,
                                       self.workspace, nbytes, self.stream.cuda_stream)
         if launch_mode != MBPCG_LAUNCH_GRAPH:
             st = mbpcg_set_launch_mode(self.h, launch_mode)

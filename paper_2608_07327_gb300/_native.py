@@ -22,6 +22,7 @@ MBPCG_PRECOND_JACOBI = 1
 MBPCG_ALGO_MBPCG = 0
 MBPCG_ALGO_CG = 1
 MBPCG_FP64 = 0
+MBPCG_MIXED_FP32 = 1
 MBPCG_FP64_TC = 2
 MBPCG_LAUNCH_GRAPH = 0
 MBPCG_LAUNCH_EAGER = 1
@@ -99,6 +100,8 @@ _SIGS = {
     "mbpcg_k_dense_tc_product": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_spmm_gram_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "mbpcg_k_spmm": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
+    "mbpcg_k_spmm_gram_f32": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "mbpcg_k_spmm_f32": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
     "mbpcg_k_dense_product": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P]),
     "mbpcg_server_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, ctypes.c_uint64]),
     "mbpcg_server_submit_csr": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _P, _I32, _I32, _I32, _D, _I32,
@@ -230,6 +233,15 @@ def mbpcg_k_dense_gram(n, A, s, P, AP, G, scratch, scratch_bytes, stream=None):
 
 def mbpcg_k_spmm(n, row_ptr, col_idx, vals, s, P, AP, stream=None):
     return lib().mbpcg_k_spmm(n, ptr(row_ptr), ptr(col_idx), ptr(vals), s, ptr(P), ptr(AP), stream)
+
+
+def mbpcg_k_spmm_gram_f32(n, row_ptr, col_idx, vals, s, P, AP, G, scratch, scratch_bytes, stream=None):
+    return lib().mbpcg_k_spmm_gram_f32(n, ptr(row_ptr), ptr(col_idx), ptr(vals), s, ptr(P), ptr(AP), ptr(G),
+                                       ptr(scratch), scratch_bytes, stream)
+
+
+def mbpcg_k_spmm_f32(n, row_ptr, col_idx, vals, s, P, AP, stream=None):
+    return lib().mbpcg_k_spmm_f32(n, ptr(row_ptr), ptr(col_idx), ptr(vals), s, ptr(P), ptr(AP), stream)
 
 
 def mbpcg_k_dense_product(n, A, s, P, AP, stream=None):

@@ -40,12 +40,15 @@ int set_err(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr size_t kAlign = 256;
+constexpr int kMixedRestarts = 12;       // refinement steps of the mixed-precision solve
+constexpr double kMixedInnerTol = 1e-5;  // smallest relative tolerance asked of an FP32 inner solve
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Dims {
   int n, kp, nb, nb_dense, nbmax, pstride;
   long long nnz;
   int dense, algo, tc, sms;
+  int mixed;  // MBPCG_MIXED_FP32: FP32 blocks and values in the inner solve
 };
 
 int num_sms() {
@@ -70,8 +73,18 @@ Dims make_dims(int n, long long nnz, int s, int algo, int dense, int sms) {
   d.nbmax = d.nb > d.nb_dense ? d.nb : d.nb_dense;
   d.pstride = (npack(d.kp) + d.kp + 1 + 3) / 4 * 4;
   d.tc = 0;
+  d.mixed = 0;
   d.sms = sm;
   return d;
+}
+
+// The FP32 row kernels of the mixed-precision inner solve are bound by memory latency and
+// bandwidth, not by the FP64 pipe: they get up to 8 CTAs per SM instead of 2.
+void apply_mixed(Dims& d) {
+  d.mixed = 1;
+  long long want = ((long long)d.n + 31) / 32;
+  d.nb = (int)(want < 8LL * d.sms ? (want > 0 ? want : 1) : 8LL * d.sms);
+  d.nbmax = d.nb > d.nb_dense ? d.nb : d.nb_dense;
 }
 
 // Byte offsets of every buffer inside one workspace.
@@ -81,6 +94,7 @@ struct Layout {
   size_t r, w, xb, p, sv;             // CG vectors
   size_t part, red, small, st, flag;  // reductions, k x k matrices, control block
   size_t oz_a, oz_ea, oz_p, oz_ep, oz_q; // tensor-core product: digits of A and P, exponents, split sums
+  size_t av32, wd32;                     // mixed precision: FP32 copies of the scaled values and of diag A
   size_t total;
 };
 
@@ -100,6 +114,10 @@ Layout make_layout(const Dims& dm) {
     L.rp = take((n + 1) * sizeof(int));
     L.ci = take((size_t)dm.nnz * sizeof(int));
     L.av = take((size_t)dm.nnz * sizeof(double));
+    if (dm.mixed) {
+      L.av32 = take((size_t)dm.nnz * sizeof(float));
+      L.wd32 = take(n * sizeof(float));
+    }
   }
   L.diag = take(n * sizeof(double));
   L.d = take(n * sizeof(double));
@@ -109,7 +127,8 @@ Layout make_layout(const Dims& dm) {
   L.bs = take(n * sizeof(double));
   L.x = take(n * sizeof(double));
   if (dm.algo == MBPCG_ALGO_MBPCG) {
-    const size_t blk = n * dm.kp * sizeof(double);
+    // Q and V are taken back to back: together they also stage a column-major n x s FP64 U
+    const size_t blk = n * dm.kp * (dm.mixed ? sizeof(float) : sizeof(double));
     L.U = take(blk);
     L.X0 = take(blk);
     L.Xt = take(blk);
@@ -164,6 +183,9 @@ struct mbpcg_ctx {
   uint8_t *oz_a, *oz_p;
   int *oz_ea, *oz_ep;
   double* oz_q;
+  // mixed precision (FP32 views of the block buffers)
+  float *fU, *fX0, *fXt, *fR, *fW, *fP, *fQ, *fV;
+  float *av32, *wd32;
   cudaGraphExec_t exec;
   cudaGraphConditionalHandle cond;
   int graph_ready;
@@ -229,6 +251,18 @@ void bind(mbpcg_ctx* h) {
   h->Gtmp = sm + 7 * q;
   h->st = at<SolveState>(h, L.st);
   h->flag = at<int>(h, L.flag);
+  if (h->dm.mixed) {
+    h->fU = at<float>(h, L.U);
+    h->fX0 = at<float>(h, L.X0);
+    h->fXt = at<float>(h, L.Xt);
+    h->fR = at<float>(h, L.R);
+    h->fW = at<float>(h, L.W);
+    h->fP = at<float>(h, L.P);
+    h->fQ = at<float>(h, L.Q);
+    h->fV = at<float>(h, L.V);
+    h->av32 = at<float>(h, L.av32);
+    h->wd32 = at<float>(h, L.wd32);
+  }
   if (h->dm.tc) {
     h->oz_a = at<uint8_t>(h, L.oz_a);
     h->oz_ea = at<int>(h, L.oz_ea);
@@ -244,8 +278,10 @@ int check_common(int n, int s, int precond, int algo, int precision, int mem) {
   if (algo == MBPCG_ALGO_MBPCG && (s < 1 || s > 32)) return set_err(MBPCG_ERR_INVALID, "s must be in [1, 32] (got %d)", s);
   if (precond != MBPCG_PRECOND_NONE && precond != MBPCG_PRECOND_JACOBI)
     return set_err(MBPCG_ERR_INVALID, "unknown precond %d", precond);
-  if (precision != MBPCG_FP64 && precision != MBPCG_FP64_TC)
+  if (precision != MBPCG_FP64 && precision != MBPCG_FP64_TC && precision != MBPCG_MIXED_FP32)
     return set_err(MBPCG_ERR_INVALID, "unsupported precision %d", precision);
+  if (precision == MBPCG_MIXED_FP32 && algo != MBPCG_ALGO_MBPCG)
+    return set_err(MBPCG_ERR_INVALID, "the mixed-precision inner solve is for MBPCG");
   if (mem != 0 && mem != 1) return set_err(MBPCG_ERR_INVALID, "mem must be 0 (host) or 1 (device)");
   return MBPCG_OK;
 }
@@ -335,6 +371,12 @@ int finish_create(mbpcg_ctx* h) {
     h->sqd = nullptr;
     h->wdiag = nullptr;
   }
+  if (h->dm.mixed) {
+    k_to_f32<<<1024, 256, 0, h->stream>>>((long long)h->dm.nnz, h->av, h->av32);
+    if (h->wdiag != nullptr) k_to_f32<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->wdiag, h->wd32);
+    else h->wd32 = nullptr;
+    CUDA_TRY(cudaGetLastError());
+  }
   if (h->dm.tc) {
     oz_prepare_a(h->stream, n, h->A, h->oz_ea, h->oz_a);
     CUDA_TRY(cudaMemsetAsync(h->oz_p, 0, oz_p_chunks_bytes(n, h->dm.kp), h->stream));
@@ -414,6 +456,48 @@ void enqueue_mbpcg_exit(mbpcg_ctx* h) {
   enqueue_true_residual(h);
 }
 
+// Mixed precision (MBPCG_MIXED_FP32): the same steps with the FP32 row kernels; the reductions,
+// the k x k steps, the exit combination and the true residual stay as above.
+void enqueue_mbpcg_setup_f(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOpsF* ops = row_ops_f(dm.kp);
+  const int kp = dm.kp, n = dm.n;
+  ops->spmm(h->stream, dm.nb, n, h->rp, h->ci, h->av32, h->fU, h->fQ, h->part, dm.pstride, nullptr, 0);  // A U
+  ops->setup_norms(h->stream, dm.nb, n, h->rhs, h->d, h->bs, h->fQ, h->part, dm.pstride);
+  enqueue_reduce(h, 3, nullptr);
+  k_small_setup<<<1, 1, 0, h->stream>>>(h->st, h->red);
+  ops->init(h->stream, dm.nb, n, h->s, h->fU, h->fQ, h->bs, h->fX0, h->fXt, h->fR, h->part, dm.pstride, h->st);
+  enqueue_reduce(h, npack(kp), nullptr);
+  launch_small_sigma(h->stream, kp, h->st, h->red, h->Sigma, h->SigmaInv);
+  ops->pw(h->stream, dm.nb, n, h->fR, h->fW, h->fP, h->SigmaInv, nullptr, nullptr, 1);
+}
+
+void enqueue_mbpcg_body_f(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOpsF* ops = row_ops_f(dm.kp);
+  const int kp = dm.kp, n = dm.n;
+  ops->spmm(h->stream, dm.nb, n, h->rp, h->ci, h->av32, h->fP, h->fQ, nullptr, 0, h->st, 0);
+  ops->gram(h->stream, dm.nb, n, h->fP, h->fQ, h->part, dm.pstride, h->st);
+  enqueue_reduce(h, npack(kp), h->st);
+  launch_small_xi(h->stream, kp, h->st, h->red, h->Sigma, h->Xi, h->T);
+  ops->axpy(h->stream, dm.nb, n, h->fP, h->fQ, h->fW, h->fR, h->fXt, h->fV, h->T, h->Xi, h->wd32, h->part,
+            dm.pstride, h->st);
+  enqueue_reduce(h, npack(kp) + kp, h->st);
+  launch_small_zeta(h->stream, kp, h->st, h->red, h->Sigma, h->Zeta, h->ZetaInv, h->cond, h->use_cond);
+  ops->pw(h->stream, dm.nb, n, h->fV, h->fW, h->fP, h->ZetaInv, h->Zeta, h->st, 0);
+}
+
+void enqueue_mbpcg_exit_f(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOpsF* ops = row_ops_f(dm.kp);
+  const int kp = dm.kp, n = dm.n;
+  ops->ls_gram(h->stream, dm.nb, n, h->fR, h->rhs, h->sqd, h->part, dm.pstride);
+  enqueue_reduce(h, npack(kp) + kp + 1, nullptr);
+  k_small_ls<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->c);
+  ops->combine(h->stream, dm.nb, n, h->s, h->fXt, h->fX0, h->c, h->d, h->x);
+  enqueue_true_residual(h);
+}
+
 void enqueue_cg_setup(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   k_cg_init<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->rhs, h->d, h->r, h->xb, h->p, h->sv, h->part, dm.pstride);
@@ -449,6 +533,7 @@ int build_graph(mbpcg_ctx* h) {
   e = cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     if (cg) enqueue_cg_setup(h);
+    else if (h->dm.mixed) enqueue_mbpcg_setup_f(h);
     else enqueue_mbpcg_setup(h);
     cudaStreamCaptureStatus cs;
     const cudaGraphNode_t* deps = nullptr;
@@ -468,6 +553,7 @@ int build_graph(mbpcg_ctx* h) {
                                                                   cudaStreamSetCaptureDependencies);
     if (e == cudaSuccess) {
       if (cg) enqueue_cg_exit(h);
+      else if (h->dm.mixed) enqueue_mbpcg_exit_f(h);
       else enqueue_mbpcg_exit(h);
     }
     cudaGraph_t captured = nullptr;
@@ -478,6 +564,7 @@ int build_graph(mbpcg_ctx* h) {
       if (e == cudaSuccess) {
         h->use_cond = 1;
         if (cg) enqueue_cg_body(h);
+        else if (h->dm.mixed) enqueue_mbpcg_body_f(h);
         else enqueue_mbpcg_body(h);
         h->use_cond = 0;
         cudaGraph_t b2 = nullptr;
@@ -502,11 +589,13 @@ int run_eager(mbpcg_ctx* h, int maxit_inner) {
   const bool cg = h->algo == MBPCG_ALGO_CG;
   h->use_cond = 0;
   if (cg) enqueue_cg_setup(h);
-  else enqueue_mbpcg_setup(h);
+  else if (h->dm.mixed) enqueue_mbpcg_setup_f(h);
+    else enqueue_mbpcg_setup(h);
   CUDA_TRY(cudaGetLastError());
   for (int i = 0; i < maxit_inner + 1; ++i) {
     if (cg) enqueue_cg_body(h);
-    else enqueue_mbpcg_body(h);
+    else if (h->dm.mixed) enqueue_mbpcg_body_f(h);
+        else enqueue_mbpcg_body(h);
     CUDA_TRY(cudaGetLastError());
     if ((i & 15) == 15 || i == maxit_inner) {
       CUDA_TRY(cudaMemcpyAsync(h->st_host, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
@@ -515,7 +604,8 @@ int run_eager(mbpcg_ctx* h, int maxit_inner) {
     }
   }
   if (cg) enqueue_cg_exit(h);
-  else enqueue_mbpcg_exit(h);
+  else if (h->dm.mixed) enqueue_mbpcg_exit_f(h);
+      else enqueue_mbpcg_exit(h);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }
@@ -540,7 +630,18 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
   CUDA_TRY(cudaMemcpyAsync(h->b, b, nb, in_kind, h->stream));
   CUDA_TRY(cudaMemcpyAsync(h->rhs, h->b, nb, cudaMemcpyDeviceToDevice, h->stream));
   CUDA_TRY(cudaMemsetAsync(h->x, 0, nb, h->stream));
-  if (h->algo == MBPCG_ALGO_MBPCG) {
+  if (h->algo == MBPCG_ALGO_MBPCG && h->dm.mixed) {
+    const RowOpsF* ops = row_ops_f(h->dm.kp);
+    if (U) {
+      // stage the column-major FP64 block across the A P and V buffers (2 n KP floats >= n s doubles)
+      double* stage = reinterpret_cast<double*>(h->fQ);
+      CUDA_TRY(cudaMemcpyAsync(stage, U, nb * h->s, in_kind, h->stream));
+      ops->from_colmajor(h->stream, n, h->s, stage, h->fU);
+    } else {
+      ops->gen_u(h->stream, n, h->s, h->seed, h->fU);
+    }
+    CUDA_TRY(cudaGetLastError());
+  } else if (h->algo == MBPCG_ALGO_MBPCG) {
     const RowOps* ops = row_ops(h->dm.kp);
     if (U) {
       // stage the column-major block in the A P buffer, then widen to row-major KP
@@ -552,7 +653,11 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
     CUDA_TRY(cudaGetLastError());
   }
   int total = 0, restarts = 0, status = MBPCG_OK;
-  double tol_rel = tol;
+  // FP64 inner solves: at most 3 true-residual restarts. Mixed precision: the restarts are the FP64
+  // refinement loop (correction solves in FP32), at most kMixedRestarts, and an inner solve is not
+  // asked for more than kMixedInnerTol relative reduction, which FP32 blocks can deliver.
+  const int max_restarts = h->dm.mixed ? kMixedRestarts : 3;
+  double tol_rel = h->dm.mixed ? (tol > kMixedInnerTol ? tol : kMixedInnerTol) : tol;
   SolveState s;
   for (;;) {
     const int maxit_inner = no_test ? maxit : (maxit - total);
@@ -578,12 +683,13 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
       status = MBPCG_OK;
       break;
     }
-    if (restarts >= 3 || total >= maxit || s.status == MBPCG_NOT_CONVERGED) {
+    if (restarts >= max_restarts || total >= maxit || s.status == MBPCG_NOT_CONVERGED) {
       status = (s.status == MBPCG_OK) ? MBPCG_NOT_CONVERGED : s.status;
       break;
     }
     ++restarts;
     tol_rel = 0.5 * tol * s.b_norm / s.true_res;
+    if (h->dm.mixed && tol_rel < kMixedInnerTol) tol_rel = kMixedInnerTol;
   }
   if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, h->x, nb, out_kind, h->stream));
   CUDA_TRY(cudaEventRecord(h->e1, h->stream));
@@ -615,9 +721,10 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
 extern "C" {
 
 size_t mbpcg_workspace_size_csr(int32_t n, int64_t nnz, int32_t s, int32_t algo, int32_t precision) {
-  (void)precision;
   if (n < 1 || nnz < 0) return 0;
-  return make_layout(make_dims(n, nnz, s, algo, 0, num_sms())).total;
+  Dims dm = make_dims(n, nnz, s, algo, 0, num_sms());
+  if (precision == MBPCG_MIXED_FP32 && algo == MBPCG_ALGO_MBPCG) apply_mixed(dm);
+  return make_layout(dm).total;
 }
 
 size_t mbpcg_workspace_size_dense(int32_t n, int32_t s, int32_t algo, int32_t precision) {
@@ -640,8 +747,9 @@ int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* r
   const int sms = num_sms();
   if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
   mbpcg_ctx* h = nullptr;
-  rc = alloc_handle(&h, make_dims(n, nnz, s, algo, 0, sms), s, precond, algo, precision, seed, workspace,
-                    workspace_bytes, stream);
+  Dims dm = make_dims(n, nnz, s, algo, 0, sms);
+  if (precision == MBPCG_MIXED_FP32) apply_mixed(dm);
+  rc = alloc_handle(&h, dm, s, precond, algo, precision, seed, workspace, workspace_bytes, stream);
   if (rc) {
     release(h);
     return rc;
@@ -676,6 +784,8 @@ int mbpcg_create_dense(mbpcg_handle* out, int32_t n, const double* A_colmajor, i
   if (rc) return rc;
   if (!A_colmajor) return set_err(MBPCG_ERR_INVALID, "A must not be NULL");
   if ((long long)n * n >= (1LL << 40)) return set_err(MBPCG_ERR_INVALID, "n too large for a dense matrix");
+  if (precision == MBPCG_MIXED_FP32)
+    return set_err(MBPCG_ERR_INVALID, "the mixed-precision inner solve is implemented for CSR A");
   const int sms = num_sms();
   if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
   mbpcg_ctx* h = nullptr;
@@ -715,6 +825,7 @@ int mbpcg_run_iterations_dev(mbpcg_handle h, const double* b, const double* U, i
                              double* Xt, double* R, double* W, double* P, double* Sigma) {
   if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
   if (h->algo != MBPCG_ALGO_MBPCG) return set_err(MBPCG_ERR_INVALID, "diagnostic needs an MBPCG handle");
+  if (h->dm.mixed) return set_err(MBPCG_ERR_INVALID, "diagnostic needs an FP64 handle");
   if (iters < 0) return set_err(MBPCG_ERR_INVALID, "iters must be >= 0");
   int rc = solve_impl(h, b, U, 1.0, iters, nullptr, nullptr, 1, 1);
   if (rc != MBPCG_OK && rc != MBPCG_BREAKDOWN) return rc;
@@ -763,7 +874,8 @@ int32_t mbpcg_k_padded_width(int32_t s) { return (s >= 1 && s <= 32) ? padded_wi
 
 size_t mbpcg_k_scratch_bytes(int32_t n, int32_t s) {
   if (n < 1 || s < 1 || s > 32) return 0;
-  const Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
+  Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
+  apply_mixed(dm);  // enough partial slots for the FP64 and the FP32 launch configurations
   return (size_t)(dm.nbmax + 1) * dm.pstride * sizeof(double);
 }
 
@@ -793,6 +905,33 @@ int mbpcg_k_spmm_gram(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                       const double* P, double* AP, double* G, void* scratch, size_t scratch_bytes, void* stream) {
   if (!row_ptr) return set_err(MBPCG_ERR_INVALID, "row_ptr is NULL");
   return k_product_gram(0, n, row_ptr, col_idx, vals, nullptr, s, P, AP, G, scratch, scratch_bytes, stream);
+}
+
+int mbpcg_k_spmm_gram_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const float* vals, int32_t s,
+                          const float* P, float* AP, double* G, void* scratch, size_t scratch_bytes, void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !row_ptr || !P || !AP || !G) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if (scratch_bytes < mbpcg_k_scratch_bytes(n, s) || !scratch) return set_err(MBPCG_ERR_INVALID, "scratch too small");
+  Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
+  apply_mixed(dm);
+  cudaStream_t st = (cudaStream_t)stream;
+  double* part = static_cast<double*>(scratch);
+  double* red = part + (size_t)dm.nbmax * dm.pstride;
+  row_ops_f(dm.kp)->spmm(st, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0);
+  row_ops_f(dm.kp)->gram(st, dm.nb, n, P, AP, part, dm.pstride, nullptr);
+  k_reduce<<<npack(dm.kp), 128, 0, st>>>(part, dm.nb, dm.pstride, red, nullptr);
+  k_unpack_full<<<1, 256, 0, st>>>(red, dm.kp, s, G);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+int mbpcg_k_spmm_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const float* vals, int32_t s,
+                     const float* P, float* AP, void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !row_ptr || !P || !AP) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
+  apply_mixed(dm);
+  row_ops_f(dm.kp)->spmm((cudaStream_t)stream, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
 }
 
 int mbpcg_k_dense_gram(int32_t n, const double* A, int32_t s, const double* P, double* AP, double* G, void* scratch,

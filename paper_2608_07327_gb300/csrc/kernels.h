@@ -57,7 +57,51 @@ inline const RowOps* row_ops(int kp) {
   }
 }
 
+// Host launchers of the FP32 row kernels of the mixed-precision inner solve (inst_f32_kp*.cu).
+struct RowOpsF {
+  int kp;
+  void (*spmm)(cudaStream_t, int nb, int n, const int* rp, const int* ci, const float* av, const float* P, float* Q,
+               double* part, int pstride, const SolveState* st, int gram);
+  void (*gram)(cudaStream_t, int nb, int n, const float* X, const float* Y, double* part, int pstride,
+               const SolveState* st);
+  void (*axpy)(cudaStream_t, int nb, int n, const float* P, const float* Q, const float* W, float* R, float* Xt,
+               float* V, const double* T, const double* Xi, const float* wdiag, double* part, int pstride,
+               const SolveState* st);
+  void (*pw)(cudaStream_t, int nb, int n, const float* V, float* W, float* P, const double* Zinv, const double* Z,
+             const SolveState* st, int setp);
+  void (*setup_norms)(cudaStream_t, int nb, int n, const double* rhs, const double* d, double* bs, const float* AU,
+                      double* part, int pstride);
+  void (*init)(cudaStream_t, int nb, int n, int s, const float* U, const float* AU, const double* bs, float* X0,
+               float* Xt, float* R, double* part, int pstride, const SolveState* st);
+  void (*ls_gram)(cudaStream_t, int nb, int n, const float* R, const double* rhs, const double* sqd, double* part,
+                  int pstride);
+  void (*combine)(cudaStream_t, int nb, int n, int s, const float* Xt, const float* X0, const double* c,
+                  const double* d, double* x);
+  void (*gen_u)(cudaStream_t, int n, int s, unsigned long long seed, float* U);
+  void (*from_colmajor)(cudaStream_t, int n, int s, const double* src, float* dst);
+};
+
+const RowOpsF* row_ops_f_kp1();
+const RowOpsF* row_ops_f_kp2();
+const RowOpsF* row_ops_f_kp4();
+const RowOpsF* row_ops_f_kp8();
+const RowOpsF* row_ops_f_kp16();
+const RowOpsF* row_ops_f_kp32();
+
+inline const RowOpsF* row_ops_f(int kp) {
+  switch (kp) {
+    case 1: return row_ops_f_kp1();
+    case 2: return row_ops_f_kp2();
+    case 4: return row_ops_f_kp4();
+    case 8: return row_ops_f_kp8();
+    case 16: return row_ops_f_kp16();
+    case 32: return row_ops_f_kp32();
+    default: return nullptr;
+  }
+}
+
 // single-CTA and vector kernels (small_kernels.cu)
+__global__ void k_to_f32(long long n, const double* __restrict__ src, float* __restrict__ dst);
 __global__ void k_reduce(const double* part, int nparts, int pstride, double* out, const SolveState* st);
 __global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s);
 __global__ void k_small_setup(SolveState* st, const double* red);

@@ -401,4 +401,10 @@ __global__ void k_cg_finish(int n, const double* __restrict__ xbar, const double
     x[i] += (d != nullptr) ? d[i] * xbar[i] : xbar[i];
 }
 
+// dst = FP32 rounding of src (the mixed-precision copies of the scaled matrix values and diag A).
+__global__ void k_to_f32(long long n, const double* __restrict__ src, float* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
 }  // namespace mbpcg
