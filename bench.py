@@ -81,6 +81,8 @@ def parse():
     p.add_argument("--precision", default=None, choices=["fp64", "tc", "mixed"],
                    help="tc: dense product on the BF16 tensor cores by exact digit splitting (FP64 accuracy); "
                         "mixed: FP32 inner solves in FP64 refinement (CSR); default: the workload's own")
+    p.add_argument("--residual", default="explicit", choices=["explicit", "implicit"],
+                   help="implicit: the loop carries R = W Sigma instead of updating R (MBPCG_RESIDUAL_IMPLICIT)")
     p.add_argument("--launch-mode", default="graph", choices=["graph", "eager"],
                    help="eager: host-launched loop (for profilers; same kernels and results)")
     return p.parse_args()
@@ -209,7 +211,8 @@ def run_ours(args, world, rank, local):
     else:
         prec, pname = mb.MBPCG_FP64, "fp64"
     mixed = prec == mb.MBPCG_MIXED_FP32
-    solver = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode, precision=prec)
+    rmode = mb.MBPCG_RESIDUAL_IMPLICIT if args.residual == "implicit" else mb.MBPCG_RESIDUAL_EXPLICIT
+    solver = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode, precision=prec, residual_mode=rmode)
     fp64 = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode) if mixed else None
     cg = mb.Solver(A, algo=mb.MBPCG_ALGO_CG, precond=cfg["precond"], launch_mode=mode)
     stream = solver.stream
@@ -389,7 +392,7 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
             "config": {"workload": cfg["desc"], "n": n, "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
                        "tol": cfg["tol"], "l2": "flushed before every step (256 MB write)",
-                       "launch_mode": args.launch_mode, "precision": pname,
+                       "launch_mode": args.launch_mode, "precision": pname, "residual": args.residual,
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "iterations": info["iterations"], "restarts": info["restarts"], "relres_true": relres_check,
             "cg_ms": round(cg_ms, 4), "cg_iterations": cg_infos[-1]["iterations"],

@@ -146,6 +146,17 @@ int mbpcg_run_iterations_dev(mbpcg_handle h, const double* b, const double* U, i
 typedef enum { MBPCG_LAUNCH_GRAPH = 0, MBPCG_LAUNCH_EAGER = 1 } mbpcg_launch_mode;
 int mbpcg_set_launch_mode(mbpcg_handle h, int32_t mode);
 
+/* How the loop carries the residual block. EXPLICIT (default): R is updated every iteration as in
+ * Algorithm 1 (R -= (A P) T). IMPLICIT: the Dubrulle-R identity R = W Sigma is used instead -- the
+ * new residual block of an iteration is V Sigma, so its column norms (the best-basis test) are
+ * sigma_j^T (V^T D^2 V) sigma_j from a Gram the iteration forms anyway (plus V^T D^2 V with
+ * scaling), R is neither read nor written in the loop (16 n s bytes and n s^2 FMAs less per
+ * iteration), and R is formed once before the exit. Not in the paper, which updates R explicitly;
+ * results agree up to rounding. MBPCG handles with FP64 or FP64_TC precision only
+ * (MBPCG_ERR_INVALID otherwise). Takes effect at the next solve. */
+typedef enum { MBPCG_RESIDUAL_EXPLICIT = 0, MBPCG_RESIDUAL_IMPLICIT = 1 } mbpcg_residual_mode;
+int mbpcg_set_residual_mode(mbpcg_handle h, int32_t mode);
+
 /* Release a handle (NULL is ignored). */
 void mbpcg_destroy(mbpcg_handle h);
 

@@ -16,7 +16,8 @@ from ._native import (  # noqa: F401  (re-exported C ABI names)
     mbpcg_set_launch_mode, mbpcg_solve, mbpcg_solve_dev, mbpcg_workspace_size_csr, mbpcg_workspace_size_dense, status_string, last_error,
     MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,
     MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_FP64_TC, MBPCG_MIXED_FP32, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER,
-    mbpcg_k_spmm_gram_f32, mbpcg_k_spmm_f32)
+    mbpcg_k_spmm_gram_f32, mbpcg_k_spmm_f32, mbpcg_set_residual_mode, MBPCG_RESIDUAL_EXPLICIT,
+    MBPCG_RESIDUAL_IMPLICIT)
 
 from ._native import (  # noqa: F401,E402
     mbpcg_server_create, mbpcg_server_destroy, mbpcg_server_get_stats, mbpcg_server_submit_csr, mbpcg_server_wait)
@@ -78,7 +79,8 @@ class Solver:
     waits for the caller's current stream."""
 
     def __init__(self, A, s: int = 4, precond: int = 0, algo: int = 0, seed: int = 0,
-                 launch_mode: int = MBPCG_LAUNCH_GRAPH, precision: int = MBPCG_FP64):
+                 launch_mode: int = MBPCG_LAUNCH_GRAPH, precision: int = MBPCG_FP64,
+                 residual_mode: int = MBPCG_RESIDUAL_EXPLICIT):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("MBPCG needs a CUDA device (GB300, sm_103a); no CPU path exists")
@@ -107,6 +109,10 @@ class Solver:
             st = mbpcg_set_launch_mode(self.h, launch_mode)
             if st != MBPCG_OK:
                 raise MBPCGError(st, "mbpcg_set_launch_mode")
+        if residual_mode != MBPCG_RESIDUAL_EXPLICIT:
+            st = mbpcg_set_residual_mode(self.h, residual_mode)
+            if st != MBPCG_OK:
+                raise MBPCGError(st, "mbpcg_set_residual_mode")
 
     def solve(self, b, U=None, tol: float = 1e-8, maxit: int = 100000):
         """Solve A x = b. b (and U, n x s column-major) are numpy arrays (host path, mbpcg_solve)

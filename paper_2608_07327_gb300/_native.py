@@ -26,6 +26,8 @@ MBPCG_MIXED_FP32 = 1
 MBPCG_FP64_TC = 2
 MBPCG_LAUNCH_GRAPH = 0
 MBPCG_LAUNCH_EAGER = 1
+MBPCG_RESIDUAL_EXPLICIT = 0
+MBPCG_RESIDUAL_IMPLICIT = 1
 
 
 class Info(ctypes.Structure):
@@ -88,6 +90,7 @@ _SIGS = {
     "mbpcg_run_iterations_dev": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _P, _P, _P, _P]),
     "mbpcg_destroy": (None, [_P]),
     "mbpcg_set_launch_mode": (ctypes.c_int, [_P, _I32]),
+    "mbpcg_set_residual_mode": (ctypes.c_int, [_P, _I32]),
     "mbpcg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mbpcg_last_error": (ctypes.c_char_p, []),
     "mbpcg_k_padded_width": (_I32, [_I32]),
@@ -301,3 +304,7 @@ def mbpcg_server_get_stats(srv) -> dict:
 
 def mbpcg_server_destroy(srv):
     lib().mbpcg_server_destroy(srv)
+
+
+def mbpcg_set_residual_mode(h, mode):
+    return lib().mbpcg_set_residual_mode(h, mode)

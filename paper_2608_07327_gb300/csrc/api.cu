@@ -78,6 +78,10 @@ Dims make_dims(int n, long long nnz, int s, int algo, int dense, int sms) {
   return d;
 }
 
+// Partial-sum slots of a solver handle also hold the weighted Gram V^T D^2 V of the
+// implicit-residual mode (after the KP norms); the component entry points keep the narrower slots.
+void widen_for_handle(Dims& d) { d.pstride = (2 * npack(d.kp) + d.kp + 1 + 3) / 4 * 4; }
+
 // The FP32 row kernels of the mixed-precision inner solve are bound by memory latency and
 // bandwidth, not by the FP64 pipe: they get up to 8 CTAs per SM instead of 2.
 void apply_mixed(Dims& d) {
@@ -190,6 +194,7 @@ struct mbpcg_ctx {
   cudaGraphConditionalHandle cond;
   int graph_ready;
   int launch_mode;  // MBPCG_LAUNCH_GRAPH or MBPCG_LAUNCH_EAGER
+  int rfree;        // MBPCG_RESIDUAL_IMPLICIT: R = W Sigma is not formed inside the loop
   int use_cond;     // 1 while the loop body is captured into the WHILE node
   cudaEvent_t e0, e1;
 };
@@ -439,8 +444,14 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
   enqueue_reduce(h, npack(kp), h->st);
   launch_small_xi(h->stream, kp, h->st, h->red, h->Sigma, h->Xi, h->T);
   ops->axpy(h->stream, dm.nb, n, h->P, h->Q, h->W, h->R, h->Xt, h->V, h->T, h->Xi, h->wdiag, h->part, dm.pstride,
-            h->st);
-  enqueue_reduce(h, npack(kp) + kp, h->st);
+            h->st, h->rfree);
+  if (h->rfree) {  // nu_j from the Gram of V (weighted with scaling) and Sigma
+    const bool w = h->wdiag != nullptr;
+    enqueue_reduce(h, w ? 2 * npack(kp) + kp : npack(kp), h->st);
+    k_small_nu<<<kp, 32, 0, h->stream>>>(h->st, h->red, h->Sigma, kp, w ? npack(kp) + kp : 0);
+  } else {
+    enqueue_reduce(h, npack(kp) + kp, h->st);
+  }
   launch_small_zeta(h->stream, kp, h->st, h->red, h->Sigma, h->Zeta, h->ZetaInv, h->cond, h->use_cond);
   ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0);
 }
@@ -449,6 +460,7 @@ void enqueue_mbpcg_exit(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   const RowOps* ops = row_ops(dm.kp);
   const int kp = dm.kp, n = dm.n;
+  if (h->rfree) ops->rsig(h->stream, dm.nb, n, h->V, h->W, h->Sigma, h->R, h->st);
   ops->ls_gram(h->stream, dm.nb, n, h->R, h->rhs, h->sqd, h->part, dm.pstride);
   enqueue_reduce(h, npack(kp) + kp + 1, nullptr);
   k_small_ls<<<1, kSmallThreads, 0, h->stream>>>(h->st, h->red, kp, h->c);
@@ -724,6 +736,7 @@ size_t mbpcg_workspace_size_csr(int32_t n, int64_t nnz, int32_t s, int32_t algo,
   if (n < 1 || nnz < 0) return 0;
   Dims dm = make_dims(n, nnz, s, algo, 0, num_sms());
   if (precision == MBPCG_MIXED_FP32 && algo == MBPCG_ALGO_MBPCG) apply_mixed(dm);
+  widen_for_handle(dm);
   return make_layout(dm).total;
 }
 
@@ -731,6 +744,7 @@ size_t mbpcg_workspace_size_dense(int32_t n, int32_t s, int32_t algo, int32_t pr
   if (n < 1) return 0;
   Dims dm = make_dims(n, (long long)n * n, s, algo, 1, num_sms());
   dm.tc = (precision == MBPCG_FP64_TC && algo == MBPCG_ALGO_MBPCG) ? 1 : 0;
+  widen_for_handle(dm);
   return make_layout(dm).total;
 }
 
@@ -749,6 +763,7 @@ int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* r
   mbpcg_ctx* h = nullptr;
   Dims dm = make_dims(n, nnz, s, algo, 0, sms);
   if (precision == MBPCG_MIXED_FP32) apply_mixed(dm);
+  widen_for_handle(dm);
   rc = alloc_handle(&h, dm, s, precond, algo, precision, seed, workspace, workspace_bytes, stream);
   if (rc) {
     release(h);
@@ -791,6 +806,7 @@ int mbpcg_create_dense(mbpcg_handle* out, int32_t n, const double* A_colmajor, i
   mbpcg_ctx* h = nullptr;
   Dims dm = make_dims(n, (long long)n * n, s, algo, 1, sms);
   dm.tc = (precision == MBPCG_FP64_TC && algo == MBPCG_ALGO_MBPCG) ? 1 : 0;
+  widen_for_handle(dm);
   rc = alloc_handle(&h, dm, s, precond, algo, precision, seed, workspace, workspace_bytes, stream);
   if (rc) {
     release(h);
@@ -847,6 +863,22 @@ int mbpcg_set_launch_mode(mbpcg_handle h, int32_t mode) {
   if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
   if (mode != MBPCG_LAUNCH_GRAPH && mode != MBPCG_LAUNCH_EAGER) return set_err(MBPCG_ERR_INVALID, "unknown mode");
   h->launch_mode = mode;
+  return MBPCG_OK;
+}
+
+int mbpcg_set_residual_mode(mbpcg_handle h, int32_t mode) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (mode != MBPCG_RESIDUAL_EXPLICIT && mode != MBPCG_RESIDUAL_IMPLICIT)
+    return set_err(MBPCG_ERR_INVALID, "unknown residual mode");
+  if (mode == MBPCG_RESIDUAL_IMPLICIT && (h->algo != MBPCG_ALGO_MBPCG || h->dm.mixed))
+    return set_err(MBPCG_ERR_INVALID, "the implicit-residual mode is for FP64 MBPCG handles");
+  const int rf = (mode == MBPCG_RESIDUAL_IMPLICIT) ? 1 : 0;
+  if (rf != h->rfree && h->graph_ready) {  // the captured loop body changes
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->exec);
+    h->graph_ready = 0;
+  }
+  h->rfree = rf;
   return MBPCG_OK;
 }
 

@@ -17,7 +17,9 @@ struct RowOps {
                const SolveState* st);
   void (*axpy)(cudaStream_t, int nb, int n, const double* P, const double* Q, const double* W, double* R,
                double* Xt, double* V, const double* T, const double* Xi, const double* wdiag, double* part,
-               int pstride, const SolveState* st);
+               int pstride, const SolveState* st, int rfree);
+  void (*rsig)(cudaStream_t, int nb, int n, const double* V, const double* W, const double* Sigma, double* R,
+               const SolveState* st);
   void (*pw)(cudaStream_t, int nb, int n, const double* V, double* W, double* P, const double* Zinv,
              const double* Z, const SolveState* st, int setp);
   void (*setup_norms)(cudaStream_t, int nb, int n, const double* rhs, const double* d, double* bs,
@@ -102,6 +104,8 @@ inline const RowOpsF* row_ops_f(int kp) {
 
 // single-CTA and vector kernels (small_kernels.cu)
 __global__ void k_to_f32(long long n, const double* __restrict__ src, float* __restrict__ dst);
+__global__ void k_small_nu(SolveState* st, double* __restrict__ red, const double* __restrict__ Sigma, int kp,
+                           int goff);
 __global__ void k_reduce(const double* part, int nparts, int pstride, double* out, const SolveState* st);
 __global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s);
 __global__ void k_small_setup(SolveState* st, const double* red);

@@ -37,6 +37,7 @@ struct SolveState {
   int32_t s;           // number of copies
   int32_t restart;     // index of the current inner solve (0 = the user's right-hand side)
   int32_t kerr;        // 1: a kernel's bounded wait timed out (the solve returns MBPCG_ERR_TIMEOUT)
+  int32_t r_from_v;    // implicit-residual mode: 1 if the current residual block is V Sigma, 0 if W Sigma
   double tol_rel;      // tolerance of the current inner solve, relative to ||rhs||
   double tol_abs;      // tol_rel * ||rhs||
   double rhs_norm;     // ||rhs|| of the current inner solve (original metric)

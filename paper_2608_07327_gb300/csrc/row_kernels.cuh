@@ -261,7 +261,10 @@ k_gram(int n, const double* __restrict__ X, const double* __restrict__ Y, double
 // plus CTA partials of nu_j = ||(D R)_j||^2 (the original-system residual norms used for the
 // best-basis test, Section 1) at part[NPACK + j] and of the upper triangle of V^T V at part[0..).
 // wdiag = diag(A) of the original matrix (D^2), or NULL without scaling.
-template <int KP>
+// RFREE (implicit residual, R = W Sigma): R is neither read nor written and nu is not formed here;
+// with scaling the CTA partials of V^T D^2 V go to part[NPACK + KP ...) instead (nu_j is then
+// sigma_j^T (V^T D^2 V) sigma_j, since the new residual block is V Sigma).
+template <int KP, bool RFREE>
 __global__ void __launch_bounds__(kThreads)
 k_axpy(int n, const double* __restrict__ P, const double* __restrict__ Q, const double* __restrict__ W,
        double* __restrict__ R, double* __restrict__ Xt, double* __restrict__ V,
@@ -276,7 +279,9 @@ k_axpy(int n, const double* __restrict__ P, const double* __restrict__ Q, const 
   __shared__ __align__(16) double Ps[C::ROWS * KP];
   __shared__ __align__(16) double Qs[C::ROWS * KP];
   __shared__ __align__(16) double Vs[C::ROWS * KP];
+  __shared__ __align__(16) double Vws[RFREE ? C::ROWS * KP : 2];
   __shared__ __align__(16) double red[RED];
+  const bool wgram = RFREE && wdiag != nullptr;
   const int tid = threadIdx.x, rl = tid / C::TPR, j0 = (tid % C::TPR) * C::CPT;
   for (int q = tid; q < KP * KP; q += kThreads) {  // column-major in global -> row-major here
     const int l = q % KP, jj = q / KP;
@@ -285,8 +290,9 @@ k_axpy(int n, const double* __restrict__ P, const double* __restrict__ Q, const 
   }
   int r0, r1;
   row_range(n, r0, r1);
-  G g;
+  G g, g2;
   g.init(tid);
+  if (wgram) g2.init(tid);
   double nu[C::CPT];
 #pragma unroll
   for (int c = 0; c < C::CPT; ++c) nu[c] = 0.0;
@@ -309,10 +315,11 @@ k_axpy(int n, const double* __restrict__ P, const double* __restrict__ Q, const 
     double vv[C::CPT];
 #pragma unroll
     for (int c = 0; c < C::CPT; ++c) vv[c] = 0.0;
+    double wi = 1.0;
     if (valid) {
       double xv[C::CPT], rv[C::CPT];
       ldv_plain<C::CPT>(Xt + (size_t)i * KP + j0, xv);
-      ldv_plain<C::CPT>(R + (size_t)i * KP + j0, rv);
+      if constexpr (!RFREE) ldv_plain<C::CPT>(R + (size_t)i * KP + j0, rv);
       ldv<C::CPT>(W + (size_t)i * KP + j0, vv);
 #pragma unroll 8
       for (int l = 0; l < KP; ++l) {
@@ -321,34 +328,72 @@ k_axpy(int n, const double* __restrict__ P, const double* __restrict__ Q, const 
         for (int c = 0; c < C::CPT; ++c) {
           const double t = Ts[l * KP + j0 + c];
           xv[c] = fma(pl, t, xv[c]);
-          rv[c] = fma(-ql, t, rv[c]);
+          if constexpr (!RFREE) rv[c] = fma(-ql, t, rv[c]);
           vv[c] = fma(-ql, Xis[l * KP + j0 + c], vv[c]);
         }
       }
       stv<C::CPT>(Xt + (size_t)i * KP + j0, xv);
-      stv<C::CPT>(R + (size_t)i * KP + j0, rv);
       stv<C::CPT>(V + (size_t)i * KP + j0, vv);
-      if (wdiag != nullptr) {
-        const double wi = __ldg(wdiag + i);
+      if constexpr (!RFREE) {
+        stv<C::CPT>(R + (size_t)i * KP + j0, rv);
+        if (wdiag != nullptr) {
+          const double w2 = __ldg(wdiag + i);
 #pragma unroll
-        for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c] * wi, rv[c], nu[c]);
-      } else {
+          for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c] * w2, rv[c], nu[c]);
+        } else {
 #pragma unroll
-        for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c], rv[c], nu[c]);
+          for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c], rv[c], nu[c]);
+        }
+      } else if (wgram) {
+        wi = __ldg(wdiag + i);
       }
     }
 #pragma unroll
-    for (int c = 0; c < C::CPT; ++c) Vs[rl * KP + j0 + c] = vv[c];
+    for (int c = 0; c < C::CPT; ++c) {
+      Vs[rl * KP + j0 + c] = vv[c];
+      if constexpr (RFREE) Vws[rl * KP + j0 + c] = wi * vv[c];
+    }
     __syncthreads();
     g.accumulate(Vs, Vs, min(C::ROWS, r1 - base));
+    if (wgram) g2.accumulate(Vws, Vs, min(C::ROWS, r1 - base));
     __syncthreads();
   }
   double* out = part + (size_t)blockIdx.x * pstride;
   g.finish(red, out);
+  if constexpr (!RFREE) {
 #pragma unroll
-  for (int c = 0; c < C::CPT; ++c) red[rl * KP + j0 + c] = nu[c];
-  cta_tree_sum(red, C::ROWS, KP);
-  for (int jj = tid; jj < KP; jj += kThreads) out[C::NPACK + jj] = red[jj];
+    for (int c = 0; c < C::CPT; ++c) red[rl * KP + j0 + c] = nu[c];
+    cta_tree_sum(red, C::ROWS, KP);
+    for (int jj = tid; jj < KP; jj += kThreads) out[C::NPACK + jj] = red[jj];
+  } else if (wgram) {
+    g2.finish(red, out + C::NPACK + KP);
+  }
+}
+
+// Exit of the implicit-residual mode: R = X Sigma (Sigma upper triangular, column-major KP x KP),
+// X = V when the loop ended at a test or a breakdown of the zeta step (the residual block of the
+// last iteration is V Sigma), X = W otherwise. Nothing is done when no iteration ran (R holds R^0).
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_rsig(int n, const double* __restrict__ V, const double* __restrict__ W, const double* __restrict__ Sg,
+       double* __restrict__ R, const SolveState* __restrict__ st) {
+  __shared__ double Ss[KP * KP];
+  if (st->it == 0) return;
+  const double* X = st->r_from_v ? V : W;
+  for (int q = threadIdx.x; q < KP * KP; q += kThreads) Ss[q] = Sg[q];
+  __syncthreads();
+  for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+    double x[KP], r[KP];
+    ldv<KP>(X + (size_t)i * KP, x);
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      double a = 0.0;
+#pragma unroll
+      for (int l = 0; l <= j; ++l) a = fma(x[l], Ss[l + j * KP], a);
+      r[j] = a;
+    }
+    stv<KP>(R + (size_t)i * KP, r);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -35,6 +35,7 @@ __global__ void k_small_setup(SolveState* st, const double* __restrict__ red) {
   st->tol_abs = st->tol_rel * rn;
   st->it = 0;
   st->done = 0;
+  st->r_from_v = 0;
   st->pw_skip = 0;
   st->status = 0;
   st->converged = 0;
@@ -405,6 +406,28 @@ __global__ void k_cg_finish(int n, const double* __restrict__ xbar, const double
 __global__ void k_to_f32(long long n, const double* __restrict__ src, float* __restrict__ dst) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
+}
+
+// Implicit-residual mode: nu_j = sigma_j^T G sigma_j for the columns j < s, into red[npack(kp) + j],
+// where G (packed upper triangle at red[goff ...)) is V^T V, or V^T D^2 V with scaling, and sigma_j
+// is column j of Sigma (upper triangular): the column norms of the new residual block V Sigma in
+// the original metric. One warp per column; lane a forms (G sigma_j)_a.
+__global__ void k_small_nu(SolveState* st, double* __restrict__ red, const double* __restrict__ Sigma, int kp,
+                           int goff) {
+  if (st->done) return;
+  const int j = blockIdx.x, a = threadIdx.x, s = st->s;
+  if (j >= s) return;
+  double t = 0.0;
+  if (a < s) {
+    for (int b = 0; b <= j; ++b) {
+      const double g = (a <= b) ? red[goff + pidx(a, b)] : red[goff + pidx(b, a)];
+      t = fma(g, Sigma[b + j * kp], t);
+    }
+  }
+  double v = (a <= j && a < s) ? Sigma[a + j * kp] * t : 0.0;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (a == 0) red[npack(kp) + j] = v;
 }
 
 }  // namespace mbpcg

@@ -229,6 +229,7 @@ k_small_zeta_w(SolveState* st, const double* __restrict__ G2nu, double* __restri
       st->done = 1;
       st->pw_skip = 1;
       st->status = 0;
+      st->r_from_v = 1;
       if (use_cond) cudaGraphSetConditional(cond, 0);
     }
     return;
@@ -248,6 +249,7 @@ k_small_zeta_w(SolveState* st, const double* __restrict__ G2nu, double* __restri
       st->done = 1;
       st->pw_skip = 1;
       st->status = 6;
+      st->r_from_v = 1;
       if (use_cond) cudaGraphSetConditional(cond, 0);
     }
     return;
@@ -274,6 +276,7 @@ k_small_zeta_w(SolveState* st, const double* __restrict__ G2nu, double* __restri
   if (j == 0) {
     st->best_col = h;
     st->nu_h = nh;
+    st->r_from_v = 0;
     int done = 0;
     if (st->it >= st->maxit) {
       done = 1;
@@ -746,6 +749,7 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
       st->done = 1;
       st->pw_skip = 1;
       st->status = 0;
+      st->r_from_v = 1;
       if (use_cond) cudaGraphSetConditional(cond, 0);
     }
     return;
@@ -757,6 +761,7 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
       st->done = 1;
       st->pw_skip = 1;
       st->status = 6;
+      st->r_from_v = 1;
       if (use_cond) cudaGraphSetConditional(cond, 0);
     }
     return;
@@ -775,6 +780,7 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
   if (lead) {
     st->best_col = h;
     st->nu_h = nh;
+    st->r_from_v = 0;
     int done = 0;
     if (st->it >= st->maxit) {
       done = 1;

@@ -336,3 +336,56 @@ def test_diffusion128_full_size_first_iteration_and_solution(mb, orc):
         solver.close()
     assert info["status"] == 0
     assert relres(A, b, x) <= 1e-8
+
+
+RFREE_CASES = [
+    # (name, matrix factory, s, precond, precision)
+    ("poisson64_s4", lambda: wl.poisson2d(64), 4, 0, 0),
+    ("poisson32_s16", lambda: wl.poisson2d(32), 16, 0, 0),
+    ("poisson32_s32", lambda: wl.poisson2d(32), 32, 0, 0),
+    ("diffusion12_s8_jacobi", lambda: wl.diffusion3d(12, 0), 8, 1, 0),
+    ("diffusion10_s1_jacobi", lambda: wl.diffusion3d(10, 1), 1, 1, 0),
+    ("stencil27_8_s16", lambda: wl.stencil27(8, 0), 16, 0, 0),
+    ("dense200_s8", lambda: wl.dense_spd(200, 0), 8, 0, 0),
+    ("dense257_s3_jacobi_tc", lambda: wl.dense_spd(257, 1, 0.0, 3.0), 3, 1, 2),
+    ("dense300_s32_tc", lambda: wl.dense_spd(300, 2, 0.0, 4.0), 32, 0, 2),
+]
+
+
+@pytest.mark.parametrize("name,factory,s,precond,precision", RFREE_CASES, ids=[c[0] for c in RFREE_CASES])
+def test_implicit_residual_matches_oracle_and_explicit(mb, orc, name, factory, s, precond, precision):
+    """The implicit-residual loop (R = W Sigma, norms from sigma_j^T V^T D^2 V sigma_j) against the
+    oracle, which updates R explicitly as Algorithm 1 prints it: same bars as the default path, and
+    the solution within 2 kappa tol of the GPU's explicit-residual solution."""
+    A = factory()
+    n = A.n
+    b = wl.rhs(n, 0)
+    U = wl.initial_block(n, s, 1)
+    sv = mb.Solver(A, s=s, precond=precond, precision=precision, residual_mode=mb.MBPCG_RESIDUAL_IMPLICIT)
+    ex = mb.Solver(A, s=s, precond=precond, precision=precision)
+    try:
+        x, info = sv.solve(b, U, tol=1e-8)
+        x2, info2 = sv.solve(b, U, tol=1e-8)
+        xe, infoe = ex.solve(b, U, tol=1e-8)
+    finally:
+        sv.close()
+        ex.close()
+    assert info["status"] == 0, info
+    assert relres(A, b, x) <= 1e-8
+    assert np.array_equal(x, x2)
+    xo, co, io = orc.mbpcg(A, b, U, precond=precond, tol=1e-8)
+    lo, hi = oracle_iteration_band(
+        lambda k: orc.mbpcg(A, perturbed(b, k), U, precond=precond, tol=1e-8)[2]["iterations"],
+        io["iterations"], -(-n // s))
+    assert lo <= info["iterations"] <= hi, (info, io, lo, hi)
+    kap = kappa_scaled(A, precond)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 2 * kap * 1e-8
+    assert np.linalg.norm(x - xe) / np.linalg.norm(xe) <= 2 * kap * 1e-8
+
+
+def test_implicit_residual_refused_for_cg_and_mixed(mb):
+    A = wl.poisson2d(8)
+    with pytest.raises(mb.MBPCGError):
+        mb.Solver(A, algo=mb.MBPCG_ALGO_CG, residual_mode=mb.MBPCG_RESIDUAL_IMPLICIT)
+    with pytest.raises(mb.MBPCGError):
+        mb.Solver(A, s=4, precision=mb.MBPCG_MIXED_FP32, residual_mode=mb.MBPCG_RESIDUAL_IMPLICIT)
