@@ -396,8 +396,9 @@ int finish_create(mbpcg_ctx* h) {
 void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y, int gram, const SolveState* st) {
   const Dims& dm = h->dm;
   if (dm.dense && dm.tc) {
-    oz_product(h->stream, dm.n, dm.kp, dm.sms, h->oz_a, h->oz_ea, X, h->oz_p, h->oz_ep, h->oz_q, Y, &h->st->kerr, st);
-    if (gram) ops->gram(h->stream, dm.nb, dm.n, X, Y, h->part, dm.pstride, st);
+    // the loop's product reads P, whose column exponents the W/P update has already formed
+    oz_product(h->stream, dm.n, dm.kp, dm.sms, h->oz_a, h->oz_ea, X, h->oz_p, h->oz_ep, h->oz_q, Y, &h->st->kerr, st,
+               gram ? h->part : nullptr, dm.pstride, dm.nb, X == h->P ? 1 : 0);
   } else if (dm.dense) {
     ops->dense(h->stream, dm.nb_dense, dm.n, h->A, X, Y, st, &h->st->kerr);
     if (gram) ops->gram(h->stream, dm.nb, dm.n, X, Y, h->part, dm.pstride, st);
@@ -433,7 +434,7 @@ void enqueue_mbpcg_setup(mbpcg_ctx* h) {
   ops->init(h->stream, dm.nb, n, h->s, h->U, h->Q, h->bs, h->X0, h->Xt, h->R, h->part, dm.pstride, h->st);
   enqueue_reduce(h, npack(kp), nullptr);
   launch_small_sigma(h->stream, kp, h->st, h->red, h->Sigma, h->SigmaInv);
-  ops->pw(h->stream, dm.nb, n, h->R, h->W, h->P, h->SigmaInv, nullptr, nullptr, 1);
+  ops->pw(h->stream, dm.nb, n, h->R, h->W, h->P, h->SigmaInv, nullptr, nullptr, 1, dm.tc ? h->oz_ep : nullptr);
 }
 
 void enqueue_mbpcg_body(mbpcg_ctx* h) {
@@ -453,7 +454,7 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
     enqueue_reduce(h, npack(kp) + kp, h->st);
   }
   launch_small_zeta(h->stream, kp, h->st, h->red, h->Sigma, h->Zeta, h->ZetaInv, h->cond, h->use_cond);
-  ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0);
+  ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0, dm.tc ? h->oz_ep : nullptr);
 }
 
 void enqueue_mbpcg_exit(mbpcg_ctx* h) {
@@ -1039,7 +1040,8 @@ int mbpcg_k_dense_tc_product(int32_t n, int32_t s, const double* P, double* AP, 
   if (scratch_bytes < mbpcg_k_dense_tc_scratch_bytes(n, s)) return set_err(MBPCG_ERR_INVALID, "scratch too small");
   const int kp = padded_width(s);
   const TcScratch t = tc_scratch(scratch, n, kp);
-  oz_product((cudaStream_t)stream, n, kp, num_sms(), t.at, t.ea, P, t.pc, t.ep, t.qp, AP, nullptr, nullptr);
+  oz_product((cudaStream_t)stream, n, kp, num_sms(), t.at, t.ea, P, t.pc, t.ep, t.qp, AP, nullptr, nullptr, nullptr, 0,
+             0, 0);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

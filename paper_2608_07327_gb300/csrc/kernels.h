@@ -21,7 +21,7 @@ struct RowOps {
   void (*rsig)(cudaStream_t, int nb, int n, const double* V, const double* W, const double* Sigma, double* R,
                const SolveState* st);
   void (*pw)(cudaStream_t, int nb, int n, const double* V, double* W, double* P, const double* Zinv,
-             const double* Z, const SolveState* st, int setp);
+             const double* Z, const SolveState* st, int setp, int* emax);
   void (*setup_norms)(cudaStream_t, int nb, int n, const double* rhs, const double* d, double* bs,
                       const double* AU, double* part, int pstride);
   void (*init)(cudaStream_t, int nb, int n, int s, const double* U, const double* AU, const double* bs, double* X0,
@@ -136,8 +136,11 @@ size_t oz_a_tiles_bytes(int n);
 size_t oz_p_chunks_bytes(int n, int kp);
 int oz_ksplit(int n, int sms);
 void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* Atiles);
+// part != NULL: also the CTA partials of P^T (A P) over nb balanced row ranges (stride pstride).
+// exp_ready: the column exponents of P are already in emaxP (written by the W/P update).
 void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
-                uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st);
+                uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st, double* part,
+                int pstride, int nb, int exp_ready);
 
 // single-warp k x k steps of the loop (small_warp.cu)
 void launch_small_sigma(cudaStream_t s, int kp, SolveState* st, const double* Gp, double* Sigma, double* SigmaInv);

@@ -341,9 +341,10 @@ k_dense_tc(int n, int KP, int nK, const uint8_t* __restrict__ Atiles, const int*
   if (warp == 0) tmem_dealloc(tmem, C::kTmemCols);
 }
 
-// Q[i][j] = sum over splits of Qpart[ks][i][j], in split order.
+// Q[i][j] = sum over splits of Qpart[ks][i][j], in split order. Block 0 then clears the column
+// exponents of P for the next product (they are rebuilt by the W/P update, which writes P).
 template <int KP>
-__global__ void k_oz_sum(int n, int KS, const double* __restrict__ Qpart, double* __restrict__ Q,
+__global__ void k_oz_sum(int n, int KS, const double* __restrict__ Qpart, double* __restrict__ Q, int* __restrict__ emaxP,
                          const SolveState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   const size_t total = (size_t)n * KP;
@@ -352,6 +353,55 @@ __global__ void k_oz_sum(int n, int KS, const double* __restrict__ Qpart, double
     for (int k = 1; k < KS; ++k) a += Qpart[(size_t)k * total + q];
     Q[q] = a;
   }
+  if (blockIdx.x == 0 && threadIdx.x < KP) emaxP[threadIdx.x] = 0;
+}
+
+// The same split sum fused with the CTA partials of the upper triangle of P^T Q (the Gram of the
+// Xi step of Algorithm 1), one pass over balanced row ranges (partials as k_gram writes them).
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_oz_sum_gram(int n, int KS, const double* __restrict__ Qpart, const double* __restrict__ P, double* __restrict__ Q,
+              int* __restrict__ emaxP, double* __restrict__ part, int pstride, const SolveState* __restrict__ st) {
+  using C = Cfg<KP>;
+  using G = GramTile<KP>;
+  if (st != nullptr && st->done) return;
+  __shared__ __align__(16) double Xs[C::ROWS * KP];
+  __shared__ __align__(16) double Ys[C::ROWS * KP];
+  __shared__ __align__(16) double red[G::RED];
+  const size_t total = (size_t)n * KP;
+  int r0, r1;
+  row_range(n, r0, r1);
+  const int tid = threadIdx.x, rl = tid / C::TPR, j0 = (tid % C::TPR) * C::CPT;
+  G g;
+  g.init(tid);
+  for (int base = r0; base < r1; base += C::ROWS) {
+    const int i = base + rl;
+    double xv[C::CPT], yv[C::CPT];
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) xv[c] = yv[c] = 0.0;
+    if (i < r1) {
+      const size_t o = (size_t)i * KP + j0;
+      ldv<C::CPT>(P + o, xv);
+      ldv<C::CPT>(Qpart + o, yv);
+      for (int k = 1; k < KS; ++k) {
+        double t[C::CPT];
+        ldv<C::CPT>(Qpart + (size_t)k * total + o, t);
+#pragma unroll
+        for (int c = 0; c < C::CPT; ++c) yv[c] += t[c];
+      }
+      stv<C::CPT>(Q + o, yv);
+    }
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) {
+      Xs[rl * KP + j0 + c] = xv[c];
+      Ys[rl * KP + j0 + c] = yv[c];
+    }
+    __syncthreads();
+    g.accumulate(Xs, Ys, min(C::ROWS, r1 - base));
+    __syncthreads();
+  }
+  g.finish(red, part + (size_t)blockIdx.x * pstride);
+  if (blockIdx.x == 0 && tid < KP) emaxP[tid] = 0;
 }
 
 // ------------------------------------------------------------------------------------ launchers
@@ -382,7 +432,8 @@ void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* A
 
 template <int KP, int KPT>
 static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
-                          uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st) {
+                          uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st,
+                          double* part, int pstride, int nb, int exp_ready) {
   using C = OzCfg<KPT>;
   static bool attr = false;
   if (!attr) {
@@ -390,24 +441,30 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
     attr = true;
   }
   const int nM = (n + kOzMT - 1) / kOzMT, nK = (n + kOzKC - 1) / kOzKC, KS = oz_ksplit(n, sms);
-  cudaMemsetAsync(emaxP, 0, sizeof(int) * KP, s);
   const int g = (int)(((size_t)n * KP + 255) / 256);
-  k_oz_colexp<KP><<<g < 1024 ? g : 1024, 256, 0, s>>>(n, P, emaxP, st);
+  if (!exp_ready) {
+    cudaMemsetAsync(emaxP, 0, sizeof(int) * KP, s);
+    k_oz_colexp<KP><<<g < 1024 ? g : 1024, 256, 0, s>>>(n, P, emaxP, st);
+  }
   k_oz_slice_p<KP, KPT><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
   k_dense_tc<KPT><<<dim3(nM, KS), kOzTcThreads, C::kSmem, s>>>(n, KP, nK, Atiles, emaxA, Pchunks, emaxP, Qpart, err, st);
-  k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, KS, Qpart, Q, st);
+  if (part != nullptr) k_oz_sum_gram<KP><<<nb, kThreads, 0, s>>>(n, KS, Qpart, P, Q, emaxP, part, pstride, st);
+  else k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, KS, Qpart, Q, emaxP, st);
 }
 
 void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
-                uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st) {
+                uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st, double* part,
+                int pstride, int nb, int exp_ready) {
+#define OZ_ARGS s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st, part, pstride, nb, exp_ready
   switch (kp) {
-    case 1: oz_product_kp<1, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
-    case 2: oz_product_kp<2, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
-    case 4: oz_product_kp<4, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
-    case 8: oz_product_kp<8, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
-    case 16: oz_product_kp<16, 16>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
-    default: oz_product_kp<32, 32>(s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st); break;
+    case 1: oz_product_kp<1, 16>(OZ_ARGS); break;
+    case 2: oz_product_kp<2, 16>(OZ_ARGS); break;
+    case 4: oz_product_kp<4, 16>(OZ_ARGS); break;
+    case 8: oz_product_kp<8, 16>(OZ_ARGS); break;
+    case 16: oz_product_kp<16, 16>(OZ_ARGS); break;
+    default: oz_product_kp<32, 32>(OZ_ARGS); break;
   }
+#undef OZ_ARGS
 }
 
 }  // namespace mbpcg

@@ -402,15 +402,21 @@ k_rsig(int n, const double* __restrict__ V, const double* __restrict__ W, const 
 //   P = W + P zeta^T  (SETP == false)   or   P = W  (SETP == true: the set-up P^0 = W^0)
 // For KP >= 8 a thread owns columns j and KP-1-j of a row: the two triangular dot products then
 // total KP+1 terms for every thread, so a warp never idles on a short triangle.
+// emax != NULL (tensor-core product): also the largest biased exponent of every column of the new
+// P, combined with atomicMax into emax (which the product has cleared), for the digit splitting.
 template <int KP, bool SETP>
 __global__ void __launch_bounds__(kThreads)
 k_pw(int n, const double* __restrict__ V, double* __restrict__ W, double* __restrict__ P,
-     const double* __restrict__ Zinvg, const double* __restrict__ Zg, const SolveState* __restrict__ st) {
+     const double* __restrict__ Zinvg, const double* __restrict__ Zg, const SolveState* __restrict__ st,
+     int* __restrict__ emax) {
   using C = Cfg<KP>;
   if (st != nullptr && st->pw_skip) return;
   __shared__ __align__(16) double Zis[KP * KP];
   __shared__ __align__(16) double Zs[KP * KP];
+  __shared__ int em[KP];
   const int tid = threadIdx.x;
+  if (tid < KP) em[tid] = 0;
+  auto bexp = [](double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); };
   for (int q = tid; q < KP * KP; q += kThreads) {
     const int l = q % KP, jj = q / KP;
     Zis[l * KP + jj] = Zinvg[q];
@@ -433,6 +439,9 @@ k_pw(int n, const double* __restrict__ V, double* __restrict__ W, double* __rest
       stv<KP>(W + (size_t)i * KP, w);
       if constexpr (SETP) {
         stv<KP>(P + (size_t)i * KP, w);
+        if (emax != nullptr)
+#pragma unroll
+          for (int j = 0; j < KP; ++j) atomicMax(&em[j], bexp(w[j]));
       } else {
         double p[KP], pn[KP];
         ldv_plain<KP>(P + (size_t)i * KP, p);
@@ -444,6 +453,9 @@ k_pw(int n, const double* __restrict__ V, double* __restrict__ W, double* __rest
           pn[j] = a;
         }
         stv<KP>(P + (size_t)i * KP, pn);
+        if (emax != nullptr)
+#pragma unroll
+          for (int j = 0; j < KP; ++j) atomicMax(&em[j], bexp(pn[j]));
       }
     }
   } else {
@@ -485,6 +497,10 @@ k_pw(int n, const double* __restrict__ V, double* __restrict__ W, double* __rest
         if constexpr (SETP) {
           P[(size_t)i * KP + ja] = wa;
           P[(size_t)i * KP + jb] = wb;
+          if (emax != nullptr) {
+            atomicMax(&em[ja], bexp(wa));
+            atomicMax(&em[jb], bexp(wb));
+          }
         } else {
           // P_ia = W_ia + sum_{l>=ja} P_il Z_ja,l ; P_ib = W_ib + sum_{l>=jb} P_il Z_jb,l
           const double* pr = Psm + rl * KP;
@@ -503,10 +519,18 @@ k_pw(int n, const double* __restrict__ V, double* __restrict__ W, double* __rest
           }
           P[(size_t)i * KP + ja] = pa;
           P[(size_t)i * KP + jb] = acc2;
+          if (emax != nullptr) {
+            atomicMax(&em[ja], bexp(pa));
+            atomicMax(&em[jb], bexp(acc2));
+          }
         }
       }
       __syncthreads();
     }
+  }
+  if (emax != nullptr) {
+    __syncthreads();
+    if (tid < KP && em[tid] > 0) atomicMax(&emax[tid], em[tid]);
   }
 }
 
