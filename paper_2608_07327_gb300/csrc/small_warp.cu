@@ -455,14 +455,13 @@ k_small_sigma_c(SolveState* st, const double* __restrict__ Gp, double* __restric
 // the sub-partitions and the CTAs of the cluster.
 //
 // Factorisation (every CTA of the cluster, redundantly): symmetric Gaussian elimination
-// G = L D L^T that builds L^{-1} alongside (the row operations applied to the identity). Warp 0 (the
-// pivot warp) carries the chain: pivot d_k -> 1/d_k -> row k+1 updated by step k -> d_{k+1}; warps
-// 1-3 and, at KP = 32, 5-7 (two per sub-partition, so that one hides the other's latencies; warp 4
-// stays idle to leave the pivot warp's sub-partition to it) apply step k to the rest of the trailing matrix and
-// to L^{-1} while the pivot warp already works on step k+1 (two named barriers per step hand rows
-// over). The Cholesky factor and the
-// inverses follow without further serial steps: Z = D^{1/2} L^T, Z^{-1} = L^{-T} D^{-1/2},
-// Xi = G^{-1} = L^{-T} D^{-1} L^{-1}.
+// G = L D L^T. Warp 0 (the pivot warp) carries the chain: pivot d_k -> 1/d_k -> row k+1 updated by
+// step k -> d_{k+1}; warps 1-3 and, at KP = 32, 5-7 (two per sub-partition, so that one hides the
+// other's latencies; warp 4 stays idle to leave the pivot warp's sub-partition to it) apply step k
+// to the rest of the trailing matrix while the pivot warp already works on step k+1 (two named
+// barriers per step hand rows over). Nothing else is on that chain: afterwards each CTA forms only
+// the columns or rows of L^{-1} it needs, by triangular solves with one KP-lane shuffle segment per
+// column. Z = D^{1/2} L^T, Z^{-1} = L^{-T} D^{-1/2}, Xi = G^{-1} = L^{-T} D^{-1} L^{-1}.
 //
 // After it, each CTA owns CPC = 128 / KP columns b = c + CS r (r < CPC; c = rank in the cluster) of
 // every result; columns computed elsewhere are read from the owner's shared memory (distributed
@@ -531,7 +530,7 @@ struct LdlWork {
   double S[KP * LD];   // in: G (identity outside s x s); then the trailing matrices; later reused
   double U[KP * LD];   // row k of D L^T: U[k][m] = d_k L[m][k] (m >= k)
   double Lt[KP * LD];  // Lt[k][m] = L[m][k] (m > k)
-  double R[KP * LD];   // L^{-1}, unit lower triangular
+  double R[KP * LD];   // L^{-1}, unit lower triangular (the Xi step fills it column by column)
   double d[KP], inv[KP];
   unsigned short tri[KP * (KP + 1) / 2];  // packed index q = m (m+1)/2 + l (l <= m) -> l | m << 8
   int bad;
@@ -559,7 +558,7 @@ __device__ void ldl_init(LdlWork<KP>& W, const double* __restrict__ packed, int 
   __syncthreads();
 }
 
-// G = L D L^T and L^{-1} (see above). Sets W.bad when a pivot of the leading s x s block is not a
+// G = L D L^T (see above). Sets W.bad when a pivot of the leading s x s block is not a
 // finite number above 64 eps max_j G_jj (or not below 2^1000). All NF threads call it; it ends with
 // a block-wide barrier.
 template <int KP>
@@ -599,34 +598,48 @@ __device__ void ldl_factor(LdlWork<KP>& W, int s) {
     }
     named_bar_sync(2, NBAR);
     if (j == 0) W.bad = bad ? 1 : 0;
-  } else if (warp != 4) {  // bulk: step k on rows k+2.. of the trailing matrix and rows k+1.. of L^{-1}
+  } else if (warp != 4) {  // bulk: step k on rows k+2.. of the trailing matrix
     static_assert(ClusterCfg<KP>::NF == 128 || ClusterCfg<KP>::NF == 256, "bulk thread numbering");
     const int bt = tid - (warp < 4 ? 32 : 64);
     double* base = W.S;
     for (int k = 0; k < s; ++k) {
       named_bar_sync(1, NBAR);
-      const int t = s - k - 2, cntS = t > 0 ? t * (t + 1) / 2 : 0;
-      const int rows = s - k - 1, cnt = cntS + rows * (k + 1);
-      const unsigned long long magic = rows > 0 ? ((1ull << 32) + rows - 1) / rows : 0;  // q / rows = q magic >> 32 (q < 2^10)
-      for (int q = bt; q < cnt; q += NB) {
-        int zo, xo, yo;
-        if (q < cntS) {  // S[l][m] -= S[k][l] S[k][m] / d_k
-          const int pk = W.tri[q], l = k + 2 + (pk & 0xFF), m = k + 2 + (pk >> 8);
-          zo = l * LD + m;
-          xo = LW::OU + k * LD + l;
-          yo = LW::OL + k * LD + m;
-        } else {  // R[l][j] -= L[l][k] R[k][j]
-          const int q2 = q - cntS, jj = (int)(((unsigned long long)q2 * magic) >> 32), l = k + 1 + (q2 - jj * rows);
-          zo = LW::OR + l * LD + jj;
-          xo = LW::OL + k * LD + l;
-          yo = LW::OR + k * LD + jj;
-        }
-        base[zo] = fma(-base[xo], base[yo], base[zo]);
+      const int t = s - k - 2, cnt = t > 0 ? t * (t + 1) / 2 : 0;
+      for (int q = bt; q < cnt; q += NB) {  // S[l][m] -= S[k][l] S[k][m] / d_k
+        const int pk = W.tri[q], l = k + 2 + (pk & 0xFF), m = k + 2 + (pk >> 8);
+        base[l * LD + m] = fma(-base[LW::OU + k * LD + l], base[LW::OL + k * LD + m], base[l * LD + m]);
       }
       named_bar_arrive(2, NBAR);
     }
   }
   __syncthreads();
+}
+
+// Column b of L^{-1} (L unit lower triangular, L[l][k] = Lt[k][l]) by forward substitution
+// L x = e_b; the thread holds row a of the column, a KP-lane shuffle segment holds the column, bmin
+// is the smallest b of the calling warp (steps before it leave x exactly as it is).
+template <int KP>
+__device__ double ldl_inv_column(const LdlWork<KP>& W, int a, int b, int bmin, int s) {
+  constexpr int LD = LdlWork<KP>::LD;
+  double x = (a == b) ? 1.0 : 0.0;
+  for (int k = bmin; k < s - 1; ++k) {
+    const double xk = __shfl_sync(kFull, x, k, KP);
+    if (a > k && a < s) x = fma(-W.Lt[k * LD + a], xk, x);
+  }
+  return x;
+}
+
+// Row b of L^{-1}, i.e. x with L^T x = e_b (x_a = 0 for a > b), by back substitution; bmax is the
+// largest b of the calling warp.
+template <int KP>
+__device__ double ldl_inv_row(const LdlWork<KP>& W, int a, int b, int bmax) {
+  constexpr int LD = LdlWork<KP>::LD;
+  double x = (a == b) ? 1.0 : 0.0;
+  for (int l = bmax; l >= 1; --l) {
+    const double xl = __shfl_sync(kFull, x, l, KP);
+    if (a < l && l <= b) x = fma(-W.Lt[a * LD + l], xl, x);  // x_l = 0 for l > b
+  }
+  return x;
 }
 
 // Copies the columns of M (ld KP+1) owned by the other CTAs of the cluster into this CTA's M
@@ -671,6 +684,11 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
     }
     return;
   }
+  // own columns of L^{-1}, then the others' through distributed shared memory
+  if (ct) W.R[a * LD + b] = ldl_inv_column<KP>(W, a, b, c + CC::CS * ((32 * (tid >> 5)) / KP), s);
+  cluster.sync();
+  cluster_gather_columns<KP>(W.R, c, false);
+  __syncthreads();
   // Xi[a][b] = sum_{j >= b} L^{-1}[j][a] (L^{-1}[j][b] / d_j) for a <= b, into W.S (upper part)
   double* X = W.S;
   if (ct) {
@@ -680,7 +698,7 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
     for (int j = b; j < s; ++j) v = fma(W.R[j * LD + a], V[j * CC::CPC + r], v);
     if (a <= b) X[a * LD + b] = v;
   }
-  cluster.sync();
+  cluster.sync();  // also: every CTA has finished reading the L^{-1} columns of the others
   cluster_gather_columns<KP>(X, c, true);
   __syncthreads();
   if (ct) {
@@ -774,7 +792,9 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
     const bool in = (a < s && b < s), up = in && a <= b;
     Sigma[a + b * KP] = in ? v * ra : 0.0;
     Zeta[a + b * KP] = up ? W.U[a * LD + b] * ra : 0.0;
-    ZetaInv[a + b * KP] = up ? W.R[b * LD + a] * rb : 0.0;
+    const int bmax = c + CC::CS * ((32 * ((tid >> 5) + 1)) / KP - 1);
+    const double lr = ldl_inv_row<KP>(W, a, b, bmax);  // L^{-1}[b][a]; every lane takes part in the shuffles
+    ZetaInv[a + b * KP] = up ? lr * rb : 0.0;
   }
   cluster.sync();  // every CTA has read the state before the leader updates it
   if (lead) {
