@@ -1,8 +1,7 @@
-// The k x k steps of Algorithm 1 inside the iteration loop. For KP <= 8 one warp, lane j owning
-// column j (k = s <= KP). On GB300 these are bound by FP64 latency, not throughput, so the algorithms
-// are chosen for short dependency chains: a right-looking Cholesky with shuffles (no block-wide
-// barriers), triangular solves in column (axpy) order, where each step is one multiply plus
-// independent FMAs, and products that read their left factor from shared memory by broadcast.
+// The k x k steps of Algorithm 1: the set-up Cholesky QR factor (one warp for KP <= 8, lane j
+// owning column j, or one CTA) and the two steps of every iteration (a thread-block cluster, see
+// below). On GB300 these are bound by FP64 latency, not throughput, so the algorithms are chosen
+// for short dependency chains.
 //
 // Padding: rows/columns s..KP-1 are factored as the identity and written back as zeros, so the row
 // kernels keep the padded columns of every block at exactly zero.
@@ -141,153 +140,6 @@ k_small_sigma_w(SolveState* st, const double* __restrict__ Gp, double* __restric
 }
 
 // Xi = (P^T A P)^{-1} = Z^{-1} Z^{-T} from the Cholesky factor of P^T A P (Section 3); T = Xi Sigma.
-template <int KP>
-__global__ void __launch_bounds__(32)
-k_small_xi_w(SolveState* st, const double* __restrict__ G1p, const double* __restrict__ Sigma,
-             double* __restrict__ Xi, double* __restrict__ T) {
-  if (st->done) return;
-  __shared__ double Zs[KP * KP], Zt[KP * KP], Xs[KP * KP], rd[KP];
-  const int j = threadIdx.x, s = st->s;
-  bool ok;
-  {
-    double a[KP];
-    load_packed_column<KP>(G1p, s, j, a);
-    ok = warp_cholesky<KP>(a, s, j);
-    store_columns<KP>(a, j, Zs);
-    if (j < KP) rd[j] = 1.0 / a[j < KP ? j : 0];
-  }
-  if (!ok) {
-    if (j == 0) {
-      st->done = 1;
-      st->pw_skip = 1;
-      st->status = 6;
-    }
-    return;
-  }
-  __syncwarp();
-  upper_inverse_column<KP>(Zs, rd, j, Zt);  // Zt[b*KP + a] = Zinv[a][b]
-  __syncwarp();
-  // Xi[i][j] = sum_{l >= max(i, j)} Zinv[i][l] Zinv[j][l]
-  if (j < KP) {
-#pragma unroll 4
-    for (int i = 0; i < KP; ++i) {
-      double v = 0.0;
-      for (int l = (i > j ? i : j); l < KP; ++l) v = fma(Zt[l * KP + i], Zt[l * KP + j], v);
-      v = (i < s && j < s) ? v : 0.0;
-      Xs[i * KP + j] = v;
-      Xi[i + j * KP] = v;
-    }
-  }
-  __syncwarp();
-  // T[i][j] = sum_{l <= j} Xi[i][l] Sigma[l][j]
-  if (j < KP) {
-    double sg[KP];
-#pragma unroll
-    for (int l = 0; l < KP; ++l) sg[l] = Sigma[l + j * KP];
-#pragma unroll 4
-    for (int i = 0; i < KP; ++i) {
-      double v = 0.0;
-#pragma unroll
-      for (int l = 0; l < KP; ++l)
-        if (l <= j) v = fma(Xs[i * KP + l], sg[l], v);
-      T[i + j * KP] = (i < s && j < s) ? v : 0.0;
-    }
-  }
-  if (j == 0) st->it += 1;
-}
-
-// Best-basis test, zeta = chol(V^T V), zeta^{-1}, Sigma = zeta Sigma; sets the WHILE condition.
-template <int KP>
-__global__ void __launch_bounds__(32)
-k_small_zeta_w(SolveState* st, const double* __restrict__ G2nu, double* __restrict__ Sigma,
-               double* __restrict__ Zeta, double* __restrict__ ZetaInv, cudaGraphConditionalHandle cond,
-               int use_cond) {
-  __shared__ double Zs[KP * KP], Zt[KP * KP], rd[KP];
-  const int j = threadIdx.x, s = st->s;
-  if (st->done) {
-    if (j == 0 && use_cond) cudaGraphSetConditional(cond, 0);
-    return;
-  }
-  // h = argmin_j nu_j, lowest index on ties (butterfly on (value, index): every lane gets the same)
-  double nv = (j < s) ? G2nu[npack(KP) + j] : __longlong_as_double(0x7ff0000000000000ll);
-  int h = j;
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    const double ov = __shfl_xor_sync(kFull, nv, off);
-    const int oh = __shfl_xor_sync(kFull, h, off);
-    if (ov < nv || (ov == nv && oh < h)) {
-      nv = ov;
-      h = oh;
-    }
-  }
-  const double nh = sqrt(nv);
-  if (!st->no_test && nh < st->tol_abs) {
-    if (j == 0) {
-      st->best_col = h;
-      st->nu_h = nh;
-      st->converged = 1;
-      st->done = 1;
-      st->pw_skip = 1;
-      st->status = 0;
-      st->r_from_v = 1;
-      if (use_cond) cudaGraphSetConditional(cond, 0);
-    }
-    return;
-  }
-  bool ok;
-  {
-    double a[KP];
-    load_packed_column<KP>(G2nu, s, j, a);
-    ok = warp_cholesky<KP>(a, s, j);
-    store_columns<KP>(a, j, Zs);
-    if (j < KP) rd[j] = 1.0 / a[j < KP ? j : 0];
-  }
-  if (!ok) {
-    if (j == 0) {
-      st->best_col = h;
-      st->nu_h = nh;
-      st->done = 1;
-      st->pw_skip = 1;
-      st->status = 6;
-      st->r_from_v = 1;
-      if (use_cond) cudaGraphSetConditional(cond, 0);
-    }
-    return;
-  }
-  __syncwarp();
-  upper_inverse_column<KP>(Zs, rd, j, Zt);
-  // Sigma[i][j] <- sum_{l=i..j} zeta[i][l] Sigma[l][j]  (lane j owns column j)
-  if (j < KP) {
-    double sg[KP];
-#pragma unroll
-    for (int l = 0; l < KP; ++l) sg[l] = Sigma[l + j * KP];
-#pragma unroll 4
-    for (int i = 0; i < KP; ++i) {
-      double v = 0.0;
-#pragma unroll
-      for (int l = 0; l < KP; ++l)
-        if (l >= i && l <= j) v = fma(Zs[i * KP + l], sg[l], v);
-      Sigma[i + j * KP] = (i < s && j < s) ? v : 0.0;
-    }
-  }
-  __syncwarp();
-  write_col_from_s<KP>(Zeta, Zs, j, s);
-  write_col_from_t<KP>(ZetaInv, Zt, j, s);
-  if (j == 0) {
-    st->best_col = h;
-    st->nu_h = nh;
-    st->r_from_v = 0;
-    int done = 0;
-    if (st->it >= st->maxit) {
-      done = 1;
-      st->done = 1;
-      st->pw_skip = 0;  // the last iteration still completes its W, P update
-      st->status = st->no_test ? 0 : 5;
-    }
-    if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
-  }
-}
-
 // ------------------------------------------------------------------------------------------------
 // KP >= 16: one CTA of 256 threads. At s = 32 each of these steps is ~20-60 thousand FP64 FMAs, so
 // the work is spread over all 8 warps of the SM; the sequential depth is kept short: a right-looking
@@ -658,9 +510,10 @@ __device__ void cluster_gather_columns(double* M, int c, bool upper) {
   }
 }
 
-// Xi = (P^T A P)^{-1} from the packed Gram G1p and T = Xi Sigma, both column-major KP x KP with zeros
-// outside s x s; the step counter advances.
-template <int KP>
+// Xi = (P^T A P)^{-1} from the packed Gram G1p and T = Xi Sigma, both column-major KL x KL with zeros
+// outside s x s; the step counter advances. KL (<= KP) is the padded width of the k x k matrices in
+// global memory; a narrower system is computed inside KP x KP with the identity outside s x s.
+template <int KP, int KL>
 __global__ void __launch_bounds__(ClusterCfg<KP>::NF) __cluster_dims__(ClusterCfg<KP>::CS, 1, 1)
 k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __restrict__ Sigma,
              double* __restrict__ Xi, double* __restrict__ T) {
@@ -673,7 +526,7 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
   const int s = st->s, tid = threadIdx.x, c = (int)cluster.block_rank();
   const bool ct = tid < CC::NT;  // column-phase thread: column b = c + CS r, row a
   const int r = tid / KP, a = tid % KP, b = c + CC::CS * r;
-  if (ct) Sg[a * CC::CPC + r] = Sigma[a + b * KP];  // own columns of Sigma (upper, zero outside s x s)
+  if (ct) Sg[a * CC::CPC + r] = (a < KL && b < KL) ? Sigma[a + b * KL] : 0.0;  // own columns (upper)
   ldl_init<KP>(W, G1p, s);
   ldl_factor<KP>(W, s);
   if (W.bad) {  // every CTA reaches the same verdict
@@ -703,10 +556,12 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
   __syncthreads();
   if (ct) {
     const bool in = (a < s && b < s);
-    Xi[a + b * KP] = in ? X[min(a, b) * LD + max(a, b)] : 0.0;
     double v = 0.0;  // T[a][b] = sum_{l <= b} Xi[a][l] Sigma[l][b]
     for (int l = 0; l <= b; ++l) v = fma(X[min(a, l) * LD + max(a, l)], Sg[l * CC::CPC + r], v);
-    T[a + b * KP] = in ? v : 0.0;
+    if (a < KL && b < KL) {
+      Xi[a + b * KL] = in ? X[min(a, b) * LD + max(a, b)] : 0.0;
+      T[a + b * KL] = in ? v : 0.0;
+    }
   }
   cluster.sync();  // no CTA leaves while another may still read its shared memory
   if (c == 0 && tid == 0) st->it += 1;
@@ -715,7 +570,8 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
 // zeta from the packed Gram V^T V (Z = D^{1/2} L^T), zeta^{-1}, Sigma <- zeta Sigma, after the
 // stopping test on nu (argmin over the columns, lowest index on ties); sets the loop's conditional.
 // The factorisation starts before the stopping test is decided and is discarded if it stops.
-template <int KP>
+// KL: padded width of the k x k matrices in global memory, as for k_small_xi_x.
+template <int KP, int KL>
 __global__ void __launch_bounds__(ClusterCfg<KP>::NF) __cluster_dims__(ClusterCfg<KP>::CS, 1, 1)
 k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restrict__ Sigma,
                double* __restrict__ Zeta, double* __restrict__ ZetaInv, cudaGraphConditionalHandle cond,
@@ -735,11 +591,11 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
   }
   const bool ct = tid < CC::NT;
   const int r = tid / KP, a = tid % KP, b = c + CC::CS * r;
-  if (ct) Sg[a * CC::CPC + r] = Sigma[a + b * KP];
+  if (ct) Sg[a * CC::CPC + r] = (a < KL && b < KL) ? Sigma[a + b * KL] : 0.0;
   ldl_init<KP>(W, G2nu, s);
   if ((tid >> 5) == CC::IDLE) {  // a warp without early factorisation work decides the stopping test
     const int j = tid & 31;  // h = argmin_j nu_j, lowest index on ties (nu >= 0: bit order = value order)
-    long long nv = (j < s) ? __double_as_longlong(G2nu[npack(KP) + j]) : 0x7FF0000000000000LL;
+    long long nv = (j < s) ? __double_as_longlong(G2nu[npack(KL) + j]) : 0x7FF0000000000000LL;
     int h = j;
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
@@ -790,11 +646,13 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
     double v = 0.0;  // (zeta Sigma)[a][b] = d_a^{-1/2} sum_{l = a..b} U[a][l] Sigma[l][b]
     for (int l = a; l <= b; ++l) v = fma(W.U[a * LD + l], Sg[l * CC::CPC + r], v);
     const bool in = (a < s && b < s), up = in && a <= b;
-    Sigma[a + b * KP] = in ? v * ra : 0.0;
-    Zeta[a + b * KP] = up ? W.U[a * LD + b] * ra : 0.0;
     const int bmax = c + CC::CS * ((32 * ((tid >> 5) + 1)) / KP - 1);
     const double lr = ldl_inv_row<KP>(W, a, b, bmax);  // L^{-1}[b][a]; every lane takes part in the shuffles
-    ZetaInv[a + b * KP] = up ? lr * rb : 0.0;
+    if (a < KL && b < KL) {
+      Sigma[a + b * KL] = in ? v * ra : 0.0;
+      Zeta[a + b * KL] = up ? W.U[a * LD + b] * ra : 0.0;
+      ZetaInv[a + b * KL] = up ? lr * rb : 0.0;
+    }
   }
   cluster.sync();  // every CTA has read the state before the leader updates it
   if (lead) {
@@ -814,7 +672,8 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
 
 // ------------------------------------------------------------------------------------ launchers
 
-// KP <= 8: one warp; KP >= 16: one CTA of 256 threads (setup) or a cluster of CTAs (loop).
+// Set-up: one warp (KP <= 8) or one CTA of 256 threads. Loop: a cluster of CTAs, computed 16 wide for
+// KP <= 8 (the identity outside s x s) and stored at the handle's width.
 #define MBPCG_SMALL_SWITCH(kp, WARP, CTA) \
   switch (kp) {                           \
     case 1: WARP(1); break;               \
@@ -834,17 +693,19 @@ void launch_small_sigma(cudaStream_t s, int kp, SolveState* st, const double* Gp
 }
 void launch_small_xi(cudaStream_t s, int kp, SolveState* st, const double* G1p, const double* Sigma, double* Xi,
                      double* T) {
-#define WARP(K) k_small_xi_w<K><<<1, 32, 0, s>>>(st, G1p, Sigma, Xi, T)
-#define CTA(K) k_small_xi_x<K><<<ClusterCfg<K>::CS, ClusterCfg<K>::NF, 0, s>>>(st, G1p, Sigma, Xi, T)
+#define WARP(K) k_small_xi_x<16, K><<<ClusterCfg<16>::CS, ClusterCfg<16>::NF, 0, s>>>(st, G1p, Sigma, Xi, T)
+#define CTA(K) k_small_xi_x<K, K><<<ClusterCfg<K>::CS, ClusterCfg<K>::NF, 0, s>>>(st, G1p, Sigma, Xi, T)
   MBPCG_SMALL_SWITCH(kp, WARP, CTA)
 #undef WARP
 #undef CTA
 }
 void launch_small_zeta(cudaStream_t s, int kp, SolveState* st, const double* G2nu, double* Sigma, double* Zeta,
                        double* ZetaInv, cudaGraphConditionalHandle cond, int use_cond) {
-#define WARP(K) k_small_zeta_w<K><<<1, 32, 0, s>>>(st, G2nu, Sigma, Zeta, ZetaInv, cond, use_cond)
+#define WARP(K)                                                                                    \
+  k_small_zeta_x<16, K><<<ClusterCfg<16>::CS, ClusterCfg<16>::NF, 0, s>>>(st, G2nu, Sigma, Zeta, ZetaInv, cond, \
+                                                                        use_cond)
 #define CTA(K) \
-  k_small_zeta_x<K><<<ClusterCfg<K>::CS, ClusterCfg<K>::NF, 0, s>>>(st, G2nu, Sigma, Zeta, ZetaInv, cond, use_cond)
+  k_small_zeta_x<K, K><<<ClusterCfg<K>::CS, ClusterCfg<K>::NF, 0, s>>>(st, G2nu, Sigma, Zeta, ZetaInv, cond, use_cond)
   MBPCG_SMALL_SWITCH(kp, WARP, CTA)
 #undef WARP
 #undef CTA
