@@ -407,6 +407,11 @@ def run_ours(args, world, rank, local):
             "gpu_launches": sum(launches_per_solve(i, dense, False, prec == mb.MBPCG_FP64_TC, mixed) for i in infos),
             "clocks": clk.summary(),
         }
+        if mixed:
+            u, c, t = solver.spmm_tuning()
+            line["spmm_autotune"] = {"unroll": u, "ctas_per_sm": c,
+                                     "times_us_(unroll,ctas_per_sm)": dict(zip(
+                                         ["4,4", "4,8", "4,16", "8,4", "8,8", "8,16"], [round(v, 2) for v in t]))}
         if fp64 is not None:
             f_ms = sum(f_times) / len(f_times)
             xfh = xf.cpu().numpy()

@@ -157,6 +157,17 @@ int mbpcg_set_launch_mode(mbpcg_handle h, int32_t mode);
 typedef enum { MBPCG_RESIDUAL_EXPLICIT = 0, MBPCG_RESIDUAL_IMPLICIT = 1 } mbpcg_residual_mode;
 int mbpcg_set_residual_mode(mbpcg_handle h, int32_t mode);
 
+/* Autotuner of the mixed-precision inner solve (MBPCG_MIXED_FP32 handles; MBPCG_ERR_INVALID
+ * otherwise). At create the FP32 product A P -- the dominant kernel of that solve -- is timed on the
+ * handle's own matrix in six launch shapes (4 or 8 nonzeros of a row in flight per thread; 4, 8 or
+ * 16 CTAs per SM; CUDA events, three launches each) and the fastest is kept. Every shape computes
+ * each row the same way, so the shape changes the time, never the result.
+ *   mbpcg_get_spmm_tuning: the kept shape and the six measured times (microseconds per launch, in
+ *     the order (4,4) (4,8) (4,16) (8,4) (8,8) (8,16) of (unroll, ctas_per_sm); times_us may be NULL).
+ *   mbpcg_set_spmm_shape: impose a shape (unroll 4 or 8, ctas_per_sm 4, 8 or 16). */
+int mbpcg_get_spmm_tuning(mbpcg_handle h, int32_t* unroll, int32_t* ctas_per_sm, float* times_us);
+int mbpcg_set_spmm_shape(mbpcg_handle h, int32_t unroll, int32_t ctas_per_sm);
+
 /* Release a handle (NULL is ignored). */
 void mbpcg_destroy(mbpcg_handle h);
 

@@ -17,7 +17,7 @@ from ._native import (  # noqa: F401  (re-exported C ABI names)
     MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,
     MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_FP64_TC, MBPCG_MIXED_FP32, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER,
     mbpcg_k_spmm_gram_f32, mbpcg_k_spmm_f32, mbpcg_set_residual_mode, MBPCG_RESIDUAL_EXPLICIT,
-    MBPCG_RESIDUAL_IMPLICIT)
+    MBPCG_RESIDUAL_IMPLICIT, mbpcg_get_spmm_tuning, mbpcg_set_spmm_shape)
 
 from ._native import (  # noqa: F401,E402
     mbpcg_server_create, mbpcg_server_destroy, mbpcg_server_get_stats, mbpcg_server_submit_csr, mbpcg_server_wait)
@@ -133,6 +133,15 @@ class Solver:
         if st not in (MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN):
             raise MBPCGError(st, "mbpcg_solve")
         return x, info.as_dict()
+
+    def spmm_tuning(self):
+        """(unroll, ctas_per_sm, times_us) the autotuner chose for the FP32 product (mixed handles)."""
+        return mbpcg_get_spmm_tuning(self.h)
+
+    def set_spmm_shape(self, unroll: int, ctas_per_sm: int):
+        st = mbpcg_set_spmm_shape(self.h, unroll, ctas_per_sm)
+        if st != MBPCG_OK:
+            raise MBPCGError(st, "mbpcg_set_spmm_shape")
 
     def run_iterations(self, b, U, iters: int):
         """Diagnostic: the state of the scaled system after exactly `iters` iterations, as torch

@@ -91,6 +91,9 @@ _SIGS = {
     "mbpcg_destroy": (None, [_P]),
     "mbpcg_set_launch_mode": (ctypes.c_int, [_P, _I32]),
     "mbpcg_set_residual_mode": (ctypes.c_int, [_P, _I32]),
+    "mbpcg_get_spmm_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                             ctypes.POINTER(ctypes.c_float)]),
+    "mbpcg_set_spmm_shape": (ctypes.c_int, [_P, _I32, _I32]),
     "mbpcg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mbpcg_last_error": (ctypes.c_char_p, []),
     "mbpcg_k_padded_width": (_I32, [_I32]),
@@ -308,3 +311,17 @@ def mbpcg_server_destroy(srv):
 
 def mbpcg_set_residual_mode(h, mode):
     return lib().mbpcg_set_residual_mode(h, mode)
+
+
+def mbpcg_get_spmm_tuning(h):
+    """(unroll, ctas_per_sm, [six measured microseconds]) of a mixed-precision handle's FP32 A P."""
+    u, c = _I32(), _I32()
+    t = (ctypes.c_float * 6)()
+    st = lib().mbpcg_get_spmm_tuning(h, ctypes.byref(u), ctypes.byref(c), t)
+    if st != MBPCG_OK:
+        raise MBPCGError(st, "mbpcg_get_spmm_tuning")
+    return int(u.value), int(c.value), [float(x) for x in t]
+
+
+def mbpcg_set_spmm_shape(h, unroll, ctas_per_sm):
+    return lib().mbpcg_set_spmm_shape(h, unroll, ctas_per_sm)

@@ -41,6 +41,7 @@ int set_err(int code, const char* fmt, ...) {
 
 constexpr size_t kAlign = 256;
 constexpr int kMixedRestarts = 12;       // refinement steps of the mixed-precision solve
+constexpr int kTuneVariants = 6;         // FP32 A P launch shapes tried by the autotuner
 constexpr double kMixedInnerTol = 1e-5;  // smallest relative tolerance asked of an FP32 inner solve
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -195,6 +196,9 @@ struct mbpcg_ctx {
   int graph_ready;
   int launch_mode;  // MBPCG_LAUNCH_GRAPH or MBPCG_LAUNCH_EAGER
   int rfree;        // MBPCG_RESIDUAL_IMPLICIT: R = W Sigma is not formed inside the loop
+  // launch shape of the FP32 A P of the mixed inner solve, picked by autotune_spmm_f at create
+  int spmm_unroll, spmm_ctas_per_sm, spmm_nb;
+  float spmm_us[kTuneVariants];
   int use_cond;     // 1 while the loop body is captured into the WHILE node
   cudaEvent_t e0, e1;
 };
@@ -353,6 +357,43 @@ int read_flag(mbpcg_ctx* h, int* flag) {
   return MBPCG_OK;
 }
 
+// Grid of the FP32 A P for `ctas_per_sm` CTAs per SM, at most one tile of rows per CTA.
+int spmm_grid(const Dims& dm, int ctas_per_sm) {
+  const int rows = rows_per_tile_f(dm.kp);
+  const long long tiles = ((long long)dm.n + rows - 1) / rows, cap = (long long)ctas_per_sm * dm.sms;
+  return (int)(tiles < cap ? tiles : cap);
+}
+
+// Autotuner of the FP32 A P (the dominant kernel of the mixed inner solve): times every launch shape
+// (unroll 4 or 8 nonzeros in flight, 4, 8 or 16 CTAs per SM) on this handle's own matrix, three
+// launches each after one untimed, and keeps the fastest. Every shape computes each row the same
+// way, so the choice changes the time, never the result.
+int autotune_spmm_f(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOpsF* ops = row_ops_f(dm.kp);
+  static const int unr[kTuneVariants] = {4, 4, 4, 8, 8, 8}, cps[kTuneVariants] = {4, 8, 16, 4, 8, 16};
+  float best = 1e30f;
+  for (int v = 0; v < kTuneVariants; ++v) {
+    const int nb = spmm_grid(dm, cps[v]);
+    ops->spmm(h->stream, nb, dm.n, h->rp, h->ci, h->av32, h->fU, h->fQ, nullptr, 0, nullptr, 0, unr[v]);
+    CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+    for (int r = 0; r < 3; ++r)
+      ops->spmm(h->stream, nb, dm.n, h->rp, h->ci, h->av32, h->fU, h->fQ, nullptr, 0, nullptr, 0, unr[v]);
+    CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    CUDA_TRY(cudaEventSynchronize(h->e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, h->e0, h->e1));
+    h->spmm_us[v] = ms * 1e3f / 3.f;
+    if (h->spmm_us[v] < best) {
+      best = h->spmm_us[v];
+      h->spmm_unroll = unr[v];
+      h->spmm_ctas_per_sm = cps[v];
+      h->spmm_nb = nb;
+    }
+  }
+  return MBPCG_OK;
+}
+
 // Diagonal, scaling vectors and the in-place scaled matrix (Section 1).
 int finish_create(mbpcg_ctx* h) {
   const int n = h->dm.n;
@@ -381,6 +422,11 @@ int finish_create(mbpcg_ctx* h) {
     if (h->wdiag != nullptr) k_to_f32<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->wdiag, h->wd32);
     else h->wd32 = nullptr;
     CUDA_TRY(cudaGetLastError());
+    h->spmm_unroll = 8;
+    h->spmm_ctas_per_sm = 8;
+    h->spmm_nb = spmm_grid(h->dm, 8);
+    int rc = autotune_spmm_f(h);
+    if (rc) return rc;
   }
   if (h->dm.tc) {
     oz_prepare_a(h->stream, n, h->A, h->oz_ea, h->oz_a);
@@ -475,7 +521,8 @@ void enqueue_mbpcg_setup_f(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   const RowOpsF* ops = row_ops_f(dm.kp);
   const int kp = dm.kp, n = dm.n;
-  ops->spmm(h->stream, dm.nb, n, h->rp, h->ci, h->av32, h->fU, h->fQ, h->part, dm.pstride, nullptr, 0);  // A U
+  ops->spmm(h->stream, h->spmm_nb, n, h->rp, h->ci, h->av32, h->fU, h->fQ, nullptr, 0, nullptr, 0,
+            h->spmm_unroll);  // A U
   ops->setup_norms(h->stream, dm.nb, n, h->rhs, h->d, h->bs, h->fQ, h->part, dm.pstride);
   enqueue_reduce(h, 3, nullptr);
   k_small_setup<<<1, 1, 0, h->stream>>>(h->st, h->red);
@@ -489,7 +536,7 @@ void enqueue_mbpcg_body_f(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   const RowOpsF* ops = row_ops_f(dm.kp);
   const int kp = dm.kp, n = dm.n;
-  ops->spmm(h->stream, dm.nb, n, h->rp, h->ci, h->av32, h->fP, h->fQ, nullptr, 0, h->st, 0);
+  ops->spmm(h->stream, h->spmm_nb, n, h->rp, h->ci, h->av32, h->fP, h->fQ, nullptr, 0, h->st, 0, h->spmm_unroll);
   ops->gram(h->stream, dm.nb, n, h->fP, h->fQ, h->part, dm.pstride, h->st);
   enqueue_reduce(h, npack(kp), h->st);
   launch_small_xi(h->stream, kp, h->st, h->red, h->Sigma, h->Xi, h->T);
@@ -867,6 +914,32 @@ int mbpcg_set_launch_mode(mbpcg_handle h, int32_t mode) {
   return MBPCG_OK;
 }
 
+int mbpcg_get_spmm_tuning(mbpcg_handle h, int32_t* unroll, int32_t* ctas_per_sm, float* times_us) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (!h->dm.mixed) return set_err(MBPCG_ERR_INVALID, "the FP32 product is tuned for MBPCG_MIXED_FP32 handles");
+  if (unroll) *unroll = h->spmm_unroll;
+  if (ctas_per_sm) *ctas_per_sm = h->spmm_ctas_per_sm;
+  if (times_us)
+    for (int v = 0; v < kTuneVariants; ++v) times_us[v] = h->spmm_us[v];
+  return MBPCG_OK;
+}
+
+int mbpcg_set_spmm_shape(mbpcg_handle h, int32_t unroll, int32_t ctas_per_sm) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (!h->dm.mixed) return set_err(MBPCG_ERR_INVALID, "the FP32 product is tuned for MBPCG_MIXED_FP32 handles");
+  if ((unroll != 4 && unroll != 8) || (ctas_per_sm != 4 && ctas_per_sm != 8 && ctas_per_sm != 16))
+    return set_err(MBPCG_ERR_INVALID, "unroll must be 4 or 8 and ctas_per_sm 4, 8 or 16");
+  if (h->graph_ready) {  // the captured launches change
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->exec);
+    h->graph_ready = 0;
+  }
+  h->spmm_unroll = unroll;
+  h->spmm_ctas_per_sm = ctas_per_sm;
+  h->spmm_nb = spmm_grid(h->dm, ctas_per_sm);
+  return MBPCG_OK;
+}
+
 int mbpcg_set_residual_mode(mbpcg_handle h, int32_t mode) {
   if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
   if (mode != MBPCG_RESIDUAL_EXPLICIT && mode != MBPCG_RESIDUAL_IMPLICIT)
@@ -949,7 +1022,7 @@ int mbpcg_k_spmm_gram_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_
   cudaStream_t st = (cudaStream_t)stream;
   double* part = static_cast<double*>(scratch);
   double* red = part + (size_t)dm.nbmax * dm.pstride;
-  row_ops_f(dm.kp)->spmm(st, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0);
+  row_ops_f(dm.kp)->spmm(st, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0, 8);
   row_ops_f(dm.kp)->gram(st, dm.nb, n, P, AP, part, dm.pstride, nullptr);
   k_reduce<<<npack(dm.kp), 128, 0, st>>>(part, dm.nb, dm.pstride, red, nullptr);
   k_unpack_full<<<1, 256, 0, st>>>(red, dm.kp, s, G);
@@ -962,7 +1035,7 @@ int mbpcg_k_spmm_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, 
   if (n < 1 || s < 1 || s > 32 || !row_ptr || !P || !AP) return set_err(MBPCG_ERR_INVALID, "bad arguments");
   Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
   apply_mixed(dm);
-  row_ops_f(dm.kp)->spmm((cudaStream_t)stream, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0);
+  row_ops_f(dm.kp)->spmm((cudaStream_t)stream, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0, 8);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

@@ -63,7 +63,7 @@ inline const RowOps* row_ops(int kp) {
 struct RowOpsF {
   int kp;
   void (*spmm)(cudaStream_t, int nb, int n, const int* rp, const int* ci, const float* av, const float* P, float* Q,
-               double* part, int pstride, const SolveState* st, int gram);
+               double* part, int pstride, const SolveState* st, int gram, int unroll);  // unroll 4 or 8 (no gram)
   void (*gram)(cudaStream_t, int nb, int n, const float* X, const float* Y, double* part, int pstride,
                const SolveState* st);
   void (*axpy)(cudaStream_t, int nb, int n, const float* P, const float* Q, const float* W, float* R, float* Xt,
@@ -89,6 +89,9 @@ const RowOpsF* row_ops_f_kp4();
 const RowOpsF* row_ops_f_kp8();
 const RowOpsF* row_ops_f_kp16();
 const RowOpsF* row_ops_f_kp32();
+
+// rows of one CTA tile in the FP32 kernels (four threads per row above KP = 4)
+inline int rows_per_tile_f(int kp) { return kp <= 4 ? 256 : 256 / (kp / 4); }
 
 inline const RowOpsF* row_ops_f(int kp) {
   switch (kp) {

@@ -139,11 +139,11 @@ struct GramTileF {
 
 // Q = A P (FP32 CSR values, FP32 accumulation) and, when GRAM, the Dot2 partials of the upper
 // triangle of P^T Q (Algorithm 1, the A P product and the Gram that defines Xi). Four threads own a
-// row (16-byte vectors of P), eight nonzeros of a row are in flight per thread. On the 27-point
+// row (16-byte vectors of P), UNR nonzeros of a row are in flight per thread. On the 27-point
 // stencil at KP = 16 this form is bound by the gathers of P rows through L2 (27 x 64 bytes per row),
 // not by the CSR stream: staging the CSR slice of a warp in shared memory or prefetching it did
 // not make it faster.
-template <int KP, bool GRAM>
+template <int KP, bool GRAM, int UNR = 8>
 __global__ void __launch_bounds__(kThreads)
 k_spmm_f(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float* __restrict__ av,
          const float* __restrict__ P, float* __restrict__ Q, double* __restrict__ part, int pstride,
@@ -166,7 +166,7 @@ k_spmm_f(int n, const int* __restrict__ rp, const int* __restrict__ ci, const fl
     for (int c = 0; c < C::CPT; ++c) acc[c] = pv[c] = 0.f;
     if (i < r1) {
       const int pe = __ldg(rp + i + 1);
-#pragma unroll 8
+#pragma unroll UNR
       for (int p = __ldg(rp + i); p < pe; ++p) {
         const int col = __ldg(ci + p);
         const float a = __ldg(av + p);

@@ -127,3 +127,31 @@ def test_mixed_precision_is_refused_where_it_does_not_apply(mb):
         assert st == mb._native.MBPCG_ERR_INVALID
     finally:
         sv.close()
+
+
+def test_spmm_autotuner_picks_the_fastest_shape_and_never_changes_results(mb):
+    A = wl.stencil27(24, 5)
+    n, s = A.n, 16
+    b = wl.rhs(n, 0)
+    U = wl.initial_block(n, s, 1)
+    sv = mb.Solver(A, s=s, precision=mb.MBPCG_MIXED_FP32)
+    try:
+        unroll, cps, times = sv.spmm_tuning()
+        assert unroll in (4, 8) and cps in (4, 8, 16) and len(times) == 6 and min(times) > 0.0
+        order = [(4, 4), (4, 8), (4, 16), (8, 4), (8, 8), (8, 16)]
+        assert times[order.index((unroll, cps))] == min(times)
+        x0, i0 = sv.solve(b, U, tol=1e-10, maxit=100000)
+        for shape in ((4, 4), (8, 16)):
+            sv.set_spmm_shape(*shape)
+            x, info = sv.solve(b, U, tol=1e-10, maxit=100000)
+            assert np.array_equal(x, x0) and info["iterations"] == i0["iterations"]
+        with pytest.raises(mb.MBPCGError):
+            sv.set_spmm_shape(3, 8)
+    finally:
+        sv.close()
+    fp = mb.Solver(A, s=s)
+    try:
+        with pytest.raises(mb.MBPCGError):
+            fp.spmm_tuning()
+    finally:
+        fp.close()
