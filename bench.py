@@ -172,6 +172,29 @@ def recorded_traffic(kernel, workload, s):
     return rec.get("dram_bytes_per_launch")
 
 
+def read_ceiling_gbs(stream, flush):
+    """HBM read-only bandwidth of this GPU right now: a sum over a 1 GiB FP32 tensor (torch's own
+    reduction), L2 flushed before each run. A read-only stream does not reach the copy bandwidth
+    of MEASURED_PEAKS.json; this is the ceiling of the kernels that only read A."""
+    import torch
+    x = torch.ones(1 << 28, dtype=torch.float32, device=flush.device)
+    out = torch.empty((), dtype=torch.float32, device=flush.device)
+    ts = []
+    with torch.cuda.stream(stream):
+        for i in range(6):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            torch.sum(x, dim=0, out=out)
+            ev1.record(stream)
+            ev1.synchronize()
+            if i >= 2:
+                ts.append(ev0.elapsed_time(ev1))
+    del x
+    return 4 * (1 << 28) / (statistics.median(ts) * 1e-3) / 1e9
+
+
 def launches_per_solve(info, dense, algo_cg, tc=False, mixed=False):
     """Kernels of ours launched by one solve call (the counter of the graph the library builds). The
     tensor-core dense product is four kernels (column exponents, digits of P, MMAs, split sum); the
@@ -341,6 +364,7 @@ def run_ours(args, world, rank, local):
                 ev1.synchronize()
                 g_ms.append(ev0.elapsed_time(ev1))
         gram_ms = sum(g_ms) / len(g_ms)
+    read_gbs = read_ceiling_gbs(stream, flush) if (mixed or tc) else None
     if mixed:
         peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
         hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -351,6 +375,7 @@ def run_ours(args, world, rank, local):
                     "kernel_ms": round(k_avg, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
                     "with_gram_ms": round(gram_ms, 5),
                     "with_gram_frac": round(nbytes / (gram_ms * 1e-3) / 1e9 / hbm_peak, 4),
+                    "read_ceiling_gbs": round(read_gbs, 1), "frac_of_read_ceiling": round(achieved_gbs / read_gbs, 4),
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
     elif tc:
         peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
@@ -361,6 +386,7 @@ def run_ours(args, world, rank, local):
                     "frac": round(achieved_gbs / hbm_peak, 4), "traffic": recorded_traffic(kname, args.workload, s),
                     "kernel_ms": round(k_avg, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
                     "fp64_equiv_tflops": round(achieved_tflops, 3),
+                    "read_ceiling_gbs": round(read_gbs, 1), "frac_of_read_ceiling": round(achieved_gbs / read_gbs, 4),
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
     else:
         roofline = {"bound": "alu", "kernel": f"{kname}<{kp}> (FP64 pipe)", "achieved": round(achieved_tflops, 4),

@@ -137,7 +137,7 @@ __global__ void k_cg_finish(int n, const double* xbar, const double* d, double* 
 // FP64-accurate dense product on the BF16 tensor cores (ozaki_tc.cu)
 size_t oz_a_tiles_bytes(int n);
 size_t oz_p_chunks_bytes(int n, int kp);
-int oz_ksplit(int n, int sms);
+int oz_ksplit(int n, int sms);  // partial slices of Q the product needs (Qpart holds this many n x kp blocks)
 void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* Atiles);
 // part != NULL: also the CTA partials of P^T (A P) over nb balanced row ranges (stride pstride).
 // exp_ready: the column exponents of P are already in emaxP (written by the W/P update).

@@ -45,6 +45,7 @@ __device__ __forceinline__ bool mbar_test_parity(uint64_t* bar, uint32_t parity)
 
 // Wait for the phase with the given parity to complete; false after the cycle budget runs out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_test_parity(bar, parity)) return true;  // the common case: no clock read
   const long long t0 = clock64();
   while (!mbar_test_parity(bar, parity)) {
     if (clock64() - t0 > (1LL << 31)) return false;
@@ -58,6 +59,24 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_addr(dst)),
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// L2 policy for data read once per pass and too large for L2: its lines are the first to go, so
+// they do not push out data that is reused (createpolicy, sm_80+).
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// tma_load_1d with an L2 cache policy for the source lines.
+__device__ __forceinline__ void tma_load_1d_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
       : "memory");
 }
 

@@ -140,10 +140,12 @@ def test_cholesky_kernel_breakdown(mb):
 
 
 @pytest.mark.parametrize("s", [1, 4, 9, 16, 32])
-@pytest.mark.parametrize("n", [64, 300, 1031])
+@pytest.mark.parametrize("n", [64, 300, 1031, 2049])
 def test_dense_tc_product_matches_oracle(mb, orc, n, s):
     """The tensor-core (exact digit splitting) product against the FP64 oracle: the error must be at
-    the FP64 rounding level of |A||P| entry by entry (an FP64 GEMM's own bound is n eps |A||P|)."""
+    the FP64 rounding level of |A||P| entry by entry (an FP64 GEMM's own bound is n eps |A||P|).
+    On 152 SMs, n = 1031 splits 153 one-chunk windows over 144 CTAs and n = 2049 splits 289
+    two-chunk windows (the last of each tile one chunk) over 136 CTAs: CTA ranges cross row tiles."""
     D = wl.dense_spd(n, 5, 0.0, 6.0)
     P, kp = padded_block(n, s, 6)
     P[:, :s] *= 10.0 ** (3 * wl.uniform_pm1(9, 77, s))[None, :]  # columns of very different scales
