@@ -36,10 +36,19 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 L2_FLUSH_BYTES = 256 << 20
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA pipe (no tensor cores)
 
 WORKLOADS = {
     "dense4096": dict(desc="dense SPD n=4096, A=Q diag(lambda) Q^T, lambda=10^U[0,6], b,U~U(-1,1), FP64, tol 1e-8",
-                      precond=0, tol=1e-8, s=32, precision="tc"),
+                      precond=0, tol=1e-8, s=32, precision="tc",
+                      mixed_desc="dense SPD n=4096, A=Q diag(lambda) Q^T, lambda=10^U[0,6], b,U~U(-1,1); FP32 A and "
+                                 "blocks with FP32 accumulation, FP64-class Grams, FP64 k x k and FP64 refinement "
+                                 "to relres 1e-10", mixed_tol=1e-10),
+    "dense4096_k1e4": dict(desc="dense SPD n=4096, A=Q diag(lambda) Q^T, lambda=10^U[0,4], b,U~U(-1,1), FP64, "
+                                "tol 1e-8", precond=0, tol=1e-8, s=32, precision="tc",
+                           mixed_desc="dense SPD n=4096, A=Q diag(lambda) Q^T, lambda=10^U[0,4], b,U~U(-1,1); FP32 A "
+                                      "and blocks with FP32 accumulation, FP64-class Grams, FP64 k x k and FP64 "
+                                      "refinement to relres 1e-10", mixed_tol=1e-10),
     "poisson64": dict(desc="2D 5-point Poisson 64x64 (n=4096, nnz=20224), CSR int32/FP64, tol 1e-8",
                       precond=0, tol=1e-8, s=4),
     "diffusion128": dict(desc="3D 7-point variable-coefficient diffusion 128^3 (n=2097152, nnz=14581760), "
@@ -54,6 +63,8 @@ WORKLOADS = {
 def make_matrix(name):
     if name == "dense4096":
         return wl.dense_spd(4096, 0)
+    if name == "dense4096_k1e4":
+        return wl.dense_spd(4096, 0, 0.0, 4.0)
     if name == "poisson64":
         return wl.poisson2d(64)
     if name == "diffusion128":
@@ -229,14 +240,19 @@ def run_ours(args, world, rank, local):
     pname = args.precision or cfg.get("precision", "fp64")
     if pname == "tc" and dense:
         prec = mb.MBPCG_FP64_TC
-    elif pname == "mixed" and not dense:
+    elif pname == "mixed":
         prec = mb.MBPCG_MIXED_FP32
     else:
         prec, pname = mb.MBPCG_FP64, "fp64"
     mixed = prec == mb.MBPCG_MIXED_FP32
+    # the mixed configuration of a workload may have its own tolerance (refinement to 1e-10)
+    tol = cfg.get("mixed_tol", cfg["tol"]) if mixed else cfg["tol"]
+    desc = cfg.get("mixed_desc", cfg["desc"]) if mixed else cfg["desc"]
     rmode = mb.MBPCG_RESIDUAL_IMPLICIT if args.residual == "implicit" else mb.MBPCG_RESIDUAL_EXPLICIT
     solver = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode, precision=prec, residual_mode=rmode)
-    fp64 = mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode) if mixed else None
+    # the FP64 solve the mixed one is compared with: the fastest FP64 path (tensor cores for dense A)
+    fp64 = (mb.Solver(A, s=s, precond=cfg["precond"], launch_mode=mode,
+                      precision=mb.MBPCG_FP64_TC if dense else mb.MBPCG_FP64) if mixed else None)
     cg = mb.Solver(A, algo=mb.MBPCG_ALGO_CG, precond=cfg["precond"], launch_mode=mode)
     stream = solver.stream
     bd = torch.as_tensor(b, device=dev)
@@ -251,7 +267,7 @@ def run_ours(args, world, rank, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(sv.stream)
-            x, info = sv.solve(bd, Uarg, tol=cfg["tol"], maxit=400000)
+            x, info = sv.solve(bd, Uarg, tol=tol, maxit=400000)
             e1.record(sv.stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -297,7 +313,19 @@ def run_ours(args, world, rank, local):
     P = torch.as_tensor(np.ascontiguousarray(np.pad(U, ((0, 0), (0, kp - s)))), device=dev)
     AP = torch.empty_like(P)
     tc = dense and prec == mb.MBPCG_FP64_TC
-    if tc:
+    launch_gram = None
+    if dense and mixed:
+        Ad = torch.as_tensor(np.asfortranarray(A.a).ravel(order="F"), device=dev)
+        ftb = mb.mbpcg_k_dense_f32_bytes(n)
+        ftiles = torch.empty(ftb // 4, dtype=torch.float32, device=dev)
+        mb.mbpcg_k_dense_f32_prepare(n, Ad, ftiles, ftb, stream.cuda_stream)  # FP32 tiles of A, once
+        P = P.float()
+        AP = torch.empty_like(P)
+        launch = lambda: mb.mbpcg_k_dense_f32(n, ftiles, s, P, AP, stream.cuda_stream)  # noqa: E731
+        kname = "k_dense_f"
+        flops = 2.0 * n * n * s
+        nbytes = 4.0 * n * n + 8.0 * n * kp  # FP32 A read once, P in, AP out
+    elif tc:
         Ad = torch.as_tensor(np.asfortranarray(A.a).ravel(order="F"), device=dev)
         tcb = mb.mbpcg_k_dense_tc_scratch_bytes(n, s)
         tcs = torch.empty(tcb, dtype=torch.uint8, device=dev)
@@ -351,7 +379,7 @@ def run_ours(args, world, rank, local):
     k_avg = sum(k_ms) / len(k_ms)
     achieved_tflops = flops / (k_avg * 1e-3) / 1e12
     gram_ms = None
-    if mixed:
+    if launch_gram is not None:
         with torch.cuda.stream(stream):
             g_ms = []
             for _ in range(max(3, args.kernel_launches // 2)):
@@ -365,7 +393,28 @@ def run_ours(args, world, rank, local):
                 g_ms.append(ev0.elapsed_time(ev1))
         gram_ms = sum(g_ms) / len(g_ms)
     read_gbs = read_ceiling_gbs(stream, flush) if (mixed or tc) else None
-    if mixed:
+    if mixed and dense:
+        # FP32 A P on the CUDA cores: 16 flop per byte of A at KP = 32, at the FP32 ridge of this GPU;
+        # the roof with the higher utilisation is the one that binds
+        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        achieved_gbs = nbytes / (k_avg * 1e-3) / 1e9
+        flops_pad = 2.0 * n * n * kp  # the kernel computes all KP columns
+        fp32_tflops = flops_pad / (k_avg * 1e-3) / 1e12
+        alu = fp32_tflops / FP32_PEAK_TFLOPS > achieved_gbs / hbm_peak
+        roofline = {"bound": "alu" if alu else "hbm",
+                    "kernel": f"{kname}<{kp}> (FP32 dense A P on the CUDA cores, the product alone)",
+                    "achieved": round(fp32_tflops if alu else achieved_gbs, 3 if alu else 1),
+                    "peak": round(FP32_PEAK_TFLOPS, 2) if alu else hbm_peak, "unit": "TFLOP/s" if alu else "GB/s",
+                    "frac": round(fp32_tflops / FP32_PEAK_TFLOPS if alu else achieved_gbs / hbm_peak, 4),
+                    "traffic": recorded_traffic(kname, args.workload, s),
+                    "kernel_ms": round(k_avg, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops_pad,
+                    "hbm_gbs": round(achieved_gbs, 1), "hbm_frac": round(achieved_gbs / hbm_peak, 4),
+                    "fp32_tflops": round(fp32_tflops, 3), "fp32_frac": round(fp32_tflops / FP32_PEAK_TFLOPS, 4),
+                    "read_ceiling_gbs": round(read_gbs, 1), "frac_of_read_ceiling": round(achieved_gbs / read_gbs, 4),
+                    "peak_note": ("FP32: derived, 152 SMs x 128 FMA/clk x 2 x 2.07 GHz; HBM: measured copy bandwidth "
+                                  "(MEASURED_PEAKS.json hbm_gbs)" if peaks else "FP32 derived; HBM fallback")}
+    elif mixed:
         peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
         hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
         achieved_gbs = nbytes / (k_avg * 1e-3) / 1e9
@@ -404,7 +453,7 @@ def run_ours(args, world, rank, local):
     e2e = []
     for it in range(args.steps + 1):
         t1 = time.perf_counter()
-        st, inf = mb.mbpcg_solve(solver.h, b_pin.data_ptr(), U_pin.data_ptr(), cfg["tol"], 100000, x_pin.data_ptr())
+        st, inf = mb.mbpcg_solve(solver.h, b_pin.data_ptr(), U_pin.data_ptr(), tol, 400000, x_pin.data_ptr())
         t2 = time.perf_counter()
         if it > 0:
             e2e.append((t2 - t1) * 1e3)
@@ -416,8 +465,8 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": round(ms_per_step, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-            "config": {"workload": cfg["desc"], "n": n, "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
-                       "tol": cfg["tol"], "l2": "flushed before every step (256 MB write)",
+            "config": {"workload": desc, "n": n, "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
+                       "tol": tol, "l2": "flushed before every step (256 MB write)",
                        "launch_mode": args.launch_mode, "precision": pname, "residual": args.residual,
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "iterations": info["iterations"], "restarts": info["restarts"], "relres_true": relres_check,
@@ -433,7 +482,7 @@ def run_ours(args, world, rank, local):
             "gpu_launches": sum(launches_per_solve(i, dense, False, prec == mb.MBPCG_FP64_TC, mixed) for i in infos),
             "clocks": clk.summary(),
         }
-        if mixed:
+        if mixed and not dense:
             u, c, t = solver.spmm_tuning()
             line["spmm_autotune"] = {"unroll": u, "ctas_per_sm": c,
                                      "times_us_(unroll,ctas_per_sm)": dict(zip(

@@ -59,8 +59,9 @@ typedef enum { MBPCG_PRECOND_NONE = 0, MBPCG_PRECOND_JACOBI = 1 } mbpcg_precond;
 typedef enum { MBPCG_ALGO_MBPCG = 0, MBPCG_ALGO_CG = 1 } mbpcg_algo;
 
 /* Arithmetic of the n-proportional work. FP64: everything in double precision on the FP64 pipe.
- * MIXED_FP32 (CSR A, MBPCG only): the inner solves keep the n x s blocks and the (scaled) matrix
- * values in FP32 and do the products and block updates in FP32 with FP32 accumulation; the s x s
+ * MIXED_FP32 (MBPCG only; CSR or dense A): the inner solves keep the n x s blocks and the (scaled)
+ * matrix in FP32 (a dense A adds an FP32 copy, n x round_up(n, 32) floats, to the workspace) and do
+ * the products and block updates in FP32 with FP32 accumulation; the s x s
  * Grams and norms are accumulated with FP64-class accuracy (compensated FP32 dot products, Ogita,
  * Rump & Oishi 2005), the s x s Cholesky steps run in FP64, and the true residual b - A x and x
  * itself are FP64: the true-residual restarts are an FP64 iterative refinement loop (at most 12
@@ -157,8 +158,8 @@ int mbpcg_set_launch_mode(mbpcg_handle h, int32_t mode);
 typedef enum { MBPCG_RESIDUAL_EXPLICIT = 0, MBPCG_RESIDUAL_IMPLICIT = 1 } mbpcg_residual_mode;
 int mbpcg_set_residual_mode(mbpcg_handle h, int32_t mode);
 
-/* Autotuner of the mixed-precision inner solve (MBPCG_MIXED_FP32 handles; MBPCG_ERR_INVALID
- * otherwise). At create the FP32 product A P -- the dominant kernel of that solve -- is timed on the
+/* Autotuner of the mixed-precision inner solve (MBPCG_MIXED_FP32 CSR handles; MBPCG_ERR_INVALID
+ * otherwise: the dense FP32 product has one launch shape). At create the FP32 product A P -- the dominant kernel of that solve -- is timed on the
  * handle's own matrix in six launch shapes (4 or 8 nonzeros of a row in flight per thread; 4, 8 or
  * 16 CTAs per SM; CUDA events, three launches each) and the fastest is kept. Every shape computes
  * each row the same way, so the shape changes the time, never the result.

@@ -65,6 +65,25 @@ int mbpcg_k_spmm_gram_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_
 int mbpcg_k_spmm_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const float* vals,
                      int32_t s, const float* P, float* AP, void* stream);
 
+/*
+ * The FP32 dense product of the mixed-precision inner solve on a dense A (MBPCG_MIXED_FP32 with
+ * mbpcg_create_dense; the Xi step's A P of Algorithm 1), in two calls like the tensor-core product:
+ *   mbpcg_k_dense_f32_bytes: size of the FP32 copy of A (tiles of 256 rows x 32 columns, zero
+ *     past n; 0 for n < 1).
+ *   mbpcg_k_dense_f32_prepare: writes that copy from A (device, column-major FP64 n x n, symmetric:
+ *     row i is read as column i) into `tiles` (device, 16-byte aligned, tiles_bytes at least
+ *     mbpcg_k_dense_f32_bytes(n)). Each entry is A rounded to FP32.
+ *   mbpcg_k_dense_f32: AP = A P from the tiles, FP32 accumulation, in the solver's launch
+ *     configuration. P, AP: device FP32 row-major n x KP (KP = mbpcg_k_padded_width(s)), P
+ *     16-byte aligned; AP is written, columns s..KP-1 get A times P's (zero) padding. The order of
+ *     accumulation is fixed for a given device (K split over a cluster of CTAs, summed in rank
+ *     order), so repeated calls give identical bits; error <= n 2^-24 |A||P|. No scratch.
+ * MBPCG_ERR_INVALID for bad sizes, pointers or alignment.
+ */
+size_t mbpcg_k_dense_f32_bytes(int32_t n);
+int mbpcg_k_dense_f32_prepare(int32_t n, const double* A, void* tiles, size_t tiles_bytes, void* stream);
+int mbpcg_k_dense_f32(int32_t n, const void* tiles, int32_t s, const float* P, float* AP, void* stream);
+
 /* Same for dense symmetric A (column-major n x n; row i is read as column i). */
 int mbpcg_k_dense_gram(int32_t n, const double* A, int32_t s, const double* P, double* AP,
                        double* G, void* scratch, size_t scratch_bytes, void* stream);

@@ -16,7 +16,8 @@ from ._native import (  # noqa: F401  (re-exported C ABI names)
     mbpcg_set_launch_mode, mbpcg_solve, mbpcg_solve_dev, mbpcg_workspace_size_csr, mbpcg_workspace_size_dense, status_string, last_error,
     MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,
     MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_FP64_TC, MBPCG_MIXED_FP32, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER,
-    mbpcg_k_spmm_gram_f32, mbpcg_k_spmm_f32, mbpcg_set_residual_mode, MBPCG_RESIDUAL_EXPLICIT,
+    mbpcg_k_spmm_gram_f32, mbpcg_k_spmm_f32, mbpcg_k_dense_f32, mbpcg_k_dense_f32_bytes, mbpcg_k_dense_f32_prepare,
+    mbpcg_set_residual_mode, MBPCG_RESIDUAL_EXPLICIT,
     MBPCG_RESIDUAL_IMPLICIT, mbpcg_get_spmm_tuning, mbpcg_set_spmm_shape)
 
 from ._native import (  # noqa: F401,E402

@@ -108,6 +108,9 @@ _SIGS = {
     "mbpcg_k_spmm": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
     "mbpcg_k_spmm_gram_f32": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_spmm_f32": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
+    "mbpcg_k_dense_f32_bytes": (ctypes.c_size_t, [_I32]),
+    "mbpcg_k_dense_f32_prepare": (ctypes.c_int, [_I32, _P, _P, ctypes.c_size_t, _P]),
+    "mbpcg_k_dense_f32": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P]),
     "mbpcg_k_dense_product": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P]),
     "mbpcg_server_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, ctypes.c_uint64]),
     "mbpcg_server_submit_csr": (ctypes.c_int, [_P, _I32, _I64, _P, _P, _P, _P, _I32, _I32, _I32, _D, _I32,
@@ -248,6 +251,18 @@ def mbpcg_k_spmm_gram_f32(n, row_ptr, col_idx, vals, s, P, AP, G, scratch, scrat
 
 def mbpcg_k_spmm_f32(n, row_ptr, col_idx, vals, s, P, AP, stream=None):
     return lib().mbpcg_k_spmm_f32(n, ptr(row_ptr), ptr(col_idx), ptr(vals), s, ptr(P), ptr(AP), stream)
+
+
+def mbpcg_k_dense_f32_bytes(n):
+    return lib().mbpcg_k_dense_f32_bytes(n)
+
+
+def mbpcg_k_dense_f32_prepare(n, A, tiles, tiles_bytes, stream=None):
+    return lib().mbpcg_k_dense_f32_prepare(n, ptr(A), ptr(tiles), tiles_bytes, stream)
+
+
+def mbpcg_k_dense_f32(n, tiles, s, P, AP, stream=None):
+    return lib().mbpcg_k_dense_f32(n, ptr(tiles), s, ptr(P), ptr(AP), stream)
 
 
 def mbpcg_k_dense_product(n, A, s, P, AP, stream=None):

@@ -100,6 +100,8 @@ struct Layout {
   size_t part, red, small, st, flag;  // reductions, k x k matrices, control block
   size_t oz_a, oz_ea, oz_p, oz_ep, oz_q; // tensor-core product: digits of A and P, exponents, split sums
   size_t av32, wd32;                     // mixed precision: FP32 copies of the scaled values and of diag A
+  size_t A32;                            // mixed precision, dense A: FP32 tiles (dense_f32_tiles_bytes)
+  size_t xbest;                          // mixed precision: best iterate of the refinement loop
   size_t total;
 };
 
@@ -115,6 +117,10 @@ Layout make_layout(const Dims& dm) {
   const size_t n = (size_t)dm.n;
   if (dm.dense) {
     L.A = take(n * n * sizeof(double));
+    if (dm.mixed) {
+      L.A32 = take(dense_f32_tiles_bytes(dm.n));
+      L.wd32 = take(n * sizeof(float));
+    }
   } else {
     L.rp = take((n + 1) * sizeof(int));
     L.ci = take((size_t)dm.nnz * sizeof(int));
@@ -131,6 +137,7 @@ Layout make_layout(const Dims& dm) {
   L.rhs = take(n * sizeof(double));
   L.bs = take(n * sizeof(double));
   L.x = take(n * sizeof(double));
+  if (dm.mixed) L.xbest = take(n * sizeof(double));
   if (dm.algo == MBPCG_ALGO_MBPCG) {
     // Q and V are taken back to back: together they also stage a column-major n x s FP64 U
     const size_t blk = n * dm.kp * (dm.mixed ? sizeof(float) : sizeof(double));
@@ -178,7 +185,7 @@ struct mbpcg_ctx {
   Layout L;
   // device pointers
   int *rp, *ci, *flag;
-  double *av, *A, *diag, *d, *sqd, *wdiag, *b, *rhs, *bs, *x;
+  double *av, *A, *diag, *d, *sqd, *wdiag, *b, *rhs, *bs, *x, *xbest;
   double *U, *X0, *Xt, *R, *W, *P, *Q, *V;
   double *r, *w, *xb, *p, *sv;
   double *part, *red;
@@ -191,6 +198,7 @@ struct mbpcg_ctx {
   // mixed precision (FP32 views of the block buffers)
   float *fU, *fX0, *fXt, *fR, *fW, *fP, *fQ, *fV;
   float *av32, *wd32;
+  float* A32;  // dense A in FP32 tiles
   cudaGraphExec_t exec;
   cudaGraphConditionalHandle cond;
   int graph_ready;
@@ -230,6 +238,7 @@ void bind(mbpcg_ctx* h) {
   h->rhs = at<double>(h, L.rhs);
   h->bs = at<double>(h, L.bs);
   h->x = at<double>(h, L.x);
+  h->xbest = h->dm.mixed ? at<double>(h, L.xbest) : nullptr;
   if (h->algo == MBPCG_ALGO_MBPCG) {
     h->U = at<double>(h, L.U);
     h->X0 = at<double>(h, L.X0);
@@ -269,8 +278,9 @@ void bind(mbpcg_ctx* h) {
     h->fP = at<float>(h, L.P);
     h->fQ = at<float>(h, L.Q);
     h->fV = at<float>(h, L.V);
-    h->av32 = at<float>(h, L.av32);
+    h->av32 = h->dm.dense ? nullptr : at<float>(h, L.av32);
     h->wd32 = at<float>(h, L.wd32);
+    h->A32 = h->dm.dense ? at<float>(h, L.A32) : nullptr;
   }
   if (h->dm.tc) {
     h->oz_a = at<uint8_t>(h, L.oz_a);
@@ -418,15 +428,18 @@ int finish_create(mbpcg_ctx* h) {
     h->wdiag = nullptr;
   }
   if (h->dm.mixed) {
-    k_to_f32<<<1024, 256, 0, h->stream>>>((long long)h->dm.nnz, h->av, h->av32);
+    if (h->dm.dense) k_dense_to_f32_tiles<<<4 * 152, 256, 0, h->stream>>>(n, h->A, h->A32);
+    else k_to_f32<<<1024, 256, 0, h->stream>>>((long long)h->dm.nnz, h->av, h->av32);
     if (h->wdiag != nullptr) k_to_f32<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->wdiag, h->wd32);
     else h->wd32 = nullptr;
     CUDA_TRY(cudaGetLastError());
-    h->spmm_unroll = 8;
-    h->spmm_ctas_per_sm = 8;
-    h->spmm_nb = spmm_grid(h->dm, 8);
-    int rc = autotune_spmm_f(h);
-    if (rc) return rc;
+    if (!h->dm.dense) {
+      h->spmm_unroll = 8;
+      h->spmm_ctas_per_sm = 8;
+      h->spmm_nb = spmm_grid(h->dm, 8);
+      int rc = autotune_spmm_f(h);
+      if (rc) return rc;
+    }
   }
   if (h->dm.tc) {
     oz_prepare_a(h->stream, n, h->A, h->oz_ea, h->oz_a);
@@ -517,12 +530,17 @@ void enqueue_mbpcg_exit(mbpcg_ctx* h) {
 
 // Mixed precision (MBPCG_MIXED_FP32): the same steps with the FP32 row kernels; the reductions,
 // the k x k steps, the exit combination and the true residual stay as above.
+void enqueue_product_f(mbpcg_ctx* h, const RowOpsF* ops, const float* X, float* Y, const SolveState* st) {
+  const Dims& dm = h->dm;
+  if (dm.dense) dense_f32_product(h->stream, dm.kp, dm.n, dm.sms, h->A32, X, Y, st);
+  else ops->spmm(h->stream, h->spmm_nb, dm.n, h->rp, h->ci, h->av32, X, Y, nullptr, 0, st, 0, h->spmm_unroll);
+}
+
 void enqueue_mbpcg_setup_f(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   const RowOpsF* ops = row_ops_f(dm.kp);
   const int kp = dm.kp, n = dm.n;
-  ops->spmm(h->stream, h->spmm_nb, n, h->rp, h->ci, h->av32, h->fU, h->fQ, nullptr, 0, nullptr, 0,
-            h->spmm_unroll);  // A U
+  enqueue_product_f(h, ops, h->fU, h->fQ, nullptr);  // A U
   ops->setup_norms(h->stream, dm.nb, n, h->rhs, h->d, h->bs, h->fQ, h->part, dm.pstride);
   enqueue_reduce(h, 3, nullptr);
   k_small_setup<<<1, 1, 0, h->stream>>>(h->st, h->red);
@@ -536,7 +554,7 @@ void enqueue_mbpcg_body_f(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   const RowOpsF* ops = row_ops_f(dm.kp);
   const int kp = dm.kp, n = dm.n;
-  ops->spmm(h->stream, h->spmm_nb, n, h->rp, h->ci, h->av32, h->fP, h->fQ, nullptr, 0, h->st, 0, h->spmm_unroll);
+  enqueue_product_f(h, ops, h->fP, h->fQ, h->st);
   ops->gram(h->stream, dm.nb, n, h->fP, h->fQ, h->part, dm.pstride, h->st);
   enqueue_reduce(h, npack(kp), h->st);
   launch_small_xi(h->stream, kp, h->st, h->red, h->Sigma, h->Xi, h->T);
@@ -713,6 +731,7 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
     CUDA_TRY(cudaGetLastError());
   }
   int total = 0, restarts = 0, status = MBPCG_OK;
+  double best_relres = INFINITY;  // mixed precision: true relative residual of xbest
   // FP64 inner solves: at most 3 true-residual restarts. Mixed precision: the restarts are the FP64
   // refinement loop (correction solves in FP32), at most kMixedRestarts, and an inner solve is not
   // asked for more than kMixedInnerTol relative reduction, which FP32 blocks can deliver.
@@ -721,7 +740,8 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
   SolveState s;
   for (;;) {
     const int maxit_inner = no_test ? maxit : (maxit - total);
-    k_params<<<1, 1, 0, h->stream>>>(h->st, tol_rel, maxit_inner, no_test, restarts, h->s);
+    k_params<<<1, 1, 0, h->stream>>>(h->st, tol_rel, maxit_inner, no_test, restarts, h->s,
+                                     h->dm.mixed && !no_test ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
     if (h->launch_mode == MBPCG_LAUNCH_EAGER) {
       int rc = run_eager(h, maxit_inner);
@@ -739,6 +759,20 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
       break;
     }
     const double relres = (s.b_norm > 0.0) ? s.true_res / s.b_norm : 0.0;
+    if (h->dm.mixed) {
+      // The refinement loop keeps its best iterate: a correction from an FP32 inner solve that
+      // made the FP64 residual larger (possible when kappa(A) u_fp32 is not small) ends the loop
+      // with the best x found.
+      if (relres < best_relres) {
+        best_relres = relres;
+        CUDA_TRY(cudaMemcpyAsync(h->xbest, h->x, nb, cudaMemcpyDeviceToDevice, h->stream));
+      } else {
+        CUDA_TRY(cudaMemcpyAsync(h->x, h->xbest, nb, cudaMemcpyDeviceToDevice, h->stream));
+        s.true_res = best_relres * s.b_norm;
+        status = best_relres <= tol ? MBPCG_OK : MBPCG_NOT_CONVERGED;
+        break;
+      }
+    }
     if (relres <= tol) {
       status = MBPCG_OK;
       break;
@@ -792,6 +826,7 @@ size_t mbpcg_workspace_size_dense(int32_t n, int32_t s, int32_t algo, int32_t pr
   if (n < 1) return 0;
   Dims dm = make_dims(n, (long long)n * n, s, algo, 1, num_sms());
   dm.tc = (precision == MBPCG_FP64_TC && algo == MBPCG_ALGO_MBPCG) ? 1 : 0;
+  if (precision == MBPCG_MIXED_FP32 && algo == MBPCG_ALGO_MBPCG) apply_mixed(dm);
   widen_for_handle(dm);
   return make_layout(dm).total;
 }
@@ -847,13 +882,12 @@ int mbpcg_create_dense(mbpcg_handle* out, int32_t n, const double* A_colmajor, i
   if (rc) return rc;
   if (!A_colmajor) return set_err(MBPCG_ERR_INVALID, "A must not be NULL");
   if ((long long)n * n >= (1LL << 40)) return set_err(MBPCG_ERR_INVALID, "n too large for a dense matrix");
-  if (precision == MBPCG_MIXED_FP32)
-    return set_err(MBPCG_ERR_INVALID, "the mixed-precision inner solve is implemented for CSR A");
   const int sms = num_sms();
   if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
   mbpcg_ctx* h = nullptr;
   Dims dm = make_dims(n, (long long)n * n, s, algo, 1, sms);
   dm.tc = (precision == MBPCG_FP64_TC && algo == MBPCG_ALGO_MBPCG) ? 1 : 0;
+  if (precision == MBPCG_MIXED_FP32) apply_mixed(dm);
   widen_for_handle(dm);
   rc = alloc_handle(&h, dm, s, precond, algo, precision, seed, workspace, workspace_bytes, stream);
   if (rc) {
@@ -916,7 +950,8 @@ int mbpcg_set_launch_mode(mbpcg_handle h, int32_t mode) {
 
 int mbpcg_get_spmm_tuning(mbpcg_handle h, int32_t* unroll, int32_t* ctas_per_sm, float* times_us) {
   if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
-  if (!h->dm.mixed) return set_err(MBPCG_ERR_INVALID, "the FP32 product is tuned for MBPCG_MIXED_FP32 handles");
+  if (!h->dm.mixed || h->dm.dense)
+    return set_err(MBPCG_ERR_INVALID, "the FP32 sparse product is tuned for MBPCG_MIXED_FP32 CSR handles");
   if (unroll) *unroll = h->spmm_unroll;
   if (ctas_per_sm) *ctas_per_sm = h->spmm_ctas_per_sm;
   if (times_us)
@@ -926,7 +961,8 @@ int mbpcg_get_spmm_tuning(mbpcg_handle h, int32_t* unroll, int32_t* ctas_per_sm,
 
 int mbpcg_set_spmm_shape(mbpcg_handle h, int32_t unroll, int32_t ctas_per_sm) {
   if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
-  if (!h->dm.mixed) return set_err(MBPCG_ERR_INVALID, "the FP32 product is tuned for MBPCG_MIXED_FP32 handles");
+  if (!h->dm.mixed || h->dm.dense)
+    return set_err(MBPCG_ERR_INVALID, "the FP32 sparse product is tuned for MBPCG_MIXED_FP32 CSR handles");
   if ((unroll != 4 && unroll != 8) || (ctas_per_sm != 4 && ctas_per_sm != 8 && ctas_per_sm != 16))
     return set_err(MBPCG_ERR_INVALID, "unroll must be 4 or 8 and ctas_per_sm 4, 8 or 16");
   if (h->graph_ready) {  // the captured launches change
@@ -1036,6 +1072,28 @@ int mbpcg_k_spmm_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, 
   Dims dm = make_dims(n, 0, s, MBPCG_ALGO_MBPCG, 0, num_sms());
   apply_mixed(dm);
   row_ops_f(dm.kp)->spmm((cudaStream_t)stream, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0, 8);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+size_t mbpcg_k_dense_f32_bytes(int32_t n) { return n < 1 ? 0 : dense_f32_tiles_bytes(n); }
+
+int mbpcg_k_dense_f32_prepare(int32_t n, const double* A, void* tiles, size_t tiles_bytes, void* stream) {
+  if (n < 1 || !A || !tiles) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if (tiles_bytes < dense_f32_tiles_bytes(n)) return set_err(MBPCG_ERR_INVALID, "tiles buffer too small");
+  if (reinterpret_cast<uintptr_t>(tiles) % 16 != 0) return set_err(MBPCG_ERR_INVALID, "tiles must be 16-byte aligned");
+  k_dense_to_f32_tiles<<<4 * 152, 256, 0, (cudaStream_t)stream>>>(n, A, static_cast<float*>(tiles));
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+int mbpcg_k_dense_f32(int32_t n, const void* tiles, int32_t s, const float* P, float* AP, void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !tiles || !P || !AP) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if ((reinterpret_cast<uintptr_t>(tiles) | reinterpret_cast<uintptr_t>(P)) % 16 != 0)
+    return set_err(MBPCG_ERR_INVALID, "tiles and P must be 16-byte aligned");
+  const int sms = num_sms();
+  if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
+  dense_f32_product((cudaStream_t)stream, padded_width(s), n, sms, static_cast<const float*>(tiles), P, AP, nullptr);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

@@ -110,7 +110,7 @@ __global__ void k_to_f32(long long n, const double* __restrict__ src, float* __r
 __global__ void k_small_nu(SolveState* st, double* __restrict__ red, const double* __restrict__ Sigma, int kp,
                            int goff);
 __global__ void k_reduce(const double* part, int nparts, int pstride, double* out, const SolveState* st);
-__global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s);
+__global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s, int stag);
 __global__ void k_small_setup(SolveState* st, const double* red);
 __global__ void k_small_ls(SolveState* st, const double* Mg, int kp, double* c_out);
 __global__ void k_small_true(SolveState* st, const double* rr);
@@ -133,6 +133,14 @@ __global__ void k_cg_dots(int n, const double* r, const double* w, const double*
 __global__ void k_cg_update(int n, double* r, const double* w, double* x, double* p, double* sv,
                             const SolveState* st);
 __global__ void k_cg_finish(int n, const double* xbar, const double* d, double* x);
+
+// FP32 dense product of the mixed-precision inner solve (dense_f32.cu): Q = A P with A in the FP32
+// tiles k_dense_to_f32_tiles writes (dense_f32_tiles_bytes(n) bytes), P and Q row-major n x kp;
+// st may be NULL.
+size_t dense_f32_tiles_bytes(int n);
+__global__ void k_dense_to_f32_tiles(int n, const double* A, float* At);
+void dense_f32_product(cudaStream_t s, int kp, int n, int sms, const float* At, const float* P, float* Q,
+                       const SolveState* st);
 
 // FP64-accurate dense product on the BF16 tensor cores (ozaki_tc.cu)
 size_t oz_a_tiles_bytes(int n);

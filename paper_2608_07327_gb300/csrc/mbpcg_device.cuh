@@ -48,6 +48,13 @@ struct SolveState {
   double true_res;     // ||b - A x||
   // Chronopoulos-Gear CG scalars
   double cg_gamma_old, cg_alpha_old, cg_alpha, cg_beta;
+  // stagnation exit of the mixed-precision inner solves (stag_check = 1): the inner solve ends when
+  // nu_h has not fallen below 0.9 nu_ref for more than max(256, 2 it_ref) iterations
+  double nu_ref;       // last nu_h that was 10 % below the one before
+  int32_t it_ref;      // iteration of nu_ref
+  int32_t stag_check;  // 1: the rule is on (mixed precision, not in diagnostic mode)
+  int32_t stagnated;   // 1: the current inner solve ended by the rule
+  int32_t pad_;
 };
 
 // Per-KP launch shape of the row kernels: a thread owns CPT consecutive columns of one row

@@ -17,13 +17,14 @@ __global__ void k_reduce(const double* __restrict__ part, int nparts, int pstrid
   if (threadIdx.x == 0) out[e] = buf[0];
 }
 
-__global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s) {
+__global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s, int stag) {
   st->tol_rel = tol_rel;
   st->maxit = maxit;
   st->no_test = no_test;
   st->restart = restart;
   st->s = s;
   st->kerr = 0;
+  st->stag_check = stag;
 }
 
 // Set-up scalars: ||rhs||, X0 = (||B||_F / ||A U||_F) U with ||B||_F = sqrt(s) ||D^{-1} rhs||.
@@ -36,6 +37,9 @@ __global__ void k_small_setup(SolveState* st, const double* __restrict__ red) {
   st->it = 0;
   st->done = 0;
   st->r_from_v = 0;
+  st->nu_ref = INFINITY;
+  st->it_ref = 0;
+  st->stagnated = 0;
   st->pw_skip = 0;
   st->status = 0;
   st->converged = 0;

@@ -665,6 +665,21 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
       st->done = 1;
       st->pw_skip = 0;  // the last iteration still completes its W, P update
       st->status = st->no_test ? 0 : 5;
+    } else if (st->stag_check) {
+      // A mixed-precision inner solve whose residual estimate has stopped falling has delivered
+      // what FP32 can: end it (the exit combination and the FP64 true residual follow) so that the
+      // refinement loop restarts from the FP64 residual instead of iterating on.
+      if (nh < 0.9 * st->nu_ref) {
+        st->nu_ref = nh;
+        st->it_ref = st->it;
+      } else if (st->it - st->it_ref > max(256, 2 * st->it_ref)) {
+        done = 1;
+        st->done = 1;
+        st->pw_skip = 0;
+        st->status = 0;
+        st->stagnated = 1;  // not converged: the exit takes column h (the least-squares combination
+                            // of drifted FP32 residuals is not to be trusted)
+      }
     }
     if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
   }

@@ -1,4 +1,4 @@
-"""The mixed-precision inner solve (MBPCG_MIXED_FP32) against the FP64 oracle.
+"""The mixed-precision inner solve (MBPCG_MIXED_FP32), CSR and dense, against the FP64 oracle.
 
 Kernel level: the FP32 product A P is within FP32 rounding of the oracle's product of the same
 FP32 data, |AP - AP_o| <= 1e-6 |A||P| (nnz_row <= 8 terms, unit roundoff 2^-24); the Gram P^T (A P)
@@ -70,6 +70,52 @@ def test_spmm_gram_f32_matches_oracle(mb, orc, n, s):
     assert np.all(np.abs(Gh - Gu) <= 1e-12 * (np.triu(bound) + np.triu(bound, 1).T) + 1e-300)
 
 
+@pytest.mark.parametrize("s", [1, 2, 3, 8, 13, 16, 32])
+@pytest.mark.parametrize("n", [1, 33, 300, 1031, 4099])
+def test_dense_f32_matches_oracle(mb, orc, n, s):
+    """The FP32 dense product of the mixed inner solve on a dense A against the oracle's product of
+    the same FP32 values: FP32 accumulation of n terms is within n 2^-24 |A||P| of the exact sum
+    (any order). The tiles hold A rounded to FP32 and zeros past n (n = 4099: a ragged row tile
+    and a ragged last chunk). The K split of a row tile over a cluster is summed in rank order:
+    two calls give identical bits."""
+    D = wl.dense_spd(n, 11, 0.0, 4.0)
+    kp = int(mb.mbpcg_k_padded_width(s))
+    P = np.zeros((n, kp), np.float32)
+    P[:, :s] = wl.initial_block(n, s, 4).astype(np.float32)
+    dev = torch.device("cuda")
+    Ad = torch.as_tensor(np.asfortranarray(D.a).ravel(order="F"), device=dev)
+    nb = mb.mbpcg_k_dense_f32_bytes(n)
+    tiles = torch.full((nb // 4,), float("nan"), dtype=torch.float32, device=dev)
+    assert mb.mbpcg_k_dense_f32_prepare(n, Ad, tiles, nb, None) == 0, mb.last_error()
+    Pd = torch.as_tensor(P, device=dev)
+    AP = torch.full_like(Pd, float("nan"))
+    AP2 = torch.full_like(Pd, float("nan"))
+    assert mb.mbpcg_k_dense_f32(n, tiles, s, Pd, AP, None) == 0, mb.last_error()
+    assert mb.mbpcg_k_dense_f32(n, tiles, s, Pd, AP2, None) == 0, mb.last_error()
+    torch.cuda.synchronize()
+    got = AP.cpu().numpy()
+    A32 = np.asarray(D.a, dtype=np.float64).astype(np.float32).astype(np.float64)  # the FP32 values, exactly
+    ref = orc.matmat(wl.Dense(n, np.asfortranarray(A32)), P.astype(np.float64))
+    scale = np.abs(A32) @ np.abs(P.astype(np.float64))
+    assert np.all(np.abs(got - ref) <= (n + 2) * 2.0 ** -24 * scale + 1e-30)
+    assert np.all(got[:, s:] == 0.0)
+    assert np.array_equal(got, AP2.cpu().numpy())
+
+
+def test_dense_f32_rejects_bad_arguments(mb):
+    dev = torch.device("cuda")
+    A = torch.zeros(64, dtype=torch.float64, device=dev)
+    nb = mb.mbpcg_k_dense_f32_bytes(8)
+    assert nb == 256 * 32 * 4 and mb.mbpcg_k_dense_f32_bytes(0) == 0
+    tiles = torch.zeros(nb // 4, dtype=torch.float32, device=dev)
+    P = torch.zeros((8, 4), dtype=torch.float32, device=dev)
+    Q = torch.zeros_like(P)
+    assert mb.mbpcg_k_dense_f32_prepare(8, A, tiles, nb - 4, None) == mb._native.MBPCG_ERR_INVALID  # too small
+    assert mb.mbpcg_k_dense_f32_prepare(0, A, tiles, nb, None) == mb._native.MBPCG_ERR_INVALID
+    assert mb.mbpcg_k_dense_f32(8, tiles, 33, P, Q, None) == mb._native.MBPCG_ERR_INVALID  # s > 32
+    assert mb.mbpcg_k_dense_f32(8, None, 4, P, Q, None) == mb._native.MBPCG_ERR_INVALID
+
+
 MIXED_CASES = [
     # (name, matrix factory, s, precond) -- shapes of the mixed-precision configuration (27-point
     # stencil, s = 16) and of the other sparse families, at sizes the oracle finishes quickly
@@ -79,11 +125,16 @@ MIXED_CASES = [
     ("diffusion16_s4_jacobi", lambda: wl.diffusion3d(16, 2), 4, 1),
     ("poisson3d_20_s1", lambda: wl.poisson3d(20), 1, 0),
     ("diffusion12_s32_jacobi", lambda: wl.diffusion3d(12, 3), 32, 1),
+    # dense SPD A = Q diag(10^U[0,hi]) Q^T (the dense configuration's family), FP32 copy of A
+    ("dense300_k1e6_s8", lambda: wl.dense_spd(300, 0, 0.0, 6.0), 8, 0),
+    ("dense257_k1e4_s32_jacobi", lambda: wl.dense_spd(257, 1, 0.0, 4.0), 32, 1),
+    ("dense1031_k1e4_s16", lambda: wl.dense_spd(1031, 2, 0.0, 4.0), 16, 0),
+    ("dense64_k1e3_s1", lambda: wl.dense_spd(64, 3, 0.0, 3.0), 1, 0),
 ]
 
 
 def kappa(A, precond):
-    M = A.to_scipy().toarray()
+    M = np.asarray(A.a, dtype=np.float64) if not hasattr(A, "row_ptr") else A.to_scipy().toarray()
     if precond:
         d = 1.0 / np.sqrt(np.diag(M))
         M = d[:, None] * M * d[None, :]
@@ -105,7 +156,7 @@ def test_mixed_solve_against_fp64_oracle(mb, orc, name, factory, s, precond):
     finally:
         sv.close()
     assert info["status"] == 0, info
-    r = b - A.to_scipy() @ x
+    r = b - (np.asarray(A.a) @ x if not hasattr(A, "row_ptr") else A.to_scipy() @ x)
     relres = np.linalg.norm(r) / np.linalg.norm(b)
     assert relres <= tol and info["relres_true"] <= tol
     assert info["restarts"] >= 1  # FP32 inner solves need the FP64 refinement for 1e-10
@@ -117,8 +168,6 @@ def test_mixed_solve_against_fp64_oracle(mb, orc, name, factory, s, precond):
 
 
 def test_mixed_precision_is_refused_where_it_does_not_apply(mb):
-    with pytest.raises(mb.MBPCGError):
-        mb.Solver(wl.dense_spd(64, 0), s=4, precision=mb.MBPCG_MIXED_FP32)
     with pytest.raises(mb.MBPCGError):
         mb.Solver(wl.poisson2d(8), s=4, algo=mb.MBPCG_ALGO_CG, precision=mb.MBPCG_MIXED_FP32)
     sv = mb.Solver(wl.poisson2d(8), s=4, precision=mb.MBPCG_MIXED_FP32)
@@ -149,9 +198,9 @@ def test_spmm_autotuner_picks_the_fastest_shape_and_never_changes_results(mb):
             sv.set_spmm_shape(3, 8)
     finally:
         sv.close()
-    fp = mb.Solver(A, s=s)
-    try:
-        with pytest.raises(mb.MBPCGError):
-            fp.spmm_tuning()
-    finally:
-        fp.close()
+    for other in (mb.Solver(A, s=s), mb.Solver(wl.dense_spd(64, 0), s=4, precision=mb.MBPCG_MIXED_FP32)):
+        try:
+            with pytest.raises(mb.MBPCGError):  # FP64 handles and the dense FP32 product have no shapes
+                other.spmm_tuning()
+        finally:
+            other.close()
