@@ -105,6 +105,13 @@ int mbpcg_k_dense_tc_prepare(int32_t n, const double* A, int32_t s, void* scratc
                              size_t scratch_bytes, void* stream);
 int mbpcg_k_dense_tc_product(int32_t n, int32_t s, const double* P, double* AP, void* scratch,
                              size_t scratch_bytes, void* stream);
+/* The MMA kernel of the tensor-core product alone (k_dense_tc: the digit stream of A and the
+ * tcgen05 MMAs; no splitting of P, no split sum), in the launch configuration of the product, on
+ * the digits of P that the last mbpcg_k_dense_tc_product call left in `scratch`. It writes only
+ * partial sums inside scratch -- never AP -- and they are not a product (that call's split sum
+ * has already cleared the column exponents of P): it exists to time the dominant kernel of an
+ * iteration in isolation. Arguments and errors as mbpcg_k_dense_tc_product. */
+int mbpcg_k_dense_tc_mma(int32_t n, int32_t s, void* scratch, size_t scratch_bytes, void* stream);
 
 /* Z = upper Cholesky factor of the SPD s x s matrix G (G = Z^T Z, positive diagonal), the k x k
  * factorisation used for Xi (Section 3) and for the Cholesky QR. *status_dev (device int) is set

@@ -104,6 +104,7 @@ _SIGS = {
     "mbpcg_k_dense_tc_scratch_bytes": (_SZ, [_I32, _I32]),
     "mbpcg_k_dense_tc_prepare": (ctypes.c_int, [_I32, _P, _I32, _P, _SZ, _P]),
     "mbpcg_k_dense_tc_product": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _SZ, _P]),
+    "mbpcg_k_dense_tc_mma": (ctypes.c_int, [_I32, _I32, _P, _SZ, _P]),
     "mbpcg_k_spmm_gram_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "mbpcg_k_spmm": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
     "mbpcg_k_spmm_gram_f32": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
@@ -275,6 +276,10 @@ def mbpcg_k_dense_tc_scratch_bytes(n, s) -> int:
 
 def mbpcg_k_dense_tc_prepare(n, A, s, scratch, scratch_bytes, stream=None):
     return lib().mbpcg_k_dense_tc_prepare(n, ptr(A), s, ptr(scratch), scratch_bytes, stream)
+
+
+def mbpcg_k_dense_tc_mma(n, s, scratch, scratch_bytes, stream=None):
+    return lib().mbpcg_k_dense_tc_mma(n, s, ptr(scratch), scratch_bytes, stream)
 
 
 def mbpcg_k_dense_tc_product(n, s, P, AP, scratch, scratch_bytes, stream=None):

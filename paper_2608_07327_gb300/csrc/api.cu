@@ -1169,6 +1169,16 @@ int mbpcg_k_dense_tc_prepare(int32_t n, const double* A, int32_t s, void* scratc
   return MBPCG_OK;
 }
 
+int mbpcg_k_dense_tc_mma(int32_t n, int32_t s, void* scratch, size_t scratch_bytes, void* stream) {
+  if (n < 1 || s < 1 || s > 32 || !scratch) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if (scratch_bytes < mbpcg_k_dense_tc_scratch_bytes(n, s)) return set_err(MBPCG_ERR_INVALID, "scratch too small");
+  const int kp = padded_width(s);
+  const TcScratch t = tc_scratch(scratch, n, kp);
+  oz_mma((cudaStream_t)stream, n, kp, num_sms(), t.at, t.ea, t.pc, t.ep, t.qp);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
 int mbpcg_k_dense_tc_product(int32_t n, int32_t s, const double* P, double* AP, void* scratch, size_t scratch_bytes,
                              void* stream) {
   if (n < 1 || s < 1 || s > 32 || !P || !AP || !scratch) return set_err(MBPCG_ERR_INVALID, "bad arguments");

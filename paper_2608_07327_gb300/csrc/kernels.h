@@ -149,6 +149,9 @@ int oz_ksplit(int n, int sms);  // partial slices of Q the product needs (Qpart 
 void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* Atiles);
 // part != NULL: also the CTA partials of P^T (A P) over nb balanced row ranges (stride pstride).
 // exp_ready: the column exponents of P are already in emaxP (written by the W/P update).
+// The MMA kernel alone (k_dense_tc) on P digits already in Pchunks: partial slices into Qpart.
+void oz_mma(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const uint8_t* Pchunks,
+            const int* emaxP, double* Qpart);
 void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
                 uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st, double* part,
                 int pstride, int nb, int exp_ready);

@@ -523,6 +523,26 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
   else k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, sp.nW, Qpart, Q, emaxP, st, sp.G);
 }
 
+template <int KPT>
+static void oz_mma_kp(cudaStream_t s, int n, int KP, int sms, const uint8_t* Atiles, const int* emaxA,
+                      const uint8_t* Pchunks, const int* emaxP, double* Qpart) {
+  using C = OzCfg<KPT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dense_tc<KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
+    attr = true;
+  }
+  const OzSplit sp(n, sms > 0 ? sms : 1);
+  k_dense_tc<KPT><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks, emaxP,
+                                                       Qpart, nullptr, nullptr, 0);
+}
+
+void oz_mma(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const uint8_t* Pchunks,
+            const int* emaxP, double* Qpart) {
+  if (kp >= 32) oz_mma_kp<32>(s, n, kp, sms, Atiles, emaxA, Pchunks, emaxP, Qpart);
+  else oz_mma_kp<16>(s, n, kp, sms, Atiles, emaxA, Pchunks, emaxP, Qpart);
+}
+
 void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
                 uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st, double* part,
                 int pstride, int nb, int exp_ready) {
