@@ -163,3 +163,24 @@ def test_dense_tc_product_matches_oracle(mb, orc, n, s):
     scale = np.abs(np.asarray(D.a)) @ np.abs(P)
     assert np.all(np.isfinite(got[:, :s]))
     assert np.all(np.abs(got[:, :s] - ref[:, :s]) <= 1e-14 * scale[:, :s] + 1e-300)
+
+
+def test_dense_tc_mma_alone_leaves_the_product_untouched(mb):
+    """The timing entry for the MMA kernel alone runs on the digits a product call left in scratch
+    and writes only inside scratch: AP from the product stays as it was."""
+    n, s = 300, 32
+    D = wl.dense_spd(n, 5, 0.0, 3.0)
+    P, kp = padded_block(n, s, 6)
+    dev = torch.device("cuda")
+    Ad = torch.as_tensor(np.asfortranarray(D.a).ravel(order="F"), device=dev)
+    Pd = torch.as_tensor(np.ascontiguousarray(P), device=dev)
+    AP = torch.full_like(Pd, float("nan"))
+    nbytes = mb.mbpcg_k_dense_tc_scratch_bytes(n, s)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    assert mb.mbpcg_k_dense_tc_mma(n, s, scratch, nbytes - 1, None) == mb._native.MBPCG_ERR_INVALID
+    assert mb.mbpcg_k_dense_tc_prepare(n, Ad, s, scratch, nbytes, None) == 0, mb.last_error()
+    assert mb.mbpcg_k_dense_tc_product(n, s, Pd, AP, scratch, nbytes, None) == 0, mb.last_error()
+    before = AP.clone()
+    assert mb.mbpcg_k_dense_tc_mma(n, s, scratch, nbytes, None) == 0, mb.last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(AP, before)
