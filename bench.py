@@ -384,7 +384,20 @@ def run_ours(args, world, rank, local):
     k_avg = sum(k_ms) / len(k_ms)
     achieved_tflops = flops / (k_avg * 1e-3) / 1e12
     seq_ms = None
+    single_ms = None
     if tc:
+        # k_dense_tc reads 268 MB of digits, more than L2 (129 MB): timed as back-to-back launches,
+        # no flush in between, so the launch latency of one launch hides behind the previous one
+        with torch.cuda.stream(stream):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(args.kernel_launches):
+                launch()
+            ev1.record(stream)
+            ev1.synchronize()
+        single_ms, k_avg = k_avg, ev0.elapsed_time(ev1) / args.kernel_launches
+        achieved_tflops = flops / (k_avg * 1e-3) / 1e12
         with torch.cuda.stream(stream):
             q_ms = []
             for _ in range(max(3, args.kernel_launches // 2)):
@@ -454,6 +467,8 @@ def run_ours(args, world, rank, local):
                     "frac": round(achieved_gbs / hbm_peak, 4), "traffic": recorded_traffic(kname, args.workload, s),
                     "kernel_ms": round(k_avg, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
                     "fp64_equiv_tflops": round(achieved_tflops, 3),
+                    "timing": f"{args.kernel_launches} back-to-back launches (input 268 MB > L2, no flush)",
+                    "kernel_ms_one_launch_l2_flushed": round(single_ms, 5),
                     "product_call_ms": round(seq_ms, 5),
                     "product_call_frac": round(nbytes / (seq_ms * 1e-3) / 1e9 / hbm_peak, 4),
                     "read_ceiling_gbs": round(read_gbs, 1), "frac_of_read_ceiling": round(achieved_gbs / read_gbs, 4),

@@ -471,7 +471,7 @@ void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y
 }
 
 void enqueue_reduce(mbpcg_ctx* h, int nent, const SolveState* st) {
-  k_reduce<<<nent, 128, 0, h->stream>>>(h->part, h->dm.nb, h->dm.pstride, h->red, st);
+  launch_reduce(h->stream, h->part, h->dm.nb, h->dm.pstride, h->red, nent, st);
 }
 
 void enqueue_true_residual(mbpcg_ctx* h) {
@@ -482,7 +482,7 @@ void enqueue_true_residual(mbpcg_ctx* h) {
     k_resid_csr<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->rp, h->ci, h->av, h->sqd, h->b, h->x, h->rhs, h->part,
                                                    dm.pstride);
   // the dense residual uses nb_dense partial slots
-  k_reduce<<<1, 128, 0, h->stream>>>(h->part, dm.dense ? dm.nb_dense : dm.nb, dm.pstride, h->red, nullptr);
+  launch_reduce(h->stream, h->part, dm.dense ? dm.nb_dense : dm.nb, dm.pstride, h->red, 1, nullptr);
   k_small_true<<<1, 1, 0, h->stream>>>(h->st, h->red);
 }
 
@@ -1041,7 +1041,7 @@ static int k_product_gram(int dense, int32_t n, const int32_t* rp, const int32_t
   } else {
     ops->spmm(st, dm.nb, n, rp, ci, av, P, AP, part, dm.pstride, nullptr, 1);
   }
-  k_reduce<<<npack(dm.kp), 128, 0, st>>>(part, dm.nb, dm.pstride, red, nullptr);
+  launch_reduce(st, part, dm.nb, dm.pstride, red, npack(dm.kp), nullptr);
   k_unpack_full<<<1, 256, 0, st>>>(red, dm.kp, s, G);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
@@ -1064,7 +1064,7 @@ int mbpcg_k_spmm_gram_f32(int32_t n, const int32_t* row_ptr, const int32_t* col_
   double* red = part + (size_t)dm.nbmax * dm.pstride;
   row_ops_f(dm.kp)->spmm(st, dm.nb, n, row_ptr, col_idx, vals, P, AP, nullptr, 0, nullptr, 0, 8);
   row_ops_f(dm.kp)->gram(st, dm.nb, n, P, AP, part, dm.pstride, nullptr);
-  k_reduce<<<npack(dm.kp), 128, 0, st>>>(part, dm.nb, dm.pstride, red, nullptr);
+  launch_reduce(st, part, dm.nb, dm.pstride, red, npack(dm.kp), nullptr);
   k_unpack_full<<<1, 256, 0, st>>>(red, dm.kp, s, G);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;

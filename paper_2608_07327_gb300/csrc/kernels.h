@@ -109,7 +109,9 @@ inline const RowOpsF* row_ops_f(int kp) {
 __global__ void k_to_f32(long long n, const double* __restrict__ src, float* __restrict__ dst);
 __global__ void k_small_nu(SolveState* st, double* __restrict__ red, const double* __restrict__ Sigma, int kp,
                            int goff);
-__global__ void k_reduce(const double* part, int nparts, int pstride, double* out, const SolveState* st);
+// out[e] = sum over p < nparts of part[p * pstride + e] for e < nent (fixed order; st may be NULL).
+void launch_reduce(cudaStream_t s, const double* part, int nparts, int pstride, double* out, int nent,
+                   const SolveState* st);
 __global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s, int stag);
 __global__ void k_small_setup(SolveState* st, const double* red);
 __global__ void k_small_ls(SolveState* st, const double* Mg, int kp, double* c_out);

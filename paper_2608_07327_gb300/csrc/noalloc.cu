@@ -78,7 +78,7 @@ extern "C" int mbpcg_k_spmm_gram_noalloc(int32_t n, const int32_t* row_ptr, cons
   double* red = scratch + (size_t)kMaxCtas * kSlot;
   cudaStream_t st = (cudaStream_t)stream;
   mbpcg::row_ops(kp)->spmm(st, nb, n, row_ptr, col_idx, vals, P, AP, scratch, kSlot, nullptr, 1);
-  mbpcg::k_reduce<<<mbpcg::npack(kp), 128, 0, st>>>(scratch, nb, kSlot, red, nullptr);
+  mbpcg::launch_reduce(st, scratch, nb, kSlot, red, mbpcg::npack(kp), nullptr);
   mbpcg::k_unpack_full<<<1, 256, 0, st>>>(red, kp, s, G);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)

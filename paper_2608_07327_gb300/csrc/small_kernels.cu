@@ -5,16 +5,31 @@
 
 namespace mbpcg {
 
-__global__ void k_reduce(const double* __restrict__ part, int nparts, int pstride, double* __restrict__ out,
-                         const SolveState* __restrict__ st) {
+// One CTA of kReduceThreads per entry: thread t sums the partials p = t, t + kReduceThreads, ...,
+// each warp combines its lanes by a butterfly, and thread 0 adds the warp sums in warp order
+// (a fixed order: the same bits on every run).
+__global__ void __launch_bounds__(kReduceThreads)
+k_reduce(const double* __restrict__ part, int nparts, int pstride, double* __restrict__ out, int nent,
+         const SolveState* __restrict__ st) {
   if (st != nullptr && st->done) return;
-  __shared__ double buf[128];
-  const int e = blockIdx.x;
+  __shared__ double ws[kReduceThreads / 32];
+  const int e = blockIdx.x, tid = threadIdx.x;
+  if (e >= nent) return;
   double a = 0.0;
-  for (int p = threadIdx.x; p < nparts; p += 128) a += part[(size_t)p * pstride + e];
-  buf[threadIdx.x] = a;
-  cta_tree_sum(buf, 128, 1);
-  if (threadIdx.x == 0) out[e] = buf[0];
+  for (int p = tid; p < nparts; p += kReduceThreads) a += part[(size_t)p * pstride + e];
+  for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+  if ((tid & 31) == 0) ws[tid >> 5] = a;
+  __syncthreads();
+  if (tid == 0) {
+    double v = ws[0];
+    for (int w = 1; w < kReduceThreads / 32; ++w) v += ws[w];
+    out[e] = v;
+  }
+}
+
+void launch_reduce(cudaStream_t s, const double* part, int nparts, int pstride, double* out, int nent,
+                   const SolveState* st) {
+  k_reduce<<<nent, kReduceThreads, 0, s>>>(part, nparts, pstride, out, nent, st);
 }
 
 __global__ void k_params(SolveState* st, double tol_rel, int maxit, int no_test, int restart, int s, int stag) {

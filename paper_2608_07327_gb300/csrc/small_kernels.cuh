@@ -10,8 +10,10 @@ namespace mbpcg {
 
 constexpr int kSmallThreads = 256;
 
-// out[e] = sum over p < nparts of part[p * pstride + e], for e = blockIdx.x, in a fixed order.
-__global__ void k_reduce(const double* __restrict__ part, int nparts, int pstride, double* __restrict__ out,
+constexpr int kReduceThreads = 128;  // threads per entry in k_reduce
+
+// out[e] = sum over p < nparts of part[p * pstride + e] for e < nent, in a fixed order.
+__global__ void k_reduce(const double* __restrict__ part, int nparts, int pstride, double* __restrict__ out, int nent,
                          const SolveState* __restrict__ st);
 
 // Right-looking Cholesky G = Z^T Z of the leading s x s block of A (shared memory, column-major,
