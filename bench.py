@@ -160,7 +160,7 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "k_dense": ("row_kernels.cuh", "mbpcg_device.cuh"),
     "k_spmm": ("row_kernels.cuh", "mbpcg_device.cuh"),
-    "k_dense_tc": ("ozaki_tc.cu", "tcgen05.cuh", "tma.cuh", "mbpcg_device.cuh"),
+    "k_dense_tc": ("ozaki_tc.cu", "ozaki_digits.cuh", "tcgen05.cuh", "tma.cuh", "mbpcg_device.cuh"),
 }
 
 

@@ -106,8 +106,12 @@ struct Layout {
   size_t av32, wd32;                     // mixed precision: FP32 copies of the scaled values and of diag A
   size_t A32;                            // mixed precision, dense A: FP32 tiles (dense_f32_tiles_bytes)
   size_t xbest;                          // mixed precision: best iterate of the refinement loop
+  size_t rp3;                            // tensor-core k x k-row products: 3 blocks n x KP (KP = 32)
   size_t total;
 };
+
+// Tensor-core handles with KP = 32 run the k x k-row products of the loop on the tensor cores.
+bool dm_uses_rowprod(const Dims& dm) { return dm.tc && dm.kp == 32 && dm.algo == MBPCG_ALGO_MBPCG; }
 
 Layout make_layout(const Dims& dm) {
   Layout L;
@@ -166,6 +170,7 @@ Layout make_layout(const Dims& dm) {
     L.oz_p = take(oz_p_chunks_bytes(dm.n, dm.kp));
     L.oz_ep = take(kMaxKP * sizeof(int));
     L.oz_q = take((size_t)oz_ksplit(dm.n, dm.sms) * n * dm.kp * sizeof(double));
+    if (dm_uses_rowprod(dm)) L.rp3 = take(3 * n * dm.kp * sizeof(double));
   }
   L.part = take((size_t)dm.nbmax * dm.pstride * sizeof(double));
   L.red = take((size_t)dm.pstride * sizeof(double));
@@ -199,6 +204,7 @@ struct mbpcg_ctx {
   uint8_t *oz_a, *oz_p;
   int *oz_ea, *oz_ep;
   double* oz_q;
+  double* rp3;  // tensor-core k x k-row products (3 blocks), or NULL
   // mixed precision (FP32 views of the block buffers)
   float *fU, *fX0, *fXt, *fR, *fW, *fP, *fQ, *fV;
   float *av32, *wd32;
@@ -292,6 +298,7 @@ void bind(mbpcg_ctx* h) {
     h->oz_p = at<uint8_t>(h, L.oz_p);
     h->oz_ep = at<int>(h, L.oz_ep);
     h->oz_q = at<double>(h, L.oz_q);
+    h->rp3 = (dm_uses_rowprod(h->dm)) ? at<double>(h, L.rp3) : nullptr;
   }
 }
 
@@ -504,11 +511,20 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   const RowOps* ops = row_ops(dm.kp);
   const int kp = dm.kp, n = dm.n;
+  // tensor-core handles at KP = 32: the k x k-row products of the two row passes on the tensor cores
+  const bool tcrows = h->rp3 != nullptr && !h->rfree;
+  double *Y0 = h->rp3, *Y1 = Y0 + (size_t)n * kp, *Y2 = Y1 + (size_t)n * kp;
   enqueue_product(h, ops, h->P, h->Q, 1, h->st);
   enqueue_reduce(h, npack(kp), h->st);
   launch_small_xi(h->stream, kp, h->st, h->red, h->Sigma, h->Xi, h->T);
-  ops->axpy(h->stream, dm.nb, n, h->P, h->Q, h->W, h->R, h->Xt, h->V, h->T, h->Xi, h->wdiag, h->part, dm.pstride,
-            h->st, h->rfree);
+  if (tcrows) {
+    const RowProdJobs jb = {{{h->P, h->T, 0, Y0}, {h->Q, h->T, 0, Y1}, {h->Q, h->Xi, 0, Y2}}};
+    rowprod_tc(h->stream, n, jb, 3, h->st, 0, &h->st->kerr);
+    ops->axpy_pre(h->stream, dm.nb, n, Y0, Y1, Y2, h->W, h->R, h->Xt, h->V, h->wdiag, h->part, dm.pstride, h->st);
+  } else {
+    ops->axpy(h->stream, dm.nb, n, h->P, h->Q, h->W, h->R, h->Xt, h->V, h->T, h->Xi, h->wdiag, h->part, dm.pstride,
+              h->st, h->rfree);
+  }
   if (h->rfree) {  // nu_j from the Gram of V (weighted with scaling) and Sigma
     const bool w = h->wdiag != nullptr;
     enqueue_reduce(h, w ? 2 * npack(kp) + kp : npack(kp), h->st);
@@ -517,7 +533,13 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
     enqueue_reduce(h, npack(kp) + kp, h->st);
   }
   launch_small_zeta(h->stream, kp, h->st, h->red, h->Sigma, h->Zeta, h->ZetaInv, h->cond, h->use_cond);
-  ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0, dm.tc ? h->oz_ep : nullptr);
+  if (tcrows) {
+    const RowProdJobs jb = {{{h->V, h->ZetaInv, 0, Y0}, {h->P, h->Zeta, 1, Y1}, {nullptr, nullptr, 0, nullptr}}};
+    rowprod_tc(h->stream, n, jb, 2, h->st, 1, &h->st->kerr);
+    ops->pw_pre(h->stream, n, Y0, Y1, h->W, h->P, h->st, h->oz_ep);
+  } else {
+    ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0, dm.tc ? h->oz_ep : nullptr);
+  }
 }
 
 void enqueue_mbpcg_exit(mbpcg_ctx* h) {
@@ -1165,6 +1187,16 @@ int mbpcg_k_dense_tc_prepare(int32_t n, const double* A, int32_t s, void* scratc
   const TcScratch t = tc_scratch(scratch, n, kp);
   oz_prepare_a(st, n, A, t.ea, t.at);
   CUDA_TRY(cudaMemsetAsync(t.pc, 0, oz_p_chunks_bytes(n, kp), st));
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+int mbpcg_k_rowprod_tc(int32_t n, const double* X, const double* M, int32_t transM, double* Y, void* stream) {
+  if (n < 1 || !X || !M || !Y || (transM != 0 && transM != 1)) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) % 16 != 0)
+    return set_err(MBPCG_ERR_INVALID, "X and Y must be 16-byte aligned");
+  const RowProdJobs jb = {{{X, M, transM, Y}, {nullptr, nullptr, 0, nullptr}, {nullptr, nullptr, 0, nullptr}}};
+  rowprod_tc((cudaStream_t)stream, n, jb, 1, nullptr, 0, nullptr);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

@@ -33,6 +33,13 @@ struct RowOps {
   void (*gen_u)(cudaStream_t, int n, int s, unsigned long long seed, double* U);
   void (*from_colmajor)(cudaStream_t, int n, int s, const double* src, double* dst);
   void (*to_colmajor)(cudaStream_t, int n, int s, const double* src, double* dst);
+  // the block update and the W/P update with their k x k-row products given (from rowprod_tc):
+  // PT = P T, QT = (AP) T, QXi = (AP) Xi; VZi = V zeta^{-1}, PZt = P zeta^T
+  void (*axpy_pre)(cudaStream_t, int nb, int n, const double* PT, const double* QT, const double* QXi,
+                   const double* W, double* R, double* Xt, double* V, const double* wdiag, double* part, int pstride,
+                   const SolveState* st);
+  void (*pw_pre)(cudaStream_t, int n, const double* VZi, const double* PZt, double* W, double* P, const SolveState* st,
+                 int* emax);
 };
 
 const RowOps* row_ops_kp1();
@@ -151,6 +158,21 @@ int oz_ksplit(int n, int sms);  // partial slices of Q the product needs (Qpart 
 void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* Atiles);
 // part != NULL: also the CTA partials of P^T (A P) over nb balanced row ranges (stride pstride).
 // exp_ready: the column exponents of P are already in emaxP (written by the W/P update).
+// k x k-row products on the tensor cores (rowprod_tc.cu): Y = X M for up to three (X, M) pairs, one
+// launch; X and Y row-major n x 32 FP64, M column-major 32 x 32 (M^T with transM). Skipped when
+// the solve is done (or, with skip_on_pw, when the W/P update is skipped).
+struct RowProdJob {
+  const double* X;
+  const double* M;
+  int transM;
+  double* Y;
+};
+struct RowProdJobs {
+  RowProdJob j[3];
+};
+void rowprod_tc(cudaStream_t s, int n, const RowProdJobs& jobs, int njobs, const SolveState* st, int skip_on_pw,
+                int* err);
+
 // The MMA kernel alone (k_dense_tc) on P digits already in Pchunks: partial slices into Qpart.
 void oz_mma(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const uint8_t* Pchunks,
             const int* emaxP, double* Qpart);

@@ -1,0 +1,37 @@
+// Exact splitting of FP64 values into signed base-128 digits for the tensor-core products (Ozaki et
+// al., "Error-free transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 2012). A value x of a group (a row or a
+// column) whose largest biased exponent is emax is written as
+//     x = 2^(emax - 1022) * sum_{t=0..7} d_t 2^(-7 - 7t)   (+ truncation below 2^-56 of the scale),
+// d_t an integer in [-127, 127] taken straight from the 53-bit significand (integer shifts): exact
+// in BF16. A product of two such digits is below 2^14.
+#pragma once
+#include <stdint.h>
+
+namespace mbpcg {
+
+constexpr int kOzDigits = 8;
+
+__device__ __forceinline__ int biased_exponent(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// The 8 signed base-128 digits of x relative to the scale 2^(emax - 1022).
+__device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDigits]) {
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  unsigned long long X = 0;
+  if (e != 0 && e != 0x7FF && emax != 0) {
+    const unsigned long long mant = ((unsigned long long)bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int shift = e - emax + 3;  // X = |x| 2^(1022 - emax) 2^56 < 2^56
+    X = shift >= 0 ? (mant << shift) : (shift > -60 ? (mant >> (-shift)) : 0ull);
+  }
+  const int sgn = bits < 0 ? -1 : 1;
+#pragma unroll
+  for (int t = 0; t < kOzDigits; ++t) d[t] = sgn * (int)((X >> (49 - 7 * t)) & 127ull);
+}
+
+// BF16 bit pattern of a small integer (exact: |v| <= 127 needs 7 significand bits).
+__device__ __forceinline__ uint16_t bf16_of_int(int v) { return (uint16_t)(__float_as_uint((float)v) >> 16); }
+
+}  // namespace mbpcg

@@ -25,13 +25,13 @@
 // uses all needed digits of P at once (N = KPT * (9 - t)), writing levels t+1..9 of the
 // accumulator. Producer, MMA issuer and drain run in separate warps; every wait is bounded.
 #include "kernels.h"
+#include "ozaki_digits.cuh"
 #include "tcgen05.cuh"
 
 namespace mbpcg {
 
 namespace {
 
-constexpr int kOzDigits = 8;
 constexpr int kOzMT = 128;                             // rows per M tile (= TMEM lanes)
 constexpr int kOzKC = 64;                              // reduction index per chunk
 constexpr int kOzWin = 2;                              // chunks per exact window (128 values of l)
@@ -42,28 +42,6 @@ constexpr int kOzPBufs = 2;
 constexpr uint32_t kAStageBytes = kOzDPS * kATileBytes;
 constexpr int kOzStagesPerChunk = kOzDigits / kOzDPS;
 static_assert(kOzDigits % kOzDPS == 0, "a stage holds whole digits of one chunk");
-
-__device__ __forceinline__ int biased_exponent(double x) {
-  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
-}
-
-// The 8 signed base-128 digits of x relative to the scale 2^(emax - 1022).
-__device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDigits]) {
-  const long long bits = __double_as_longlong(x);
-  const int e = (int)((bits >> 52) & 0x7FF);
-  unsigned long long X = 0;
-  if (e != 0 && e != 0x7FF && emax != 0) {
-    const unsigned long long mant = ((unsigned long long)bits & ((1ull << 52) - 1)) | (1ull << 52);
-    const int shift = e - emax + 3;  // X = |x| 2^(1022 - emax) 2^56 < 2^56
-    X = shift >= 0 ? (mant << shift) : (shift > -60 ? (mant >> (-shift)) : 0ull);
-  }
-  const int sgn = bits < 0 ? -1 : 1;
-#pragma unroll
-  for (int t = 0; t < kOzDigits; ++t) d[t] = sgn * (int)((X >> (49 - 7 * t)) & 127ull);
-}
-
-// BF16 bit pattern of a small integer (exact: |v| <= 127 needs 7 significand bits).
-__device__ __forceinline__ uint16_t bf16_of_int(int v) { return (uint16_t)(__float_as_uint((float)v) >> 16); }
 
 }  // namespace
 

@@ -256,6 +256,97 @@ k_gram(int n, const double* __restrict__ X, const double* __restrict__ Y, double
 }
 
 // ------------------------------------------------------------------------------------------------
+// Block update of Algorithm 1 with its three products given (computed on the tensor cores):
+//   X~ += PT,  R -= QT,  V = W - QXi,
+// with the same CTA partials as k_axpy (explicit residual): nu_j at part[NPACK + j] and the upper
+// triangle of V^T V at part[0..).
+template <int KP>
+__global__ void __launch_bounds__(kThreads)
+k_axpy_pre(int n, const double* __restrict__ PT, const double* __restrict__ QT, const double* __restrict__ QXi,
+           const double* __restrict__ W, double* __restrict__ R, double* __restrict__ Xt, double* __restrict__ V,
+           const double* __restrict__ wdiag, double* __restrict__ part, int pstride, const SolveState* __restrict__ st) {
+  using C = Cfg<KP>;
+  using G = GramTile<KP>;
+  constexpr int RED = (G::RED > C::ROWS * KP) ? G::RED : C::ROWS * KP;
+  if (st->done) return;
+  __shared__ __align__(16) double Vs[C::ROWS * KP];
+  __shared__ __align__(16) double red[RED];
+  const int tid = threadIdx.x, rl = tid / C::TPR, j0 = (tid % C::TPR) * C::CPT;
+  int r0, r1;
+  row_range(n, r0, r1);
+  G g;
+  g.init(tid);
+  double nu[C::CPT];
+#pragma unroll
+  for (int c = 0; c < C::CPT; ++c) nu[c] = 0.0;
+  for (int base = r0; base < r1; base += C::ROWS) {
+    const int i = base + rl;
+    double vv[C::CPT];
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) vv[c] = 0.0;
+    if (i < r1) {
+      const size_t o = (size_t)i * KP + j0;
+      double xv[C::CPT], pt[C::CPT], rv[C::CPT], qt[C::CPT], qx[C::CPT];
+      ldv_plain<C::CPT>(Xt + o, xv);
+      ldv<C::CPT>(PT + o, pt);
+      ldv_plain<C::CPT>(R + o, rv);
+      ldv<C::CPT>(QT + o, qt);
+      ldv<C::CPT>(W + o, vv);
+      ldv<C::CPT>(QXi + o, qx);
+#pragma unroll
+      for (int c = 0; c < C::CPT; ++c) {
+        xv[c] += pt[c];
+        rv[c] -= qt[c];
+        vv[c] -= qx[c];
+      }
+      stv<C::CPT>(Xt + o, xv);
+      stv<C::CPT>(R + o, rv);
+      stv<C::CPT>(V + o, vv);
+      const double w2 = wdiag != nullptr ? __ldg(wdiag + i) : 1.0;
+#pragma unroll
+      for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c] * w2, rv[c], nu[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) Vs[rl * KP + j0 + c] = vv[c];
+    __syncthreads();
+    g.accumulate(Vs, Vs, min(C::ROWS, r1 - base));
+    __syncthreads();
+  }
+  double* out = part + (size_t)blockIdx.x * pstride;
+  g.finish(red, out);
+#pragma unroll
+  for (int c = 0; c < C::CPT; ++c) red[rl * KP + j0 + c] = nu[c];
+  cta_tree_sum(red, C::ROWS, KP);
+  for (int jj = tid; jj < KP; jj += kThreads) out[C::NPACK + jj] = red[jj];
+}
+
+// W/P update of Algorithm 1 with its products given: W = VZi, P = W + PZt, and the column
+// exponents of the new P (atomicMax into emax, when given) for the tensor-core A P product.
+// Element-parallel: the thread stride is a multiple of KP, so each thread stays on one column.
+template <int KP>
+__global__ void k_pw_pre(int n, const double* __restrict__ VZi, const double* __restrict__ PZt, double* __restrict__ W,
+                         double* __restrict__ P, const SolveState* __restrict__ st, int* __restrict__ emax) {
+  if (st != nullptr && st->pw_skip) return;
+  __shared__ int em[KP];
+  if (threadIdx.x < KP) em[threadIdx.x] = 0;
+  __syncthreads();
+  const size_t total = (size_t)n * KP, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  int loc = 0;
+  for (size_t q = q0; q < total; q += stride) {
+    const double w = VZi[q], p = w + PZt[q];
+    W[q] = w;
+    P[q] = p;
+    loc = max(loc, (int)((__double_as_longlong(p) >> 52) & 0x7FF));
+  }
+  if (emax != nullptr) {
+    atomicMax(&em[q0 % KP], loc);
+    __syncthreads();
+    if (threadIdx.x < KP) atomicMax(&emax[threadIdx.x], em[threadIdx.x]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Block update of Algorithm 1, one pass over the rows:
 //   X~ += P T,  R -= (A P) T  with T = Xi Sigma;   V = W - (A P) Xi   (input of the Cholesky QR)
 // plus CTA partials of nu_j = ||(D R)_j||^2 (the original-system residual norms used for the
