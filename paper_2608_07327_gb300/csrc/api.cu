@@ -69,8 +69,7 @@ Dims make_dims(int n, long long nnz, int s, int algo, int dense, int sms) {
   const int sm = sms > 0 ? sms : 1;
   // row kernels: at most 2 CTAs per SM, and at least 8 rows per CTA at KP = 32 (the FP64 block
   // updates are bound by the FP64 pipe and gain from more CTAs: dense n = 4096, s = 32, 157 against
-  // 162 us per iteration) or 32 rows below (latency-bound: Poisson n = 4096, s = 4, 38 against 41;
-  // small systems served side by side leave the SMs to each other)
+  // 162 us per iteration) or 32 rows below (latency-bound: Poisson n = 4096, s = 4, 38 against 41)
   const int rows_per_cta = d.kp >= 32 ? 8 : 32;
   long long want = ((long long)n + rows_per_cta - 1) / rows_per_cta;
   d.nb = (int)(want < 2LL * sm ? (want > 0 ? want : 1) : 2LL * sm);
