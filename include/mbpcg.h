@@ -69,9 +69,9 @@ typedef enum { MBPCG_ALGO_MBPCG = 0, MBPCG_ALGO_CG = 1 } mbpcg_algo;
  * the FP64 path; the requested tol is still checked on the FP64 true residual.
  * FP64_TC (dense A, MBPCG only): the same FP64 solve, but the product A P runs on the BF16 tensor
  * cores by exact splitting of A and P into 8 base-128 digits (Ozaki scheme); its result has the
- * accuracy of an FP64 product. The digits of A take 16 bytes per entry of workspace. At s > 16
+ * accuracy of an FP64 product. The digits of A take 16 bytes per entry of workspace. At s > 8
  * the k x k-row products of the block update and of the W/P update (P T, (AP) T, (AP) Xi,
- * V zeta^-1, P zeta^T) run on the tensor cores the same way (3 more n x 32 blocks of workspace);
+ * V zeta^-1, P zeta^T) run on the tensor cores the same way (3 more n x KP blocks of workspace);
  * the Grams, the norms and the k x k steps stay FP64. */
 typedef enum { MBPCG_FP64 = 0, MBPCG_MIXED_FP32 = 1, MBPCG_FP64_TC = 2 } mbpcg_precision;
 

@@ -114,14 +114,16 @@ int mbpcg_k_dense_tc_product(int32_t n, int32_t s, const double* P, double* AP, 
 int mbpcg_k_dense_tc_mma(int32_t n, int32_t s, void* scratch, size_t scratch_bytes, void* stream);
 
 /* The k x k-row products of the block update and of the W/P update of Algorithm 1 (P T, (AP) T,
- * (AP) Xi, V zeta^{-1}, P zeta^T) as the solver runs them for tensor-core handles at s > 16:
+ * (AP) Xi, V zeta^{-1}, P zeta^T) as the solver runs them for tensor-core handles at s > 8:
  * Y = X M on the BF16 tensor cores by exact digit splitting (X row by row, M column by column;
  * 8 base-128 digits each), with the accuracy of an FP64 product: error about 2^-53 times
- * (max_l |X_il|) (sum_l |M_lj|) per entry, against an FP64 product's 32 u sum_l |X_il||M_lj|.
- * X, Y: device, row-major n x 32 FP64, 16-byte aligned; M: device, column-major 32 x 32 FP64,
- * used as M (transM = 0) or as its transpose (transM = 1). Y is written. No scratch.
- * MBPCG_ERR_INVALID for bad sizes, pointers or alignment. */
-int mbpcg_k_rowprod_tc(int32_t n, const double* X, const double* M, int32_t transM, double* Y, void* stream);
+ * (max_l |X_il|) (sum_l |M_lj|) per entry, against an FP64 product's w u sum_l |X_il||M_lj|.
+ * width = 32 or 16 (the padded width KP). X, Y: device, row-major n x width FP64, 16-byte
+ * aligned; M: device, column-major width x width FP64, used as M (transM = 0) or as its
+ * transpose (transM = 1). Y is written. No scratch.
+ * MBPCG_ERR_INVALID for bad sizes, width, pointers or alignment. */
+int mbpcg_k_rowprod_tc(int32_t n, int32_t width, const double* X, const double* M, int32_t transM, double* Y,
+                       void* stream);
 
 /* Z = upper Cholesky factor of the SPD s x s matrix G (G = Z^T Z, positive diagonal), the k x k
  * factorisation used for Xi (Section 3) and for the Cholesky QR. *status_dev (device int) is set

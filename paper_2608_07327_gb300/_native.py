@@ -105,7 +105,7 @@ _SIGS = {
     "mbpcg_k_dense_tc_prepare": (ctypes.c_int, [_I32, _P, _I32, _P, _SZ, _P]),
     "mbpcg_k_dense_tc_product": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_dense_tc_mma": (ctypes.c_int, [_I32, _I32, _P, _SZ, _P]),
-    "mbpcg_k_rowprod_tc": (ctypes.c_int, [_I32, _P, _P, _I32, _P, _P]),
+    "mbpcg_k_rowprod_tc": (ctypes.c_int, [_I32, _I32, _P, _P, _I32, _P, _P]),
     "mbpcg_k_spmm_gram_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "mbpcg_k_spmm": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P]),
     "mbpcg_k_spmm_gram_f32": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
@@ -279,8 +279,8 @@ def mbpcg_k_dense_tc_prepare(n, A, s, scratch, scratch_bytes, stream=None):
     return lib().mbpcg_k_dense_tc_prepare(n, ptr(A), s, ptr(scratch), scratch_bytes, stream)
 
 
-def mbpcg_k_rowprod_tc(n, X, M, transM, Y, stream=None):
-    return lib().mbpcg_k_rowprod_tc(n, ptr(X), ptr(M), transM, ptr(Y), stream)
+def mbpcg_k_rowprod_tc(n, width, X, M, transM, Y, stream=None):
+    return lib().mbpcg_k_rowprod_tc(n, width, ptr(X), ptr(M), transM, ptr(Y), stream)
 
 
 def mbpcg_k_dense_tc_mma(n, s, scratch, scratch_bytes, stream=None):

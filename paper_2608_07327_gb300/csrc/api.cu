@@ -106,12 +106,12 @@ struct Layout {
   size_t av32, wd32;                     // mixed precision: FP32 copies of the scaled values and of diag A
   size_t A32;                            // mixed precision, dense A: FP32 tiles (dense_f32_tiles_bytes)
   size_t xbest;                          // mixed precision: best iterate of the refinement loop
-  size_t rp3;                            // tensor-core k x k-row products: 3 blocks n x KP (KP = 32)
+  size_t rp3;                            // tensor-core k x k-row products: 3 blocks n x KP (KP >= 16)
   size_t total;
 };
 
-// Tensor-core handles with KP = 32 run the k x k-row products of the loop on the tensor cores.
-bool dm_uses_rowprod(const Dims& dm) { return dm.tc && dm.kp == 32 && dm.algo == MBPCG_ALGO_MBPCG; }
+// Tensor-core handles with KP = 16 or 32 run the k x k-row products of the loop on the tensor cores.
+bool dm_uses_rowprod(const Dims& dm) { return dm.tc && dm.kp >= 16 && dm.algo == MBPCG_ALGO_MBPCG; }
 
 Layout make_layout(const Dims& dm) {
   Layout L;
@@ -511,7 +511,7 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   const RowOps* ops = row_ops(dm.kp);
   const int kp = dm.kp, n = dm.n;
-  // tensor-core handles at KP = 32: the k x k-row products of the two row passes on the tensor cores
+  // tensor-core handles at KP >= 16: the k x k-row products of the two row passes on the tensor cores
   const bool tcrows = h->rp3 != nullptr && !h->rfree;
   double *Y0 = h->rp3, *Y1 = Y0 + (size_t)n * kp, *Y2 = Y1 + (size_t)n * kp;
   enqueue_product(h, ops, h->P, h->Q, 1, h->st);
@@ -519,7 +519,7 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
   launch_small_xi(h->stream, kp, h->st, h->red, h->Sigma, h->Xi, h->T);
   if (tcrows) {
     const RowProdJobs jb = {{{h->P, h->T, 0, Y0}, {h->Q, h->T, 0, Y1}, {h->Q, h->Xi, 0, Y2}}};
-    rowprod_tc(h->stream, n, jb, 3, h->st, 0, &h->st->kerr);
+    rowprod_tc(h->stream, n, kp, jb, 3, h->st, 0, &h->st->kerr);
     ops->axpy_pre(h->stream, dm.nb, n, Y0, Y1, Y2, h->W, h->R, h->Xt, h->V, h->wdiag, h->part, dm.pstride, h->st);
   } else {
     ops->axpy(h->stream, dm.nb, n, h->P, h->Q, h->W, h->R, h->Xt, h->V, h->T, h->Xi, h->wdiag, h->part, dm.pstride,
@@ -535,7 +535,7 @@ void enqueue_mbpcg_body(mbpcg_ctx* h) {
   launch_small_zeta(h->stream, kp, h->st, h->red, h->Sigma, h->Zeta, h->ZetaInv, h->cond, h->use_cond);
   if (tcrows) {
     const RowProdJobs jb = {{{h->V, h->ZetaInv, 0, Y0}, {h->P, h->Zeta, 1, Y1}, {nullptr, nullptr, 0, nullptr}}};
-    rowprod_tc(h->stream, n, jb, 2, h->st, 1, &h->st->kerr);
+    rowprod_tc(h->stream, n, kp, jb, 2, h->st, 1, &h->st->kerr);
     ops->pw_pre(h->stream, n, Y0, Y1, h->W, h->P, h->st, h->oz_ep);
   } else {
     ops->pw(h->stream, dm.nb, n, h->V, h->W, h->P, h->ZetaInv, h->Zeta, h->st, 0, dm.tc ? h->oz_ep : nullptr);
@@ -1191,12 +1191,14 @@ int mbpcg_k_dense_tc_prepare(int32_t n, const double* A, int32_t s, void* scratc
   return MBPCG_OK;
 }
 
-int mbpcg_k_rowprod_tc(int32_t n, const double* X, const double* M, int32_t transM, double* Y, void* stream) {
+int mbpcg_k_rowprod_tc(int32_t n, int32_t width, const double* X, const double* M, int32_t transM, double* Y,
+                       void* stream) {
   if (n < 1 || !X || !M || !Y || (transM != 0 && transM != 1)) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  if (width != 16 && width != 32) return set_err(MBPCG_ERR_INVALID, "width must be 16 or 32");
   if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) % 16 != 0)
     return set_err(MBPCG_ERR_INVALID, "X and Y must be 16-byte aligned");
   const RowProdJobs jb = {{{X, M, transM, Y}, {nullptr, nullptr, 0, nullptr}, {nullptr, nullptr, 0, nullptr}}};
-  rowprod_tc((cudaStream_t)stream, n, jb, 1, nullptr, 0, nullptr);
+  rowprod_tc((cudaStream_t)stream, n, width, jb, 1, nullptr, 0, nullptr);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

@@ -159,8 +159,8 @@ void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* A
 // part != NULL: also the CTA partials of P^T (A P) over nb balanced row ranges (stride pstride).
 // exp_ready: the column exponents of P are already in emaxP (written by the W/P update).
 // k x k-row products on the tensor cores (rowprod_tc.cu): Y = X M for up to three (X, M) pairs, one
-// launch; X and Y row-major n x 32 FP64, M column-major 32 x 32 (M^T with transM). Skipped when
-// the solve is done (or, with skip_on_pw, when the W/P update is skipped).
+// launch; X and Y row-major n x kp FP64, M column-major kp x kp (M^T with transM), kp = 16 or 32.
+// Skipped when the solve is done (or, with skip_on_pw, when the W/P update is skipped).
 struct RowProdJob {
   const double* X;
   const double* M;
@@ -170,8 +170,8 @@ struct RowProdJob {
 struct RowProdJobs {
   RowProdJob j[3];
 };
-void rowprod_tc(cudaStream_t s, int n, const RowProdJobs& jobs, int njobs, const SolveState* st, int skip_on_pw,
-                int* err);
+void rowprod_tc(cudaStream_t s, int n, int kp, const RowProdJobs& jobs, int njobs, const SolveState* st,
+                int skip_on_pw, int* err);
 
 // The MMA kernel alone (k_dense_tc) on P digits already in Pchunks: partial slices into Qpart.
 void oz_mma(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const uint8_t* Pchunks,

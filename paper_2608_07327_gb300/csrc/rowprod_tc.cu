@@ -1,25 +1,26 @@
-// FP64-accurate products Y = X M of an n x 32 block X by a 32 x 32 matrix M on the BF16 tensor
-// cores (tcgen05), by the exact digit splitting of ozaki_digits.cuh: X split row by row (scale of
-// the row), M column by column. These are the k x k-row products of the block update and of the W/P
+// FP64-accurate products Y = X M of an n x K block X by a K x K matrix M (K = 32 or 16, the padded
+// width) on the BF16 tensor cores (tcgen05), by the exact digit splitting of ozaki_digits.cuh: X
+// split row by row (scale of the row), M column by column. These are the k x k-row products of the block update and of the W/P
 // update of Algorithm 1 (P T, (AP) T, (AP) Xi; V zeta^{-1}, P zeta^T), which on the FP64 pipe of
 // this GPU (2 FMA per clock per SM) cost more than the A P product's digit stream.
 //
-// Exactness. The reduction index has 32 values, so a level sum S_L = sum_{t+u=L} sum_l x^t_il m^u_lj
+// Exactness. The reduction index has K <= 32 values, so a level sum S_L = sum_{t+u=L} sum_l x^t_il m^u_lj
 // is at most 8 * 32 * 127^2 < 2^22: every level of the FP32 accumulator is an exact integer. Levels
 // 0..4 are combined in int64 (exact), levels 5..7 in FP32 (rounding below 2^-56 of the scales),
 // levels above 7 are dropped (below 2^-56 of the scales), as in the dense A P product:
 //     Y_ij = 2^(e_i + f_j - 2044) * sum_{L=0..7} S_L 2^(-14 - 7L);
 // the two parts meet in one int64 below 2^62, converted to FP64 once (its only rounding).
 //
-// One CTA of 256 threads per (128-row tile, product, half of the 32 output columns): M is staged in
-// shared memory by one coalesced load; two threads per row write the 8 digits of their 16 values of
-// X into shared memory (K-major, no swizzle: 8 tiles of 128 x 32 bf16; 16-byte stores of 8
-// consecutive digits; the row scale is combined by one shuffle), 64 threads the 8 digits of the
-// CTA's 16 columns of M (128 x 32: row 16 u + j holds digit u of column j); one thread issues 16
-// MMAs (digit t of X against digits 0..7-t of M, N = 16 (8 - t), into TMEM columns 16 t .. 127),
+// One CTA of 256 threads per (128-row tile, product, 16 output columns: K / 16 CTAs): M is staged
+// in shared memory by one coalesced load; two threads per row write the 8 digits of their K / 2
+// values of X into shared memory (K-major, no swizzle: 8 tiles of 128 x K bf16; 16-byte stores of 8
+// consecutive digits; the row scale is combined by one shuffle), 4 K threads the 8 digits of the
+// CTA's 16 columns of M (128 x K: row 16 u + j holds digit u of column j); one thread issues
+// 8 K / 16 MMAs (digit t of X against digits 0..7-t of M, N = 16 (8 - t), into TMEM columns
+// 16 t .. 127),
 // and each warp drains 8 columns of its 32 rows (warps w and w + 4 share a TMEM lane quarter): 8
 // loads, the combination above, and one FP64 scaling per value. Two CTAs fit on an SM (81 KB of
-// shared memory, 128 TMEM columns each), so one phase of a CTA overlaps another's.
+// shared memory at K = 32, 128 TMEM columns each), so one phase of a CTA overlaps another's.
 #include "kernels.h"
 #include "ozaki_digits.cuh"
 #include "tcgen05.cuh"
@@ -28,15 +29,22 @@ namespace mbpcg {
 
 namespace {
 
-constexpr int kRpRows = 128;                                 // rows per CTA (= TMEM lanes)
-constexpr int kRpK = 32;                                     // columns of X, order of M
-constexpr int kRpN = 16;                                     // output columns per CTA
+constexpr int kRpRows = 128;                        // rows per CTA (= TMEM lanes)
+constexpr int kRpN = 16;                            // output columns per CTA
 constexpr int kRpThreads = 256;
-constexpr uint32_t kRpATile = kRpRows * kRpK * 2;            // one digit of the X tile: 8 KB
-constexpr uint32_t kRpBBytes = kOzDigits * kRpN * kRpK * 2;  // the digits of 16 columns of M: 8 KB
-constexpr uint32_t kRpTmemCols = kOzDigits * kRpN;           // 8 levels x 16 columns
-constexpr size_t kRpSmem = 1024 + (size_t)kOzDigits * kRpATile + kRpBBytes + kRpK * kRpK * sizeof(double);
-constexpr uint32_t kRpSbo = (kRpK / 8) * 128;                // 8-row groups of a K = 32 tile
+constexpr uint32_t kRpTmemCols = kOzDigits * kRpN;  // 8 levels x 16 columns
+
+// K = 32 or 16: columns of X, order of M (the padded width of the blocks)
+template <int K>
+struct RpCfg {
+  static constexpr uint32_t ATile = kRpRows * K * 2;            // one digit of the X tile: 8 / 4 KB
+  static constexpr uint32_t BBytes = kOzDigits * kRpN * K * 2;  // the digits of 16 columns of M
+  static constexpr size_t Smem = 1024 + (size_t)kOzDigits * ATile + BBytes + K * K * sizeof(double);
+  static constexpr uint32_t Sbo = (K / 8) * 128;                // 8-row groups of a K-wide tile
+  static constexpr int Xh = K / 2;                              // values of a row per thread
+  static constexpr int Halves = K / kRpN;                       // CTAs per (tile, product)
+  static_assert(K == 16 || K == 32, "width");
+};
 
 // v 2^k for an integer k: an integer add to the exponent field while the result stays a normal
 // number (no rounding: the FP64 pipe of this GPU is slow), else ldexp
@@ -67,8 +75,10 @@ __device__ __forceinline__ uint4 pack8(const int (&d)[8]) {
 
 }  // namespace
 
+template <int K>
 __global__ void __launch_bounds__(kRpThreads)
 k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int skip_on_pw, int* __restrict__ err) {
+  using C = RpCfg<K>;
   if (st != nullptr && (skip_on_pw ? st->pw_skip : st->done)) return;
   extern __shared__ __align__(1024) uint8_t rsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(rsm);
@@ -76,10 +86,10 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
   int* fexp = reinterpret_cast<int*>(rsm + 16);    // scales of this CTA's 16 columns of M
   int* erows = reinterpret_cast<int*>(rsm + 128);  // row scales of the X tile (128 ints)
   uint8_t* As = rsm + 1024;
-  uint8_t* Bs = As + (size_t)kOzDigits * kRpATile;
-  double* Ms = reinterpret_cast<double*>(Bs + kRpBBytes);  // M as stored (column-major 32 x 32)
-  const RowProdJob J = jobs.j[blockIdx.y >> 1];
-  const int jb = kRpN * (blockIdx.y & 1);  // first output column of this CTA
+  uint8_t* Bs = As + (size_t)kOzDigits * C::ATile;
+  double* Ms = reinterpret_cast<double*>(Bs + C::BBytes);  // M as stored (column-major K x K)
+  const RowProdJob J = jobs.j[blockIdx.y / C::Halves];
+  const int jb = kRpN * (blockIdx.y % C::Halves);  // first output column of this CTA
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = tid >> 1, hx = tid & 1;  // digit phase: row r of the tile, values 16 hx .. 16 hx + 15
   const int row = blockIdx.x * kRpRows + r;
@@ -90,12 +100,12 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
   }
   if (warp == 0) tmem_alloc(tmem_slot, kRpTmemCols);
 #pragma unroll
-  for (int i = 0; i < kRpK * kRpK / kRpThreads; ++i) Ms[tid + kRpThreads * i] = J.M[tid + kRpThreads * i];
-  // this thread's 16 values of its row of X (zeros past n)
-  constexpr int kXh = kRpK / 2;
+  for (int i = 0; i < K * K / kRpThreads; ++i) Ms[tid + kRpThreads * i] = J.M[tid + kRpThreads * i];
+  // this thread's K / 2 values of its row of X (zeros past n)
+  constexpr int kXh = C::Xh;
   double x[kXh];
   if (row < n) {
-    const double2* xr = reinterpret_cast<const double2*>(J.X + (size_t)row * kRpK + kXh * hx);
+    const double2* xr = reinterpret_cast<const double2*>(J.X + (size_t)row * K + kXh * hx);
 #pragma unroll
     for (int c = 0; c < kXh / 2; ++c) {
       const double2 v = xr[c];
@@ -108,11 +118,11 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
   }
   __syncthreads();  // M staged
   // element (l, j) of the matrix used: M, or M^T with transM
-  auto mu = [&](int l, int j) { return J.transM ? Ms[j + l * kRpK] : Ms[l + j * kRpK]; };
+  auto mu = [&](int l, int j) { return J.transM ? Ms[j + l * K] : Ms[l + j * K]; };
   if (tid < kRpN) {
     int m = 0;
 #pragma unroll 8
-    for (int l = 0; l < kRpK; ++l) m = max(m, biased_exponent(mu(l, jb + tid)));
+    for (int l = 0; l < K; ++l) m = max(m, biased_exponent(mu(l, jb + tid)));
     fexp[tid] = m;
   }
   int erow = 0;
@@ -125,15 +135,15 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
     int d[8][kOzDigits];
 #pragma unroll
     for (int e = 0; e < 8; ++e) ozaki_digits(x[c8 + e], erow, d[e]);
-    const uint32_t off = umma_kmajor_offset(r, kXh * hx + c8, kRpK);
+    const uint32_t off = umma_kmajor_offset(r, kXh * hx + c8, K);
 #pragma unroll
     for (int t = 0; t < kOzDigits; ++t) {
       const int dt[8] = {d[0][t], d[1][t], d[2][t], d[3][t], d[4][t], d[5][t], d[6][t], d[7][t]};
-      *reinterpret_cast<uint4*>(As + (size_t)t * kRpATile + off) = pack8(dt);
+      *reinterpret_cast<uint4*>(As + (size_t)t * C::ATile + off) = pack8(dt);
     }
   }
   __syncthreads();  // column and row scales ready
-  if (tid < kRpN * (kRpK / 8)) {  // column jj, values 8 g .. 8 g + 7 of l
+  if (tid < kRpN * (K / 8)) {  // column jj, values 8 g .. 8 g + 7 of l
     const int jj = tid % kRpN, g = tid / kRpN;
     int d[8][kOzDigits];
 #pragma unroll
@@ -141,7 +151,7 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
 #pragma unroll
     for (int u = 0; u < kOzDigits; ++u) {
       const int du[8] = {d[0][u], d[1][u], d[2][u], d[3][u], d[4][u], d[5][u], d[6][u], d[7][u]};
-      *reinterpret_cast<uint4*>(Bs + umma_kmajor_offset(kRpN * u + jj, 8 * g, kRpK)) = pack8(du);
+      *reinterpret_cast<uint4*>(Bs + umma_kmajor_offset(kRpN * u + jj, 8 * g, K)) = pack8(du);
     }
   }
   // the digits were written by ordinary stores; the MMAs read shared memory through the async proxy
@@ -156,9 +166,9 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
     for (int t = 0; t < kOzDigits; ++t) {
       const uint32_t idesc = umma_idesc_bf16_f32(kRpRows, kRpN * (kOzDigits - t));
 #pragma unroll
-      for (int k = 0; k < kRpK / 16; ++k)
-        umma_bf16(tmem + (uint32_t)(kRpN * t), umma_smem_desc(a0 + (uint32_t)t * kRpATile + 256u * k, 128, kRpSbo),
-                  umma_smem_desc(b0 + 256u * k, 128, kRpSbo), idesc, (t == 0 && k == 0) ? 0u : 1u);
+      for (int k = 0; k < K / 16; ++k)
+        umma_bf16(tmem + (uint32_t)(kRpN * t), umma_smem_desc(a0 + (uint32_t)t * C::ATile + 256u * k, 128, C::Sbo),
+                  umma_smem_desc(b0 + 256u * k, 128, C::Sbo), idesc, (t == 0 && k == 0) ? 0u : 1u);
     }
     umma_commit(bar);
   }
@@ -195,7 +205,7 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
     // rounding drops less than 2^-56 of the scales), one conversion to FP64, the scale by exponent
     const int orow = blockIdx.x * kRpRows + dr, er = erows[dr];
     if (orow < n) {
-      double* yr = J.Y + (size_t)orow * kRpK + jb + c0;
+      double* yr = J.Y + (size_t)orow * K + jb + c0;
 #pragma unroll
       for (int j = 0; j < kDn; j += 2) {
         double2 v;
@@ -215,15 +225,23 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
   if (warp == 0) tmem_dealloc(tmem, kRpTmemCols);
 }
 
-void rowprod_tc(cudaStream_t s, int n, const RowProdJobs& jobs, int njobs, const SolveState* st, int skip_on_pw,
-                int* err) {
+template <int K>
+static void rowprod_tc_k(cudaStream_t s, int n, const RowProdJobs& jobs, int njobs, const SolveState* st,
+                         int skip_on_pw, int* err) {
+  using C = RpCfg<K>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_rowprod_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRpSmem);
+    cudaFuncSetAttribute(k_rowprod_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::Smem);
     attr = true;
   }
-  k_rowprod_tc<<<dim3((n + kRpRows - 1) / kRpRows, 2 * njobs), kRpThreads, kRpSmem, s>>>(n, jobs, st, skip_on_pw,
-                                                                                            err);
+  k_rowprod_tc<K><<<dim3((n + kRpRows - 1) / kRpRows, C::Halves * njobs), kRpThreads, C::Smem, s>>>(n, jobs, st,
+                                                                                                    skip_on_pw, err);
+}
+
+void rowprod_tc(cudaStream_t s, int n, int kp, const RowProdJobs& jobs, int njobs, const SolveState* st,
+                int skip_on_pw, int* err) {
+  if (kp == 16) rowprod_tc_k<16>(s, n, jobs, njobs, st, skip_on_pw, err);
+  else rowprod_tc_k<32>(s, n, jobs, njobs, st, skip_on_pw, err);
 }
 
 }  // namespace mbpcg

@@ -165,17 +165,18 @@ def test_dense_tc_product_matches_oracle(mb, orc, n, s):
     assert np.all(np.abs(got[:, :s] - ref[:, :s]) <= 1e-14 * scale[:, :s] + 1e-300)
 
 
+@pytest.mark.parametrize("w", [16, 32])
 @pytest.mark.parametrize("trans", [0, 1])
 @pytest.mark.parametrize("n", [1, 127, 128, 300, 4099])
-def test_rowprod_tc_matches_oracle(mb, orc, n, trans):
-    """The k x k-row products on the tensor cores (Y = X M, X n x 32, M 32 x 32, digit splitting)
+def test_rowprod_tc_matches_oracle(mb, orc, n, trans, w):
+    """The k x k-row products on the tensor cores (Y = X M, X n x w, M w x w, digit splitting)
     against the oracle's FP64 product of the same data. Columns of X and entries of M spread over
     several orders of magnitude, as in the loop (T = Xi Sigma). Bound: the digits keep 56 bits of
     each row scale of X and column scale of M, so the error is a few 2^-53 of
-    max_l |X_il| sum_l |M_lj| + sum_l |X_il| max_l |M_lj|; the oracle's own FP64 sum adds 32 u of
+    max_l |X_il| sum_l |M_lj| + sum_l |X_il| max_l |M_lj|; the oracle's own FP64 sum adds w u of
     sum_l |X_il||M_lj|."""
-    X = wl.initial_block(n, 32, 12) * 10.0 ** (2 * wl.uniform_pm1(3, 91, 32))[None, :]
-    M = (wl.uniform_pm1(5, 92, 32 * 32) * 10.0 ** (3 * wl.uniform_pm1(5, 93, 32 * 32))).reshape(32, 32, order="F")
+    X = wl.initial_block(n, w, 12) * 10.0 ** (2 * wl.uniform_pm1(3, 91, w))[None, :]
+    M = (wl.uniform_pm1(5, 92, w * w) * 10.0 ** (3 * wl.uniform_pm1(5, 93, w * w))).reshape(w, w, order="F")
     M[5, :] = 0.0  # a zero row and column
     M[:, 7] = 0.0
     X[::7, :] = 0.0  # zero rows of X
@@ -183,19 +184,20 @@ def test_rowprod_tc_matches_oracle(mb, orc, n, trans):
     Xd = torch.as_tensor(np.ascontiguousarray(X), device=dev)
     Md = torch.as_tensor(np.asfortranarray(M).ravel(order="F"), device=dev)
     Yd = torch.full_like(Xd, float("nan"))
-    assert mb.mbpcg_k_rowprod_tc(n, Xd, Md, trans, Yd, None) == 0, mb.last_error()
+    assert mb.mbpcg_k_rowprod_tc(n, w, Xd, Md, trans, Yd, None) == 0, mb.last_error()
     torch.cuda.synchronize()
     got = Yd.cpu().numpy()
     Mu = M.T if trans else M  # the matrix used
     # the oracle's product: Y^T = Mu^T X^T, Mu^T as a 32 x 32 dense matrix
-    ref = orc.matmat(wl.Dense(32, np.asfortranarray(Mu.T)), np.asfortranarray(X.T)).T
+    ref = orc.matmat(wl.Dense(w, np.asfortranarray(Mu.T)), np.asfortranarray(X.T)).T
     aX, aM = np.abs(X), np.abs(Mu)
     bound = aX.max(axis=1)[:, None] * aM.sum(axis=0)[None, :] + aX.sum(axis=1)[:, None] * aM.max(axis=0)[None, :]
     assert np.all(np.isfinite(got))
     assert np.all(np.abs(got - ref) <= 2.0 ** -48 * bound + 1e-300)
     zero_col = 5 if trans else 7  # the zero column of the matrix used
     assert np.all(got[::7, :] == 0.0) and np.all(got[:, zero_col] == 0.0)
-    assert mb.mbpcg_k_rowprod_tc(n, Xd, Md, 2, Yd, None) == mb._native.MBPCG_ERR_INVALID
+    assert mb.mbpcg_k_rowprod_tc(n, w, Xd, Md, 2, Yd, None) == mb._native.MBPCG_ERR_INVALID
+    assert mb.mbpcg_k_rowprod_tc(n, 8, Xd, Md, 0, Yd, None) == mb._native.MBPCG_ERR_INVALID
 
 
 def test_dense_tc_mma_alone_leaves_the_product_untouched(mb):

@@ -99,10 +99,13 @@ TC_CASES = [
     # rounding-level perturbations of b, so that case is not a parity case; s = 8 is stable)
     ("dense_mtm150_s8_tc", lambda: wl.dense_mtm(150, 0), 8, 0),
     ("dense300_s32_tc", lambda: wl.dense_spd(300, 2, 0.0, 4.0), 32, 0),
-    # s > 16 also runs the k x k-row products of both row passes on the tensor cores: several
+    # s > 8 also runs the k x k-row products of both row passes on the tensor cores: several
     # 128-row tiles with a ragged last one, and the scaled residual norms (Jacobi)
     ("dense1031_s32_tc", lambda: wl.dense_spd(1031, 4, 0.0, 4.0), 32, 0),
     ("dense300_s20_jacobi_tc", lambda: wl.dense_spd(300, 6, 0.0, 3.0), 20, 1),
+    # s = 9..16 (KP = 16): the same products at width 16
+    ("dense300_s16_tc", lambda: wl.dense_spd(300, 7, 0.0, 4.0), 16, 0),
+    ("dense257_s12_jacobi_tc", lambda: wl.dense_spd(257, 8, 0.0, 3.0), 12, 1),
 ]
 
 
