@@ -50,6 +50,44 @@ def test_library_loads_and_answers_without_gpu(libpath):
     assert [L.mbpcg_k_padded_width(s) for s in (1, 2, 3, 5, 9, 17, 32, 33)] == [1, 2, 4, 8, 16, 32, 32, 0]
 
 
+def test_component_entries_reject_bad_arguments_without_gpu(libpath):
+    """Argument checks of the component entries come before any device call, so they answer on a
+    machine without a GPU: MBPCG_ERR_INVALID (1) for bad sizes, widths, NULL or misaligned pointers,
+    and sizes of the FP32 copy of a dense A that follow its tiling (256 x 32 FP32 tiles)."""
+    L = ctypes.CDLL(libpath)
+    P, I32, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+    L.mbpcg_k_dense_f32_bytes.restype = SZ
+    L.mbpcg_k_dense_f32_bytes.argtypes = [I32]
+    tile = 256 * 32 * 4
+    assert L.mbpcg_k_dense_f32_bytes(0) == 0
+    assert L.mbpcg_k_dense_f32_bytes(1) == tile
+    assert L.mbpcg_k_dense_f32_bytes(256) == 8 * tile
+    assert L.mbpcg_k_dense_f32_bytes(257) == 2 * 9 * tile
+    assert L.mbpcg_k_dense_f32_bytes(4096) == 4096 * 4096 * 4
+    buf = ctypes.create_string_buffer(64)
+    aligned = ctypes.addressof(buf) // 16 * 16 + 16  # inside buf, 16-byte aligned
+    L.mbpcg_k_rowprod_tc.restype = ctypes.c_int
+    L.mbpcg_k_rowprod_tc.argtypes = [I32, I32, P, P, I32, P, P]
+    assert L.mbpcg_k_rowprod_tc(0, 32, aligned, aligned, 0, aligned, None) == 1  # n < 1
+    assert L.mbpcg_k_rowprod_tc(4, 8, aligned, aligned, 0, aligned, None) == 1   # width not 16 or 32
+    assert L.mbpcg_k_rowprod_tc(4, 32, aligned, aligned, 2, aligned, None) == 1  # transM not 0 or 1
+    assert L.mbpcg_k_rowprod_tc(4, 32, None, aligned, 0, aligned, None) == 1     # NULL X
+    assert L.mbpcg_k_rowprod_tc(4, 32, aligned + 8, aligned, 0, aligned, None) == 1  # X not 16-byte aligned
+    L.mbpcg_k_dense_f32_prepare.restype = ctypes.c_int
+    L.mbpcg_k_dense_f32_prepare.argtypes = [I32, P, P, SZ, P]
+    assert L.mbpcg_k_dense_f32_prepare(8, aligned, aligned, tile - 1, None) == 1  # tiles too small
+    assert L.mbpcg_k_dense_f32_prepare(8, None, aligned, tile, None) == 1         # NULL A
+    assert L.mbpcg_k_dense_f32_prepare(8, aligned, aligned + 8, tile, None) == 1  # tiles misaligned
+    L.mbpcg_k_dense_f32.restype = ctypes.c_int
+    L.mbpcg_k_dense_f32.argtypes = [I32, P, I32, P, P, P]
+    assert L.mbpcg_k_dense_f32(8, aligned, 33, aligned, aligned, None) == 1  # s > 32
+    assert L.mbpcg_k_dense_f32(8, None, 4, aligned, aligned, None) == 1      # NULL tiles
+    L.mbpcg_k_dense_tc_mma.restype = ctypes.c_int
+    L.mbpcg_k_dense_tc_mma.argtypes = [I32, I32, P, SZ, P]
+    assert L.mbpcg_k_dense_tc_mma(0, 32, aligned, 1 << 30, None) == 1  # n < 1
+    assert L.mbpcg_k_dense_tc_mma(64, 0, aligned, 1 << 30, None) == 1  # s < 1
+
+
 def test_binding_names_match_the_abi():
     import paper_2608_07327_gb300 as pkg
     for name in declared_functions():
