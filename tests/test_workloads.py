@@ -41,3 +41,26 @@ def test_serving_requests_mix():
     dec = np.histogram(np.log10(ns), bins=[2.9, 4.0, 5.0, 6.1])[0]
     assert dec.min() > 800
     assert all(r["precond"] == (1 if r["kind"] == "diffusion3d" else 0) for r in reqs)
+
+
+def test_dense_spd_spectrum_and_symmetry():
+    """The dense family A = Q diag(lambda) Q^T: exactly symmetric, eigenvalues the drawn lambdas
+    (up to rounding), all inside [10^lo, 10^hi]; the kappa <= 1e4 variant stays inside its band."""
+    for n, lo, hi in ((64, 0.0, 6.0), (100, 0.0, 4.0)):
+        D = wl.dense_spd(n, 3, lo, hi)
+        A = np.asarray(D.a)
+        assert A.flags.f_contiguous and abs(A - A.T).max() == 0.0
+        lam = 10.0 ** (lo + (hi - lo) * wl.uniform01(3, 2002, n))
+        ev = np.linalg.eigvalsh(A)
+        assert np.allclose(np.sort(ev), np.sort(lam), rtol=1e-9, atol=1e-9 * lam.max())
+        assert ev.min() >= 10.0 ** lo * (1 - 1e-9) and ev.max() <= 10.0 ** hi * (1 + 1e-9)
+
+
+def test_stencil27_diagonal_shift():
+    """27-point family: every diagonal entry is the row's sum of |off-diagonals| plus 1e-2, so the
+    smallest eigenvalue is at least 1e-2 (Gershgorin) and the matrix is SPD."""
+    S = wl.stencil27(6, 1).to_scipy().tocsr()
+    d = S.diagonal()
+    off = np.asarray(abs(S).sum(axis=1)).ravel() - np.abs(d)
+    assert np.allclose(d, off + 1e-2, rtol=0, atol=1e-12)
+    assert np.linalg.eigvalsh(S.toarray()).min() >= 1e-2 - 1e-12
