@@ -14,7 +14,7 @@
 // One CTA of 256 threads per (128-row tile, product, 16 output columns: K / 16 CTAs): M is staged
 // in shared memory by one coalesced load; two threads per row write the 8 digits of their K / 2
 // values of X into shared memory (K-major, no swizzle: 8 tiles of 128 x K bf16; 16-byte stores of 8
-// consecutive digits; the row scale is combined by one shuffle), 4 K threads the 8 digits of the
+// consecutive digits; the row scale is combined by one shuffle), 2 K threads the 8 digits of the
 // CTA's 16 columns of M (128 x K: row 16 u + j holds digit u of column j); one thread issues
 // 8 K / 16 MMAs (digit t of X against digits 0..7-t of M, N = 16 (8 - t), into TMEM columns
 // 16 t .. 127),
