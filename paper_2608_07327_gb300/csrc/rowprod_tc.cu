@@ -17,9 +17,8 @@
 // consecutive digits; the row scale is combined by one shuffle), 2 K threads the 8 digits of the
 // CTA's 16 columns of M (128 x K: row 16 u + j holds digit u of column j); one thread issues
 // 8 K / 16 MMAs (digit t of X against digits 0..7-t of M, N = 16 (8 - t), into TMEM columns
-// 16 t .. 127),
-// and each warp drains 8 columns of its 32 rows (warps w and w + 4 share a TMEM lane quarter): 8
-// loads, the combination above, and one FP64 scaling per value. Two CTAs fit on an SM (81 KB of
+// 16 t .. 127), and each warp drains 8 columns of its 32 rows (warps w and w + 4 share a TMEM lane
+// quarter): 8 loads, the combination above, and one FP64 scaling per value. Two CTAs fit on an SM (81 KB of
 // shared memory at K = 32, 128 TMEM columns each), so one phase of a CTA overlaps another's.
 #include "kernels.h"
 #include "ozaki_digits.cuh"
