@@ -41,7 +41,7 @@ typedef struct mbpcg_ctx* mbpcg_handle;
 
 typedef enum {
   MBPCG_OK = 0,
-  MBPCG_ERR_INVALID = 1,   /* bad argument or malformed CSR (checked at create) */
+  MBPCG_ERR_INVALID = 1,   /* bad argument, malformed CSR or non-finite A (checked at create) */
   MBPCG_ERR_OOM = 2,       /* device allocation failed or workspace too small */
   MBPCG_ERR_CUDA = 3,      /* CUDA runtime error (see mbpcg_last_error) */
   MBPCG_ERR_NOT_SPD = 4,   /* a diagonal entry is missing, not positive or not finite */
@@ -101,8 +101,8 @@ size_t mbpcg_workspace_size_dense(int32_t n, int32_t s, int32_t algo, int32_t pr
  *   workspace device buffer of mbpcg_workspace_size_csr() bytes, or NULL to let the library
  *             allocate; stream: a cudaStream_t, or NULL for a stream owned by the handle.
  * Validation: 1 <= n, 0 <= nnz < 2^31, row_ptr[0] = 0, row_ptr monotone, row_ptr[n] = nnz,
- * 0 <= col_idx < n (MBPCG_ERR_INVALID); every row has a positive finite diagonal
- * (MBPCG_ERR_NOT_SPD). Symmetry is a precondition and is not checked.
+ * 0 <= col_idx < n, every value finite (MBPCG_ERR_INVALID); every row has a positive finite
+ * diagonal (MBPCG_ERR_NOT_SPD). Symmetry is a precondition and is not checked.
  */
 int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* row_ptr,
                      const int32_t* col_idx, const double* vals, int32_t s, int32_t precond,
@@ -110,7 +110,8 @@ int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* r
                      size_t workspace_bytes, void* stream);
 
 /* Create a solver for dense SPD A (column-major n x n doubles; A symmetric, so either triangle
- * may be read). Same conventions as mbpcg_create_csr. */
+ * may be read). Same conventions as mbpcg_create_csr; every entry must be finite
+ * (MBPCG_ERR_INVALID). */
 int mbpcg_create_dense(mbpcg_handle* out, int32_t n, const double* A_colmajor, int32_t s,
                        int32_t precond, int32_t algo, int32_t precision, uint64_t seed,
                        int32_t mem, void* workspace, size_t workspace_bytes, void* stream);

@@ -420,12 +420,15 @@ int finish_create(mbpcg_ctx* h) {
   const int n = h->dm.n;
   const int g = (n + 255) / 256;
   CUDA_TRY(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+  const long long nvals = h->dm.dense ? (long long)n * n : h->dm.nnz;
+  if (nvals > 0) k_check_finite<<<4 * 152, 256, 0, h->stream>>>(nvals, h->dm.dense ? h->A : h->av, h->flag);
   if (h->dm.dense) k_diag_dense<<<g, 256, 0, h->stream>>>(n, h->A, h->diag, h->flag);
   else k_diag_csr<<<g, 256, 0, h->stream>>>(n, h->rp, h->ci, h->av, h->diag, h->flag);
   CUDA_TRY(cudaGetLastError());
   int flag = 0;
   int rc = read_flag(h, &flag);
   if (rc) return rc;
+  if (flag & 4) return set_err(MBPCG_ERR_INVALID, "an entry of A is NaN or infinite");
   if (flag & 2) return set_err(MBPCG_ERR_NOT_SPD, "a diagonal entry of A is missing, not positive or not finite");
   if (h->precond == MBPCG_PRECOND_JACOBI) {
     k_make_scaling<<<g, 256, 0, h->stream>>>(n, h->diag, h->d, h->sqd);

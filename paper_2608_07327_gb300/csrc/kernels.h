@@ -128,6 +128,7 @@ __global__ void k_small_cg(SolveState* st, const double* red, cudaGraphCondition
 __global__ void k_validate_csr(int n, long long nnz, const int* rp, const int* ci, int* flag);
 __global__ void k_diag_csr(int n, const int* rp, const int* ci, const double* av, double* diag, int* flag);
 __global__ void k_diag_dense(int n, const double* A, double* diag, int* flag);
+__global__ void k_check_finite(long long count, const double* v, int* flag);
 __global__ void k_make_scaling(int n, const double* diag, double* d, double* sqd);
 __global__ void k_scale_csr(int n, const int* rp, const int* ci, double* av, const double* d);
 __global__ void k_scale_dense(int n, double* A, const double* d);

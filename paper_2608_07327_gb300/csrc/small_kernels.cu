@@ -274,6 +274,15 @@ __global__ void k_diag_dense(int n, const double* __restrict__ A, double* __rest
   if (!(a > 0.0) || !isfinite(a)) atomicOr(flag, 2);
 }
 
+// flag |= 4 if any of the count values is NaN or infinite (grid-stride; one atomic per warp).
+__global__ void k_check_finite(long long count, const double* __restrict__ v, int* __restrict__ flag) {
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    bad |= !isfinite(v[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 4);
+}
+
 // d = 1/sqrt(diag) (= D^{-1} of Section 1), sqd = sqrt(diag) (= D), wdiag = diag (= D^2).
 __global__ void k_make_scaling(int n, const double* __restrict__ diag, double* __restrict__ d,
                                double* __restrict__ sqd) {

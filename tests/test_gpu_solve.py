@@ -304,6 +304,17 @@ def test_invalid_inputs_fail_loudly(mb):
     assert e.value.status == 4
     with pytest.raises(mb.MBPCGError):
         mb.Solver(A, s=33)
+    nan_off = wl.CSR(A.n, A.row_ptr.copy(), A.col_idx.copy(), A.val.copy())
+    off = next(p for p in range(A.row_ptr[1]) if A.col_idx[p] != 0)
+    nan_off.val[off] = np.nan
+    with pytest.raises(mb.MBPCGError) as e:
+        mb.Solver(nan_off, s=2)
+    assert e.value.status == 1
+    D = wl.dense_spd(40, 0)
+    D.a[3, 7] = np.inf
+    with pytest.raises(mb.MBPCGError) as e:
+        mb.Solver(D, s=2)
+    assert e.value.status == 1
 
 
 # ------------------------------------------------------------------ full-size workloads
