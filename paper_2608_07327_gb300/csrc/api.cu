@@ -421,7 +421,7 @@ int finish_create(mbpcg_ctx* h) {
   const int g = (n + 255) / 256;
   CUDA_TRY(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
   const long long nvals = h->dm.dense ? (long long)n * n : h->dm.nnz;
-  if (nvals > 0) k_check_finite<<<4 * 152, 256, 0, h->stream>>>(nvals, h->dm.dense ? h->A : h->av, h->flag);
+  if (nvals > 0) k_check_finite<<<4 * h->dm.sms, 256, 0, h->stream>>>(nvals, h->dm.dense ? h->A : h->av, h->flag);
   if (h->dm.dense) k_diag_dense<<<g, 256, 0, h->stream>>>(n, h->A, h->diag, h->flag);
   else k_diag_csr<<<g, 256, 0, h->stream>>>(n, h->rp, h->ci, h->av, h->diag, h->flag);
   CUDA_TRY(cudaGetLastError());
@@ -432,7 +432,7 @@ int finish_create(mbpcg_ctx* h) {
   if (flag & 2) return set_err(MBPCG_ERR_NOT_SPD, "a diagonal entry of A is missing, not positive or not finite");
   if (h->precond == MBPCG_PRECOND_JACOBI) {
     k_make_scaling<<<g, 256, 0, h->stream>>>(n, h->diag, h->d, h->sqd);
-    if (h->dm.dense) k_scale_dense<<<4 * 152, 256, 0, h->stream>>>(n, h->A, h->d);
+    if (h->dm.dense) k_scale_dense<<<4 * h->dm.sms, 256, 0, h->stream>>>(n, h->A, h->d);
     else k_scale_csr<<<g, 256, 0, h->stream>>>(n, h->rp, h->ci, h->av, h->d);
     CUDA_TRY(cudaGetLastError());
     h->wdiag = h->diag;
@@ -442,7 +442,7 @@ int finish_create(mbpcg_ctx* h) {
     h->wdiag = nullptr;
   }
   if (h->dm.mixed) {
-    if (h->dm.dense) k_dense_to_f32_tiles<<<4 * 152, 256, 0, h->stream>>>(n, h->A, h->A32);
+    if (h->dm.dense) k_dense_to_f32_tiles<<<4 * h->dm.sms, 256, 0, h->stream>>>(n, h->A, h->A32);
     else k_to_f32<<<1024, 256, 0, h->stream>>>((long long)h->dm.nnz, h->av, h->av32);
     if (h->wdiag != nullptr) k_to_f32<<<(n + 255) / 256, 256, 0, h->stream>>>(n, h->wdiag, h->wd32);
     else h->wd32 = nullptr;
@@ -1111,7 +1111,9 @@ int mbpcg_k_dense_f32_prepare(int32_t n, const double* A, void* tiles, size_t ti
   if (n < 1 || !A || !tiles) return set_err(MBPCG_ERR_INVALID, "bad arguments");
   if (tiles_bytes < dense_f32_tiles_bytes(n)) return set_err(MBPCG_ERR_INVALID, "tiles buffer too small");
   if (reinterpret_cast<uintptr_t>(tiles) % 16 != 0) return set_err(MBPCG_ERR_INVALID, "tiles must be 16-byte aligned");
-  k_dense_to_f32_tiles<<<4 * 152, 256, 0, (cudaStream_t)stream>>>(n, A, static_cast<float*>(tiles));
+  const int sms = num_sms();
+  if (sms <= 0) return set_err(MBPCG_ERR_CUDA, "no CUDA device available");
+  k_dense_to_f32_tiles<<<4 * sms, 256, 0, (cudaStream_t)stream>>>(n, A, static_cast<float*>(tiles));
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }
