@@ -130,6 +130,15 @@ int mbpcg_k_rowprod_tc(int32_t n, int32_t width, const double* X, const double* 
  * to 0, or to 6 (MBPCG_BREAKDOWN) when a pivot is not finite or not above 64 eps max_j G_jj. */
 int mbpcg_k_cholesky(int32_t s, const double* G, double* Z, int32_t* status_dev, void* stream);
 
+/* The reciprocal 1/d and the inverse square root 1/sqrt(d) that the loop's k x k steps take of
+ * their pivots (the LDL^T elimination behind Xi = (P^T A P)^{-1} and the Cholesky QR of V,
+ * Section 3): the FP32 hardware approximation of d's leading 23 significand bits, rescaled by d's
+ * exponent with integer operations, then one third-order Newton step in FP64. For a positive
+ * normal d below 2^1000 (the only pivots those steps accept) inv is within 0.51 ulp of 1/d and rsq
+ * within 1.01 ulp of 1/sqrt(d); other d give unspecified values, with no error. d, inv, rsq:
+ * device, n doubles each; inv and rsq are written. MBPCG_ERR_INVALID for n < 1 or a NULL pointer. */
+int mbpcg_k_pivot_reciprocals(int32_t n, const double* d, double* inv, double* rsq, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

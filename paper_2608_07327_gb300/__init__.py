@@ -11,7 +11,7 @@ import numpy as np
 
 from . import _native
 from ._native import (  # noqa: F401  (re-exported C ABI names)
-    Info, MBPCGError, lib, lib_path, mbpcg_create_csr, mbpcg_create_dense, mbpcg_destroy, mbpcg_k_cholesky,
+    Info, MBPCGError, lib, lib_path, mbpcg_create_csr, mbpcg_create_dense, mbpcg_destroy, mbpcg_k_cholesky, mbpcg_k_pivot_reciprocals,
     mbpcg_k_dense_gram, mbpcg_k_dense_product, mbpcg_k_dense_tc_prepare, mbpcg_k_dense_tc_product, mbpcg_k_dense_tc_mma, mbpcg_k_rowprod_tc, mbpcg_k_dense_tc_scratch_bytes, mbpcg_k_spmm, mbpcg_k_spmm_gram_noalloc, mbpcg_k_padded_width, mbpcg_k_scratch_bytes, mbpcg_k_spmm_gram, mbpcg_run_iterations_dev,
     mbpcg_set_launch_mode, mbpcg_solve, mbpcg_solve_dev, mbpcg_workspace_size_csr, mbpcg_workspace_size_dense, status_string, last_error,
     MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN, MBPCG_PRECOND_NONE, MBPCG_PRECOND_JACOBI, MBPCG_ALGO_MBPCG,

@@ -101,6 +101,7 @@ _SIGS = {
     "mbpcg_k_spmm_gram": (ctypes.c_int, [_I32, _P, _P, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_dense_gram": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P, _P, _SZ, _P]),
     "mbpcg_k_cholesky": (ctypes.c_int, [_I32, _P, _P, _P, _P]),
+    "mbpcg_k_pivot_reciprocals": (ctypes.c_int, [_I32, _P, _P, _P, _P]),
     "mbpcg_k_dense_tc_scratch_bytes": (_SZ, [_I32, _I32]),
     "mbpcg_k_dense_tc_prepare": (ctypes.c_int, [_I32, _P, _I32, _P, _SZ, _P]),
     "mbpcg_k_dense_tc_product": (ctypes.c_int, [_I32, _I32, _P, _P, _P, _SZ, _P]),
@@ -293,6 +294,10 @@ def mbpcg_k_dense_tc_product(n, s, P, AP, scratch, scratch_bytes, stream=None):
 
 def mbpcg_k_cholesky(s, G, Z, status_dev, stream=None):
     return lib().mbpcg_k_cholesky(s, ptr(G), ptr(Z), ptr(status_dev), stream)
+
+
+def mbpcg_k_pivot_reciprocals(n, d, inv, rsq, stream=None):
+    return lib().mbpcg_k_pivot_reciprocals(n, ptr(d), ptr(inv), ptr(rsq), stream)
 
 
 def mbpcg_server_create(slots, hbm_budget_bytes=0):

@@ -1237,6 +1237,13 @@ int mbpcg_k_cholesky(int32_t s, const double* G, double* Z, int32_t* status_dev,
   return MBPCG_OK;
 }
 
+int mbpcg_k_pivot_reciprocals(int32_t n, const double* d, double* inv, double* rsq, void* stream) {
+  if (n < 1 || !d || !inv || !rsq) return set_err(MBPCG_ERR_INVALID, "bad arguments");
+  launch_pivot_recips((cudaStream_t)stream, n, d, inv, rsq);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
 }  // extern "C"
 
 namespace mbpcg {

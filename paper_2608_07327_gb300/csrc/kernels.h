@@ -187,6 +187,8 @@ void launch_small_xi(cudaStream_t s, int kp, SolveState* st, const double* G1p, 
                      double* T);
 void launch_small_zeta(cudaStream_t s, int kp, SolveState* st, const double* G2nu, double* Sigma, double* Zeta,
                        double* ZetaInv, cudaGraphConditionalHandle cond, int use_cond);
+// the pivots' 1/d and 1/sqrt(d) of those steps, elementwise over n values (small_warp.cu)
+void launch_pivot_recips(cudaStream_t s, int n, const double* d, double* inv, double* rsq);
 
 // launch shape of the CSR product + Gram entry points, and the thread-local error message (api.cu)
 void product_gram_shape(int n, int s, int* kp, int* nb, int* pstride);

@@ -685,7 +685,24 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
   }
 }
 
+// 1/d and 1/sqrt(d) exactly as the k x k steps take them of their pivots, one value per thread
+// (grid-stride), for the component entry that checks them against their error bounds.
+__global__ void k_pivot_recips(long long n, const double* __restrict__ d, double* __restrict__ inv,
+                               double* __restrict__ rsq) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double v = d[i];
+    inv[i] = rcp_pos(v);
+    rsq[i] = rsqrt_pos(v);
+  }
+}
+
 // ------------------------------------------------------------------------------------ launchers
+
+void launch_pivot_recips(cudaStream_t s, int n, const double* d, double* inv, double* rsq) {
+  const int nb = n / 256 + 1 < 1024 ? n / 256 + 1 : 1024;
+  k_pivot_recips<<<nb, 256, 0, s>>>(n, d, inv, rsq);
+}
 
 // Set-up: one warp (KP <= 8) or one CTA of 256 threads. Loop: a cluster of CTAs, computed 16 wide for
 // KP <= 8 (the identity outside s x s) and stored at the handle's width.

@@ -86,6 +86,10 @@ def test_component_entries_reject_bad_arguments_without_gpu(libpath):
     L.mbpcg_k_dense_tc_mma.argtypes = [I32, I32, P, SZ, P]
     assert L.mbpcg_k_dense_tc_mma(0, 32, aligned, 1 << 30, None) == 1  # n < 1
     assert L.mbpcg_k_dense_tc_mma(64, 0, aligned, 1 << 30, None) == 1  # s < 1
+    L.mbpcg_k_pivot_reciprocals.restype = ctypes.c_int
+    L.mbpcg_k_pivot_reciprocals.argtypes = [I32, P, P, P, P]
+    assert L.mbpcg_k_pivot_reciprocals(0, aligned, aligned, aligned, None) == 1  # n < 1
+    assert L.mbpcg_k_pivot_reciprocals(4, aligned, None, aligned, None) == 1     # NULL inv
 
 
 def test_binding_names_match_the_abi():

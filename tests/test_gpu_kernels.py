@@ -139,6 +139,49 @@ def test_cholesky_kernel_breakdown(mb):
     assert int(status.item()) == 6
 
 
+def _ulp_error(y, ref):
+    """|y - ref| in units of the FP64 ulp of ref (2^(floor(log2 ref) - 52)), in extended precision."""
+    _, ex = np.frexp(ref)
+    ulp = np.ldexp(np.longdouble(1.0), (ex - 53).astype(np.int64))
+    return np.abs(y.astype(np.longdouble) - ref) / ulp
+
+
+def test_pivot_reciprocals_within_their_error_bounds(mb):
+    """The pivots' 1/d and 1/sqrt(d) of the k x k steps (FP32 hardware seed + one third-order Newton
+    step in FP64) against the exact values, computed in extended precision: within 0.51 ulp and
+    1.01 ulp (the bounds the error analysis of the Newton step gives: the seed's relative error is
+    below 2^-22, so the truncated series adds below 2^-64; the inverse square root takes one more
+    rounding, of d y0, worth half an ulp), over the whole accepted range 2^-1022 <= d < 2^1000."""
+    if np.finfo(np.longdouble).nmant < 63:
+        pytest.skip("no extended-precision long double for the exact reference")
+    m = 200_003  # ragged against the 256-thread CTAs
+    sig = 1.0 + wl.uniform01(3, 7000, m)
+    ex = np.floor(-1022 + 2022 * wl.uniform01(3, 7001, m)).astype(np.int64)
+    top = np.nextafter(2.0 ** 1000, 0.0)
+    edges = np.array([1.0, 2.0, np.nextafter(2.0, 0.0), np.nextafter(1.0, 2.0), 2.0 ** -1022, top, 3.0, 0.75,
+                      np.nextafter(4.0, 0.0), 2.0 ** 999, 2.0 ** -1021 * 1.5])
+    pw2 = np.ldexp(1.0, np.arange(-1022, 1000))  # powers of two: both results are exact for even exponents
+    d = np.concatenate([np.minimum(np.ldexp(sig, ex), top), edges, pw2])
+    assert np.all(d >= 2.0 ** -1022) and np.all(d < 2.0 ** 1000)
+    dev = torch.device("cuda")
+    dd = torch.as_tensor(d, device=dev)
+    inv = torch.full_like(dd, float("nan"))
+    rsq = torch.full_like(dd, float("nan"))
+    assert mb.mbpcg_k_pivot_reciprocals(d.size, dd, inv, rsq, None) == 0
+    torch.cuda.synchronize()
+    inv_h, rsq_h = inv.cpu().numpy(), rsq.cpu().numpy()
+    dl = d.astype(np.longdouble)
+    e_inv = _ulp_error(inv_h, 1 / dl)
+    e_rsq = _ulp_error(rsq_h, 1 / np.sqrt(dl))
+    assert np.all(np.isfinite(inv_h)) and np.all(np.isfinite(rsq_h))
+    assert e_inv.max() <= 0.51, (float(e_inv.max()), d[np.argmax(e_inv)])
+    assert e_rsq.max() <= 1.01, (float(e_rsq.max()), d[np.argmax(e_rsq)])
+    k = d.size - pw2.size
+    assert np.array_equal(inv_h[k:], 1.0 / pw2)  # 1 / 2^j is exact
+    even = (np.arange(-1022, 1000) % 2) == 0
+    assert np.array_equal(rsq_h[k:][even], 1.0 / np.sqrt(pw2[even]))  # 2^(-j/2) is exact for even j
+
+
 @pytest.mark.parametrize("s", [1, 4, 9, 16, 32])
 @pytest.mark.parametrize("n", [64, 300, 1031, 2049])
 def test_dense_tc_product_matches_oracle(mb, orc, n, s):
