@@ -64,3 +64,36 @@ def test_stencil27_diagonal_shift():
     off = np.asarray(abs(S).sum(axis=1)).ravel() - np.abs(d)
     assert np.allclose(d, off + 1e-2, rtol=0, atol=1e-12)
     assert np.linalg.eigvalsh(S.toarray()).min() >= 1e-2 - 1e-12
+
+
+def test_diffusion3d_harmonic_faces_and_dirichlet_boundary():
+    """7-point variable-coefficient diffusion: exactly symmetric, n = m^3 and nnz = 7 m^3 - 6 m^2;
+    every off-diagonal is minus the harmonic mean 2 k_a k_b / (k_a + k_b) of the two cells'
+    conductivities; each diagonal minus its row's |off-diagonals| is the cell's own k once per
+    boundary face (6 minus its neighbours); and the matrix is SPD."""
+    m = 5
+    A = wl.diffusion3d(m, 2)
+    kap = wl.conductivity(m, 2)
+    assert kap.min() >= 1e-2 and kap.max() <= 1e2
+    assert A.n == m ** 3 and A.nnz == 7 * m ** 3 - 6 * m ** 2
+    S = A.to_scipy().tocoo()
+    D = S.toarray()
+    assert np.array_equal(D, D.T)
+    off = S.row != S.col
+    r, c, v = S.row[off], S.col[off], S.data[off]
+    assert np.allclose(-v, 2 * kap[r] * kap[c] / (kap[r] + kap[c]), rtol=1e-15, atol=0)
+    assert np.all(-v >= np.minimum(kap[r], kap[c])) and np.all(-v <= 2 * np.minimum(kap[r], kap[c]))
+    nbrs = np.bincount(r, minlength=A.n)
+    rowoff = np.bincount(r, weights=-v, minlength=A.n)
+    assert np.allclose(np.diag(D) - rowoff, (6 - nbrs) * kap, rtol=1e-13, atol=0)
+    assert np.linalg.eigvalsh(D).min() > 0
+
+
+def test_stencil27_sizes_and_symmetry():
+    for m in (1, 2, 4):
+        A = wl.stencil27(m, 0)
+        assert A.n == m ** 3 and A.nnz == (3 * m - 2) ** 3
+        D = A.to_scipy().toarray()
+        assert np.array_equal(D, D.T)
+        o = D - np.diag(np.diag(D))
+        assert np.all(o <= 0) and np.all(o >= -1)
