@@ -340,6 +340,29 @@ def test_dense4096_full_size_first_iterations_and_solution(mb, orc):
     assert relres(A, b, x) <= 1e-8
 
 
+def test_dense4096_tc_s32_full_size_first_iterations_and_solution(mb, orc):
+    """The benchmark's default configuration: dense n = 4096, kappa = 1e6, s = 32, with the product
+    and the k x k-row products on the tensor cores (MBPCG_FP64_TC) and the graph-launched loop the
+    bench times. The state after 2 iterations element-wise against the oracle, and the full
+    solve's true residual recomputed here. (Its iteration count lies past the exact-arithmetic
+    bound of 128 block steps, where the count depends on rounding order: not compared here.)"""
+    A = wl.dense_spd(4096, 0)
+    b = wl.rhs(4096, 0)
+    s = 32
+    U = wl.initial_block(4096, s, 1)
+    solver = mb.Solver(A, s=s, precision=mb.MBPCG_FP64_TC)
+    try:
+        got, st = solver.run_iterations(b, U, 2)
+        ref, st_o = orc.mbpcg_state(A, b, U, 2)
+        for key in ("Xt", "R", "W", "P", "Sigma"):
+            assert np.abs(got[key] - ref[key]).max() <= 1e-9 * np.abs(ref[key]).max(), key
+        x, info = solver.solve(b, U, tol=1e-8)
+    finally:
+        solver.close()
+    assert info["status"] == 0
+    assert relres(A, b, x) <= 1e-8
+
+
 def test_diffusion128_full_size_first_iteration_and_solution(mb, orc):
     A = wl.diffusion3d(128, 0)
     b = wl.rhs(A.n, 0)
