@@ -363,6 +363,28 @@ def test_dense4096_tc_s32_full_size_first_iterations_and_solution(mb, orc):
     assert relres(A, b, x) <= 1e-8
 
 
+def test_stencil27_96_mixed_full_size_solution(mb):
+    """The 27-point workload at full size (96^3, n = 884 736, nnz = 23 393 656) in the bench's
+    configuration: s = 16, FP32 inner solves inside FP64 refinement, tol 1e-10, graph launch.
+    An oracle solve of it takes many minutes, so it is checked through what holds at any size:
+    status 0, the true residual b - A x recomputed here within tol, and the same bits on a second
+    solve (fixed summation order)."""
+    A = wl.stencil27(96, 0)
+    assert A.n == 884_736 and A.nnz == 23_393_656
+    b = wl.rhs(A.n, 0)
+    s = 16
+    U = wl.initial_block(A.n, s, 1)
+    solver = mb.Solver(A, s=s, precision=mb.MBPCG_MIXED_FP32)
+    try:
+        x, info = solver.solve(b, U, tol=1e-10)
+        x2, _ = solver.solve(b, U, tol=1e-10)
+    finally:
+        solver.close()
+    assert info["status"] == 0, info
+    assert relres(A, b, x) <= 1e-10
+    assert np.array_equal(x, x2)
+
+
 def test_diffusion128_full_size_first_iteration_and_solution(mb, orc):
     A = wl.diffusion3d(128, 0)
     b = wl.rhs(A.n, 0)
