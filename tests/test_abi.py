@@ -110,3 +110,31 @@ def test_oracle_and_library_share_no_code():
         if os.path.isfile(f):
             txt = open(f).read()
             assert "paper_2608_07327_gb300" not in txt and "csrc" not in txt, f
+
+
+def test_no_cpu_fallback_without_a_device(libpath):
+    """Without a CUDA device the library refuses to solve instead of computing on the host:
+    mbpcg_create_csr with host arrays returns MBPCG_ERR_CUDA (3) and no handle, and the Python
+    Solver raises before any arithmetic."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import numpy as np
+
+    import workloads as wl
+    A = wl.poisson2d(4)
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+    v = np.ascontiguousarray(A.val, dtype=np.float64)
+    L = ctypes.CDLL(libpath)
+    P, I32 = ctypes.c_void_p, ctypes.c_int32
+    L.mbpcg_create_csr.restype = ctypes.c_int
+    L.mbpcg_create_csr.argtypes = [ctypes.POINTER(P), I32, ctypes.c_int64, P, P, P, I32, I32, I32, I32,
+                                   ctypes.c_uint64, I32, P, ctypes.c_size_t, P]
+    h = P(None)
+    st = L.mbpcg_create_csr(ctypes.byref(h), A.n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, v.ctypes.data, 2, 0, 0,
+                            0, 1, 0, None, 0, None)
+    assert st == 3 and not h.value
+    import paper_2608_07327_gb300 as mb
+    with pytest.raises(Exception):
+        mb.Solver(A, s=2)
