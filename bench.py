@@ -220,6 +220,36 @@ def launches_per_solve(info, dense, algo_cg, tc=False, mixed=False):
     return inner * (1 + setup + exit_) + body * info["iterations"] + (0 if algo_cg else 1)
 
 
+def roofline_tc(n, s, kp, k_ms, single_ms, seq_ms, read_gbs, peaks, traffic, launches):
+    """Roofline of k_dense_tc, the MMA kernel of the tensor-core product (k_ms: its average
+    duration over `launches` back-to-back launches). Algorithmic bytes are those of the dense
+    product itself: FP64 A read once (8 n^2), P in and A P out (16 n KP). The kernel reads A as
+    8 BF16 digits per entry instead, 16 n^2 bytes: twice the algorithmic bytes, so its digit stream
+    is reported beside the roofline (bytes, GB/s, fraction of the read-only ceiling `read_gbs`)."""
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    nbytes = 8.0 * n * n + 16.0 * n * kp
+    stream_bytes = 16.0 * n * n + 16.0 * n * kp
+    flops = 2.0 * n * n * s
+    achieved_gbs = nbytes / (k_ms * 1e-3) / 1e9
+    stream_gbs = stream_bytes / (k_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": f"k_dense_tc<{kp}> (digit stream of A + tcgen05 MMAs, the kernel alone)",
+            "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved_gbs / hbm_peak, 4), "traffic": traffic,
+            "kernel_ms": round(k_ms, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
+            "fp64_equiv_tflops": round(flops / (k_ms * 1e-3) / 1e12, 3),
+            "digit_stream_bytes": stream_bytes, "digit_stream_gbs": round(stream_gbs, 1),
+            "digit_stream_frac_of_peak": round(stream_gbs / hbm_peak, 4),
+            "digit_stream_frac_of_read_ceiling": round(stream_gbs / read_gbs, 4),
+            "traffic_note": "DRAM bytes of one launch: the digit stream (16 B per entry of A), twice the "
+                            "algorithmic bytes by design, not re-reads",
+            "timing": f"{launches} back-to-back launches (digits of A > L2, no flush)",
+            "kernel_ms_one_launch_l2_flushed": round(single_ms, 5),
+            "product_call_ms": round(seq_ms, 5),
+            "product_call_frac": round(nbytes / (seq_ms * 1e-3) / 1e9 / hbm_peak, 4),
+            "read_ceiling_gbs": round(read_gbs, 1), "frac_of_read_ceiling": round(achieved_gbs / read_gbs, 4),
+            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+
+
 def max_over_ranks(values, world, device=None):
     """Element-wise maximum of per-rank step timings over all ranks (the values as given at world
     size 1). Every rank calls it at the same point; the tensor lives on `device` (a CUDA device
@@ -348,7 +378,7 @@ def run_ours(args, world, rank, local):
         launch = lambda: mb.mbpcg_k_dense_tc_mma(n, s, tcs, tcb, stream.cuda_stream)  # noqa: E731
         kname = "k_dense_tc"
         flops = 2.0 * n * n * s
-        nbytes = 16.0 * n * n + 16.0 * n * kp  # 8 bf16 digits of A per entry, P in, AP out
+        nbytes = 8.0 * n * n + 16.0 * n * kp  # algorithmic: FP64 A read once, P in, AP out
     elif dense:
         Ad = torch.as_tensor(np.asfortranarray(A.a).ravel(order="F"), device=dev)
         launch = lambda: mb.mbpcg_k_dense_product(n, Ad, s, P, AP, stream.cuda_stream)  # noqa: E731
@@ -470,19 +500,8 @@ def run_ours(args, world, rank, local):
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
     elif tc:
         peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-        achieved_gbs = nbytes / (k_avg * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": f"{kname}<{kp}> (digit stream of A + tcgen05 MMAs, the kernel alone)",
-                    "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                    "frac": round(achieved_gbs / hbm_peak, 4), "traffic": recorded_traffic(kname, args.workload, s),
-                    "kernel_ms": round(k_avg, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
-                    "fp64_equiv_tflops": round(achieved_tflops, 3),
-                    "timing": f"{args.kernel_launches} back-to-back launches (input 268 MB > L2, no flush)",
-                    "kernel_ms_one_launch_l2_flushed": round(single_ms, 5),
-                    "product_call_ms": round(seq_ms, 5),
-                    "product_call_frac": round(nbytes / (seq_ms * 1e-3) / 1e9 / hbm_peak, 4),
-                    "read_ceiling_gbs": round(read_gbs, 1), "frac_of_read_ceiling": round(achieved_gbs / read_gbs, 4),
-                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+        roofline = roofline_tc(n, s, kp, k_avg, single_ms, seq_ms, read_gbs, peaks,
+                               recorded_traffic(kname, args.workload, s), args.kernel_launches)
     else:
         roofline = {"bound": "alu", "kernel": f"{kname}<{kp}> (FP64 pipe)", "achieved": round(achieved_tflops, 4),
                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
