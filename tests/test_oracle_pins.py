@@ -323,3 +323,82 @@ def test_state_matches_full_solve_prefix(orc):
     assert status == 0
     for name in ("Xt", "R", "W", "P", "Sigma", "X0"):
         assert np.array_equal(st[name], seen[5][name])
+
+
+# ------------------------------------------------------------------------------ breakdown
+
+
+def one_block_step(A, r, U):
+    """One step of textbook block CG from X0 = c U on A e = r, written from its closed form: with
+    R0 = r 1^T - A X0, the first block iterate is the A-orthogonal (Galerkin) correction over
+    span(R0), X1 = X0 + R0 (R0^T A R0)^{-1} R0^T R0 (Algorithm 1 reaches the same X1, since P0 spans
+    R0). c = ||r 1^T||_F / ||A U||_F as in the set-up of Algorithm 1. Returns X1 and the residual
+    norms of its columns."""
+    M = np.asarray(A.a)
+    s = U.shape[1]
+    c = np.sqrt(s) * np.linalg.norm(r) / np.linalg.norm(M @ U)
+    X0 = c * U
+    R0 = r[:, None] - M @ X0
+    X1 = X0 + R0 @ np.linalg.solve(R0.T @ M @ R0, R0.T @ R0)
+    return X1, np.linalg.norm(r[:, None] - M @ X1, axis=0)
+
+
+def breakdown_system(n=6, s=4):
+    # a well-conditioned SPD 6 x 6 with s = 4 copies: after one block step the residual block lies in
+    # the 2-dimensional A-orthogonal complement of span(R0), so V (whose column space is that of the
+    # new residual block) has rank 2 < 4 and the Cholesky QR of V meets a zero pivot: breakdown
+    A = spd_with_spectrum(n, np.linspace(1.0, 4.0, n), 11)
+    return A, wl.rhs(n, 3), wl.initial_block(n, s, 5)
+
+
+def test_breakdown_when_block_krylov_space_is_exhausted(orc):
+    """Cholesky breakdown (pivot not above 64 eps max G_jj) in the Cholesky QR of V after the first
+    iteration: status BREAKDOWN after exactly one iteration, x = the best column of the first block
+    iterate (Algorithm 1's best-basis choice h = argmin_j ||R_j||), checked against the closed form."""
+    A, b, U = breakdown_system()
+    x, c, info = orc.mbpcg(A, b, U, tol=1e-12, max_restarts=0)
+    assert info["status"] == 6 and info["iterations"] == 1, info
+    X1, res = one_block_step(A, b, U)
+    h = int(np.argmin(res))
+    assert info["best_col"] == h
+    assert np.array_equal(c, np.eye(U.shape[1])[h])
+    assert np.linalg.norm(x - X1[:, h]) <= 1e-12 * np.linalg.norm(X1[:, h])
+    assert np.isclose(info["relres_recurrence"], res[h] / np.linalg.norm(b), rtol=1e-8)
+
+
+def test_breakdown_then_restarts_follow_the_same_rule(orc):
+    """With the true-residual restarts on, each correction solve breaks down the same way and adds
+    the best column of its own first block iterate (same U, right-hand side b - A x); the solve ends
+    with status BREAKDOWN after max_restarts restarts unless the true residual reaches tol first."""
+    A, b, U = breakdown_system()
+    tol = 1e-12
+    x, c, info = orc.mbpcg(A, b, U, tol=tol, max_restarts=3)
+    M = np.asarray(A.a)
+    xr = np.zeros_like(b)
+    rounds = 0
+    while True:
+        r = b - M @ xr
+        X1, res = one_block_step(A, r, U)
+        xr = xr + X1[:, int(np.argmin(res))]
+        rounds += 1
+        if np.linalg.norm(b - M @ xr) <= tol * np.linalg.norm(b) or rounds == 4:
+            break
+    assert info["iterations"] == rounds and info["restarts"] == rounds - 1, info
+    assert info["status"] == (0 if np.linalg.norm(b - M @ xr) <= tol * np.linalg.norm(b) else 6), info
+    assert np.linalg.norm(x - xr) <= 1e-10 * np.linalg.norm(xr)
+
+
+def test_breakdown_at_setup_when_s_exceeds_n(orc):
+    """s > n: R0 (n x s) has rank n < s, so the set-up Cholesky QR breaks down before the first
+    iteration; x = c U_h, the best column of X0 (h = argmin_j ||b - c A U_j||)."""
+    A = spd_with_spectrum(3, np.array([1.0, 2.0, 3.0]), 12)
+    b = wl.rhs(3, 4)
+    U = wl.initial_block(3, 4, 6)
+    x, c, info = orc.mbpcg(A, b, U, tol=1e-12, max_restarts=0)
+    assert info["status"] == 6 and info["iterations"] == 0, info
+    M = np.asarray(A.a)
+    cs = np.sqrt(4) * np.linalg.norm(b) / np.linalg.norm(M @ U)
+    res = np.linalg.norm(b[:, None] - cs * (M @ U), axis=0)
+    h = int(np.argmin(res))
+    assert info["best_col"] == h
+    assert np.linalg.norm(x - cs * U[:, h]) <= 1e-14 * np.linalg.norm(cs * U[:, h])

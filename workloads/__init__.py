@@ -69,6 +69,15 @@ def rhs(n: int, seed: int) -> np.ndarray:
     return uniform_pm1(seed, 0, n)
 
 
+def perturbed_rhs(b: np.ndarray, k: int) -> np.ndarray:
+    """b with every entry scaled by (1 + 1e-16 u), u ~ Uniform(-1,1) from seed k, stream 7000: a
+    rounding-level change of b (about half the entries move by one ulp) used to measure how far
+    an iteration count moves under rounding alone. k = 0 is b itself."""
+    if k == 0:
+        return np.array(b, dtype=np.float64)
+    return b * (1 + 1e-16 * uniform_pm1(k, 7000, b.size))
+
+
 def initial_block(n: int, k: int, seed: int) -> np.ndarray:
     """U (n x k, column-major / Fortran order) with i.i.d. Uniform(-1,1) entries (Algorithm 1);
     column j comes from stream 1 + j."""
