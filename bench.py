@@ -263,6 +263,24 @@ def max_over_ranks(values, world, device=None):
     return t.tolist()
 
 
+def resolve_precision(args, cfg, dense):
+    """Name of the arithmetic a run uses: "tc" (dense only), "mixed" or "fp64"."""
+    pname = args.precision or cfg.get("precision", "fp64")
+    if pname == "tc" and not dense:
+        pname = "fp64"
+    return pname if pname in ("tc", "mixed") else "fp64"
+
+
+def bench_config(args, cfg, A, s, pname, world):
+    """The "config" object of the JSON line (the same for this library's arm and the reference arm)."""
+    mixed = pname == "mixed"
+    return {"workload": cfg.get("mixed_desc", cfg["desc"]) if mixed else cfg["desc"], "n": int(A.n),
+            "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
+            "tol": cfg.get("mixed_tol", cfg["tol"]) if mixed else cfg["tol"],
+            "l2": "flushed before every step (256 MB write)", "launch_mode": args.launch_mode, "precision": pname,
+            "residual": args.residual, "parallelism": "replicas only" if world > 1 else "single GPU"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2608_07327_gb300 as mb
@@ -280,13 +298,8 @@ def run_ours(args, world, rank, local):
     U = wl.initial_block(n, s, 1)
     dev = torch.device("cuda", local)
     mode = mb.MBPCG_LAUNCH_EAGER if args.launch_mode == "eager" else mb.MBPCG_LAUNCH_GRAPH
-    pname = args.precision or cfg.get("precision", "fp64")
-    if pname == "tc" and dense:
-        prec = mb.MBPCG_FP64_TC
-    elif pname == "mixed":
-        prec = mb.MBPCG_MIXED_FP32
-    else:
-        prec, pname = mb.MBPCG_FP64, "fp64"
+    pname = resolve_precision(args, cfg, dense)
+    prec = {"tc": mb.MBPCG_FP64_TC, "mixed": mb.MBPCG_MIXED_FP32}.get(pname, mb.MBPCG_FP64)
     mixed = prec == mb.MBPCG_MIXED_FP32
     # the mixed configuration of a workload may have its own tolerance (refinement to 1e-10)
     tol = cfg.get("mixed_tol", cfg["tol"]) if mixed else cfg["tol"]
@@ -530,10 +543,7 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": round(ms_per_step, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-            "config": {"workload": desc, "n": n, "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
-                       "tol": tol, "l2": "flushed before every step (256 MB write)",
-                       "launch_mode": args.launch_mode, "precision": pname, "residual": args.residual,
-                       "parallelism": "replicas only" if world > 1 else "single GPU"},
+            "config": bench_config(args, cfg, A, s, pname, world),
             "iterations": info["iterations"], "restarts": info["restarts"], "relres_true": relres_check,
             "cg_ms": round(cg_ms, 4), "cg_iterations": cg_infos[-1]["iterations"],
             "speedup_vs_cg": round(cg_ms / ms_per_step, 4),
@@ -566,15 +576,32 @@ def run_ours(args, world, rank, local):
     return line
 
 
+def host_cpu():
+    """(threads the OpenMP oracle uses, CPU model) of this host."""
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return threads, model or "unknown"
+
+
 def oracle_sample(args, A, s, precond, iters):
-    """Time `iters` oracle iterations (plus its set-up) on this host; returns seconds/iteration."""
+    """Time `iters` iterations (plus the set-up) of the oracle's OpenMP build (same source and bits
+    as the parity oracle, independent loops shared among all host cores); returns
+    (seconds per iteration, set-up seconds)."""
     import oracle
     b = wl.rhs(A.n, 0)
     U = wl.initial_block(A.n, s, 1)
     t0 = time.perf_counter()
-    oracle.mbpcg_state(A, b, U, 0, precond=precond)
+    oracle.mbpcg_state(A, b, U, 0, precond=precond, omp=True)
     t1 = time.perf_counter()
-    oracle.mbpcg_state(A, b, U, iters, precond=precond)
+    oracle.mbpcg_state(A, b, U, iters, precond=precond, omp=True)
     t2 = time.perf_counter()
     return ((t2 - t1) - (t1 - t0)) / iters, (t1 - t0)
 
@@ -590,9 +617,13 @@ def full_solve_iterations(workload, s):
 def cpu_baseline(args, A, s, precond, gpu_iterations):
     per_it, setup = oracle_sample(args, A, s, precond, args.cpu_sample_iters)
     its = full_solve_iterations(args.workload, s) or gpu_iterations
-    return {"value": round((setup + per_it * its) * 1e3, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{args.cpu_sample_iters} oracle iterations (+ set-up) timed on one host core, scaled to the "
-                      f"{its} iterations of the full solve"}
+    threads, model = host_cpu()
+    return {"value": round((setup + per_it * its) * 1e3, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "cpu_model": model, "build": "oracle source, gcc -O3 -fopenmp (independent loops over all host cores; "
+                                         "same bits as the single-thread parity build)",
+            "sample": f"{args.cpu_sample_iters} oracle iterations (+ set-up) timed on {threads} host threads, "
+                      f"extrapolated linearly to the {its} iterations of the oracle's full solve "
+                      f"(oracle/full_solve_counts.json)"}
 
 
 def run_reference(args, world, rank):
@@ -604,19 +635,28 @@ def run_reference(args, world, rank):
     its = full_solve_iterations(args.workload, s)
     if its is None:
         return {"impl": "reference", "unavailable": f"no recorded oracle iteration count for {args.workload} s={s}"}
+    pname = resolve_precision(args, cfg, isinstance(A, wl.Dense))
+    if pname == "mixed":
+        return {"impl": "reference", "unavailable": "the oracle is FP64 only; no oracle form of the mixed-precision "
+                                                    "solve exists to time"}
     per = []
+    iters = max(1, args.cpu_sample_iters // 2)
     for k in range(args.warmup + args.steps):
-        p, setup = oracle_sample(args, A, s, cfg["precond"], max(1, args.cpu_sample_iters // 2))
+        p, setup = oracle_sample(args, A, s, cfg["precond"], iters)
         if k >= args.warmup:
             per.append((setup + p * its) * 1e3)
     ms = sum(per) / len(per)
+    threads, model = host_cpu()
     return {"impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["desc"], "n": A.n, "s": s, "precond": cfg["precond"], "tol": cfg["tol"]},
-            "cpu_baseline": {"value": round(ms, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: {max(1, args.cpu_sample_iters // 2)} oracle iterations (+ set-up)"
-                                       f" on one host core, scaled to the oracle's {its}-iteration full solve"},
+            "config": bench_config(args, cfg, A, s, pname, world),
+            "cpu_baseline": {"value": round(ms, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "cpu_model": model,
+                             "sample": f"each step: {iters} iterations (+ set-up) of the oracle's OpenMP build on "
+                                       f"{threads} host threads, extrapolated linearly to the oracle's "
+                                       f"{its}-iteration full solve; the step value is that extrapolation, not "
+                                       f"time spent (a full oracle solve takes minutes)"},
             "e2e": {"value": round(ms, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -42,8 +42,9 @@ int mbpcg_k_spmm_gram(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
  * device memory left to give). Its scratch is a fixed array of about 400 KB compiled into the
  * library, which every GPU that loads the library holds until the process exits; nothing is
  * allocated or freed. Limits: s <= 16 and at most 320 CTAs of partial sums (a GB300 uses 304);
- * larger requests return MBPCG_ERR_INVALID with a message. The first call on each device looks up
- * the array's device address, so make that first call before any stream capture. All calls share
+ * larger requests return MBPCG_ERR_INVALID with a message. The first call in each CUDA context (per
+ * device, and again after a device reset) looks up the array's device address, so make that first
+ * call before any stream capture. All calls share
  * the one array: calls whose work overlaps on the GPU (e.g. on two streams) race and give wrong
  * results; serialise them. Inputs, outputs and errors are those of mbpcg_k_spmm_gram.
  */

@@ -21,8 +21,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mbpcg_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_OMP_PATH = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 STATUS = {0: "ok", 1: "invalid", 4: "not_spd", 5: "not_converged", 6: "breakdown"}
 
@@ -50,23 +51,27 @@ ITER_CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32
                            _DP, _DP, _DP, _DP, _DP, _DP)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/_build/liboracle.so (plain -O2, single thread)."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc: oracle/_build/liboracle.so (plain -O2, single thread: the parity
+    oracle), or with omp=True oracle/_build/liboracle_omp.so (-O3 -fopenmp: the same source with its
+    independent loops shared among the host cores, for the timed CPU baseline; same results bit for
+    bit)."""
+    path = _OMP_PATH if omp else _LIB_PATH
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mbpcg_oracle.h"))):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-Wextra", "-shared", "-fPIC",
+        tmp = path + f".tmp{os.getpid()}"
+        flags = ["-O3", "-fopenmp"] if omp else ["-O2"]
+        subprocess.check_call(["gcc", *flags, "-std=c99", "-Wall", "-Wextra", "-shared", "-fPIC",
                                "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
     with _lock:
-        if _lib is None:
-            path = build()
+        if omp not in _libs:
+            path = build(omp=omp)
             L = ctypes.CDLL(path)
             L.orc_matmat.argtypes = [ctypes.c_int32, _IP, _IP, _DP, _DP, ctypes.c_int32, _DP, _DP]
             L.orc_mbpcg.argtypes = [ctypes.c_int32, _IP, _IP, _DP, _DP, _DP, _DP, ctypes.c_int32,
@@ -79,8 +84,8 @@ def lib():
                                           ctypes.c_int32, ctypes.c_int32, _DP, _DP, _DP, _DP, _DP, _DP]
             for f in (L.orc_matmat, L.orc_mbpcg, L.orc_cg_cgear, L.orc_mbpcg_state):
                 f.restype = ctypes.c_int
-            _lib = L
-    return _lib
+            _libs[omp] = L
+    return _libs[omp]
 
 
 def _dp(a):
@@ -114,7 +119,7 @@ def matmat(A, X: np.ndarray) -> np.ndarray:
 
 
 def mbpcg(A, b, U, precond: int = 0, tol: float = 1e-8, maxit: int = 100000, max_restarts: int = 3,
-          callback=None):
+          callback=None, omp: bool = False):
     """Algorithm 1 solve. Returns (x, c, info_dict). callback(iter, exiting, restart, state_dict)
     receives copies of X0, Xt, R, W, P (n x k) and Sigma (k x k) of the scaled system."""
     (n, rp, ci, v, dn), keep = _mat_args(A)
@@ -134,23 +139,24 @@ def mbpcg(A, b, U, precond: int = 0, tol: float = 1e-8, maxit: int = 100000, max
         cb = ITER_CB(_cb)
     else:
         cb = ITER_CB()
-    lib().orc_mbpcg(n, _ip(rp), _ip(ci), _dp(v), _dp(dn), _dp(b), _dp(U), k, precond, tol, maxit,
+    lib(omp).orc_mbpcg(n, _ip(rp), _ip(ci), _dp(v), _dp(dn), _dp(b), _dp(U), k, precond, tol, maxit,
                     max_restarts, _dp(x), _dp(c), ctypes.byref(info), cb, None)
     return x, c, info.as_dict()
 
 
-def cg_cgear(A, b, precond: int = 0, tol: float = 1e-8, maxit: int = 100000, max_restarts: int = 3):
+def cg_cgear(A, b, precond: int = 0, tol: float = 1e-8, maxit: int = 100000, max_restarts: int = 3,
+             omp: bool = False):
     """Chronopoulos-Gear CG from x0 = 0. Returns (x, info_dict)."""
     (n, rp, ci, v, dn), keep = _mat_args(A)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(n)
     info = OrcInfo()
-    lib().orc_cg_cgear(n, _ip(rp), _ip(ci), _dp(v), _dp(dn), _dp(b), precond, tol, maxit, max_restarts,
+    lib(omp).orc_cg_cgear(n, _ip(rp), _ip(ci), _dp(v), _dp(dn), _dp(b), precond, tol, maxit, max_restarts,
                        _dp(x), ctypes.byref(info))
     return x, info.as_dict()
 
 
-def mbpcg_state(A, b, U, iters: int, precond: int = 0):
+def mbpcg_state(A, b, U, iters: int, precond: int = 0, omp: bool = False):
     """Raw state after exactly `iters` iterations: dict(X0, Xt, R, W, P, Sigma) and the status."""
     (n, rp, ci, v, dn), keep = _mat_args(A)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -158,7 +164,7 @@ def mbpcg_state(A, b, U, iters: int, precond: int = 0):
     k = U.shape[1]
     out = {name: np.zeros((n, k), order="F") for name in ("X0", "Xt", "R", "W", "P")}
     out["Sigma"] = np.zeros((k, k), order="F")
-    st = lib().orc_mbpcg_state(n, _ip(rp), _ip(ci), _dp(v), _dp(dn), _dp(b), _dp(U), k, precond, iters,
+    st = lib(omp).orc_mbpcg_state(n, _ip(rp), _ip(ci), _dp(v), _dp(dn), _dp(b), _dp(U), k, precond, iters,
                                _dp(out["X0"]), _dp(out["Xt"]), _dp(out["R"]), _dp(out["W"]), _dp(out["P"]),
                                _dp(out["Sigma"]))
     return out, st

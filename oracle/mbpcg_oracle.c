@@ -14,6 +14,18 @@
 
 enum { ORC_OK = 0, ORC_INVALID = 1, ORC_NOT_SPD = 4, ORC_NOT_CONVERGED = 5, ORC_BREAKDOWN = 6 };
 
+/* Loops whose iterations are independent (one column, row or entry each, every sum inside one
+ * iteration in its sequential order) are marked ORC_PAR. The parity build compiles without OpenMP
+ * and ignores the mark; the timed CPU-baseline build (-fopenmp) shares those iterations among the
+ * host cores, which changes no sum's order and so gives the same bits. */
+#ifdef _OPENMP
+#define ORC_PAR _Pragma("omp parallel for schedule(static)")
+#define ORC_PAR2 _Pragma("omp parallel for collapse(2) schedule(static)")
+#else
+#define ORC_PAR
+#define ORC_PAR2
+#endif
+
 typedef struct {
   int32_t n;
   const int32_t* row_ptr;
@@ -27,6 +39,7 @@ typedef struct {
 /* Y = A X, X and Y column-major n*k. Dense A is walked column by column (axpy form). */
 static void mat_block(const orc_mat* A, int32_t k, const double* X, double* Y) {
   const int32_t n = A->n;
+  ORC_PAR
   for (int32_t j = 0; j < k; ++j) {
     const double* x = X + (size_t)j * n;
     double* y = Y + (size_t)j * n;
@@ -55,12 +68,14 @@ static double dot(int32_t n, const double* a, const double* b) {
 
 /* C (m*k) = A^T B for column-major A (n*m), B (n*k). */
 static void gram(int32_t n, int32_t m, int32_t k, const double* A, const double* B, double* C) {
+  ORC_PAR2
   for (int32_t a = 0; a < m; ++a)
     for (int32_t c = 0; c < k; ++c) C[a + (size_t)c * m] = dot(n, A + (size_t)a * n, B + (size_t)c * n);
 }
 
 /* C (n*k) = A (n*k) S (k*k); C must not alias A. */
 static void block_times_small(int32_t n, int32_t k, const double* A, const double* S, double* C) {
+  ORC_PAR
   for (int32_t j = 0; j < k; ++j)
     for (int32_t i = 0; i < n; ++i) {
       double s = 0.0;
@@ -124,6 +139,7 @@ static void spd_inverse_from_chol(int32_t k, const double* Z, double* Ginv) {
 
 /* W = V Z^{-1} for an upper triangular Z: each row w solves w Z = v. */
 static void right_solve_upper(int32_t n, int32_t k, const double* V, const double* Z, double* W) {
+  ORC_PAR
   for (int32_t i = 0; i < n; ++i)
     for (int32_t j = 0; j < k; ++j) {
       double s = V[i + (size_t)j * n];
@@ -303,11 +319,14 @@ static void mbpcg_core(const orc_mat* As, const double* d, const double* rhs, co
     small_times_small(k, Xi, Sigma, T); /* T = Xi Sigma */
     /* X~ = X~ + P Xi Sigma;  R = R - A P Xi Sigma */
     block_times_small(n, k, P, T, Tmp);
+    ORC_PAR
     for (size_t q = 0; q < nk; ++q) Xt[q] += Tmp[q];
     block_times_small(n, k, Q, T, Tmp);
+    ORC_PAR
     for (size_t q = 0; q < nk; ++q) R[q] -= Tmp[q];
     if (force_iters < 0) {
       /* h = argmin_j ||R_j|| / ||b||, measured on the original-system residual D R (Section 1) */
+      ORC_PAR
       for (int32_t j = 0; j < k; ++j) {
         double s = 0.0;
         for (int32_t i = 0; i < n; ++i) {
@@ -357,9 +376,11 @@ static void mbpcg_core(const orc_mat* As, const double* d, const double* rhs, co
     }
     /* W, zeta = qr(W - A P Xi);  P = W + P zeta^T;  Sigma = zeta Sigma */
     block_times_small(n, k, Q, Xi, Tmp);
+    ORC_PAR
     for (size_t q = 0; q < nk; ++q) V[q] = W[q] - Tmp[q];
     st = cholesky_qr(n, k, V, W, Z);
     if (st != ORC_OK) break;
+    ORC_PAR
     for (int32_t j = 0; j < k; ++j)
       for (int32_t i = 0; i < n; ++i) {
         double s = W[i + (size_t)j * n];

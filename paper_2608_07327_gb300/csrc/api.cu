@@ -50,6 +50,7 @@ struct Dims {
   long long nnz;
   int dense, algo, tc, sms;
   int mixed;  // MBPCG_MIXED_FP32: FP32 blocks and values in the inner solve
+  int cg_fused;  // dense CG in one launch per iteration (k_cg_dense_iter)
 };
 
 int num_sms() {
@@ -80,6 +81,7 @@ Dims make_dims(int n, long long nnz, int s, int algo, int dense, int sms) {
   d.tc = 0;
   d.mixed = 0;
   d.sms = sm;
+  d.cg_fused = (dense && algo == MBPCG_ALGO_CG && cg_dense_fused_ok(n)) ? 1 : 0;
   return d;
 }
 
@@ -101,6 +103,7 @@ struct Layout {
   size_t rp, ci, av, A, diag, d, sqd, b, rhs, bs, x;
   size_t U, X0, Xt, R, W, P, Q, V;    // MBPCG blocks, n x KP each
   size_t r, w, xb, p, sv;             // CG vectors
+  size_t r2, w2, sv2, cnt;            // dense CG in one launch: second copies of r, w, s; arrival counter
   size_t part, red, small, st, flag;  // reductions, k x k matrices, control block
   size_t oz_a, oz_ea, oz_p, oz_ep, oz_q; // tensor-core product: digits of A and P, exponents, split sums
   size_t av32, wd32;                     // mixed precision: FP32 copies of the scaled values and of diag A
@@ -163,6 +166,12 @@ Layout make_layout(const Dims& dm) {
     L.xb = take(n * sizeof(double));
     L.p = take(n * sizeof(double));
     L.sv = take(n * sizeof(double));
+    if (dm.cg_fused) {
+      L.r2 = take(n * sizeof(double));
+      L.w2 = take(n * sizeof(double));
+      L.sv2 = take(n * sizeof(double));
+      L.cnt = take(sizeof(unsigned int));
+    }
   }
   if (dm.tc) {
     L.oz_a = take(oz_a_tiles_bytes(dm.n));
@@ -197,6 +206,8 @@ struct mbpcg_ctx {
   double *av, *A, *diag, *d, *sqd, *wdiag, *b, *rhs, *bs, *x, *xbest;
   double *U, *X0, *Xt, *R, *W, *P, *Q, *V;
   double *r, *w, *xb, *p, *sv;
+  double *r2, *w2, *sv2;
+  unsigned int* cg_cnt;
   double *part, *red;
   double *Sigma, *SigmaInv, *Xi, *T, *Zeta, *ZetaInv, *c, *Gtmp;
   SolveState* st;
@@ -264,6 +275,12 @@ void bind(mbpcg_ctx* h) {
     h->xb = at<double>(h, L.xb);
     h->p = at<double>(h, L.p);
     h->sv = at<double>(h, L.sv);
+    if (h->dm.cg_fused) {
+      h->r2 = at<double>(h, L.r2);
+      h->w2 = at<double>(h, L.w2);
+      h->sv2 = at<double>(h, L.sv2);
+      h->cg_cnt = at<unsigned int>(h, L.cnt);
+    }
   }
   h->part = at<double>(h, L.part);
   h->red = at<double>(h, L.red);
@@ -455,6 +472,7 @@ int finish_create(mbpcg_ctx* h) {
       if (rc) return rc;
     }
   }
+  if (h->dm.cg_fused) CUDA_TRY(cg_dense_configure(n, h->dm.nb_dense));
   if (h->dm.tc) {
     oz_prepare_a(h->stream, n, h->A, h->oz_ea, h->oz_a);
     CUDA_TRY(cudaMemsetAsync(h->oz_p, 0, oz_p_chunks_bytes(n, h->dm.kp), h->stream));
@@ -608,12 +626,22 @@ void enqueue_mbpcg_exit_f(mbpcg_ctx* h) {
 void enqueue_cg_setup(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   k_cg_init<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->rhs, h->d, h->r, h->xb, h->p, h->sv, h->part, dm.pstride);
+  if (dm.cg_fused) {  // s_{-1} = 0 in the second copy; the arrival counter starts at zero
+    cudaMemsetAsync(h->sv2, 0, (size_t)dm.n * sizeof(double), h->stream);
+    cudaMemsetAsync(h->cg_cnt, 0, sizeof(unsigned int), h->stream);
+  }
   enqueue_reduce(h, 1, nullptr);
   k_small_cg_setup<<<1, 1, 0, h->stream>>>(h->st, h->red);
 }
 
 void enqueue_cg_body(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
+  if (dm.cg_fused) {
+    const CgVectors v = {{h->r, h->r2}, {h->w, h->w2}, {h->sv, h->sv2}, h->p, h->xb};
+    launch_cg_dense_iter(h->stream, dm.nb_dense, dm.n, h->A, v, h->wdiag, h->part, dm.pstride, h->cg_cnt, h->st,
+                         h->cond, h->use_cond);
+    return;
+  }
   const RowOps* ops = row_ops(1);
   enqueue_product(h, ops, h->r, h->w, 0, h->st);  // w = A u, u = r
   k_cg_dots<<<dm.nb, kThreads, 0, h->stream>>>(dm.n, h->r, h->w, h->wdiag, h->part, dm.pstride, h->st);

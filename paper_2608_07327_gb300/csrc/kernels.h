@@ -144,6 +144,24 @@ __global__ void k_cg_update(int n, double* r, const double* w, double* x, double
                             const SolveState* st);
 __global__ void k_cg_finish(int n, const double* xbar, const double* d, double* x);
 
+// Chronopoulos-Gear CG on a dense A, one launch per iteration (cg_dense.cu). r, w and s in two
+// copies (by the parity of the iteration), p and x in one; counter: one zeroed unsigned int.
+constexpr int kCgDenseMaxN = 16384;  // the whole vector r_j lives in each CTA's shared memory
+struct CgVectors {
+  double* r[2];
+  double* w[2];
+  double* s[2];
+  double* p;
+  double* x;
+};
+bool cg_dense_fused_ok(int n);  // n even and at most kCgDenseMaxN
+__host__ __device__ int cg_dense_fragments(int n, int nb);
+size_t cg_dense_smem_bytes(int n, int nb);
+cudaError_t cg_dense_configure(int n, int nb);
+void launch_cg_dense_iter(cudaStream_t s, int nb, int n, const double* A, const CgVectors& v, const double* wdiag,
+                          double* part, int pstride, unsigned int* counter, SolveState* st,
+                          cudaGraphConditionalHandle cond, int use_cond);
+
 // FP32 dense product of the mixed-precision inner solve (dense_f32.cu): Q = A P with A in the FP32
 // tiles k_dense_to_f32_tiles writes (dense_f32_tiles_bytes(n) bytes), P and Q row-major n x kp;
 // st may be NULL.

@@ -8,8 +8,13 @@
 // keeps that scratch in a fixed array compiled into the library instead.
 //
 // The array below is a host-side stand-in in host code, not a device address. Its device address is
-// looked up once per device (cudaGetSymbolAddress, with that device current) on the first call
-// from that device and cached; only that address is passed to kernels.
+// looked up (cudaGetSymbolAddress, with the caller's device current) on the first call in each CUDA
+// context and cached under that context's unique id (cuCtxGetId, reached through the runtime's
+// driver entry-point query, so the library does not link libcuda). A device reset creates a new
+// context with a new id, so the next call looks the address up again; only looked-up addresses are
+// passed to kernels.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "../../include/mbpcg.h"
@@ -28,28 +33,67 @@ constexpr size_t kScratchDoubles = (size_t)(kMaxCtas + 1) * kSlot;
 
 static __device__ __align__(256) double g_spmm_gram_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
+typedef CUresult(CUDAAPI* PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult(CUDAAPI* PfnCtxGetId)(CUcontext, unsigned long long*);
 
-// Device address of the static scratch on the current device (set up on first use).
+constexpr int kCacheSlots = 64;
+struct CacheEntry {
+  unsigned long long ctx_id;
+  double* addr;
+};
+std::mutex g_mutex;
+CacheEntry g_cache[kCacheSlots] = {};
+int g_cache_next = 0;
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+
+// Unique id of the current context (0 when none can be had).
+unsigned long long current_context_id() {
+  if (g_ctx_get_current == nullptr || g_ctx_get_id == nullptr) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+    g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f2);
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the static scratch in the current context (looked up on first use there).
 int scratch_address(double** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return mbpcg::set_last_error(MBPCG_ERR_CUDA, "mbpcg_k_spmm_gram_noalloc: no usable current device");
   }
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (g_scratch_addr[dev] == nullptr) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_spmm_gram_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return mbpcg::set_last_error(MBPCG_ERR_CUDA, "mbpcg_k_spmm_gram_noalloc: cudaGetSymbolAddress failed");
+  unsigned long long id = current_context_id();  // 0 before the runtime has made a context current
+  for (int q = 0; id != 0 && q < kCacheSlots; ++q) {
+    if (g_cache[q].ctx_id == id && g_cache[q].addr != nullptr) {
+      *out = g_cache[q].addr;
+      return MBPCG_OK;
     }
-    g_scratch_addr[dev] = static_cast<double*>(p);
   }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_spmm_gram_scratch);  // makes the context current if needed
+  if (e != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return mbpcg::set_last_error(MBPCG_ERR_CUDA, "mbpcg_k_spmm_gram_noalloc: cudaGetSymbolAddress failed");
+  }
+  if (id == 0) id = current_context_id();
+  if (id == 0) return mbpcg::set_last_error(MBPCG_ERR_CUDA, "mbpcg_k_spmm_gram_noalloc: no current CUDA context");
+  g_cache[g_cache_next] = {id, static_cast<double*>(p)};
+  g_cache_next = (g_cache_next + 1) % kCacheSlots;
+  *out = static_cast<double*>(p);
   return MBPCG_OK;
 }
 

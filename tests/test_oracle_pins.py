@@ -402,3 +402,23 @@ def test_breakdown_at_setup_when_s_exceeds_n(orc):
     h = int(np.argmin(res))
     assert info["best_col"] == h
     assert np.linalg.norm(x - cs * U[:, h]) <= 1e-14 * np.linalg.norm(cs * U[:, h])
+
+
+# ------------------------------------------------------------------------------ OpenMP build
+
+
+@pytest.mark.parametrize("dense", [True, False])
+def test_openmp_build_gives_the_same_bits(orc, dense):
+    """The timed CPU baseline runs the same oracle source built with OpenMP: it only shares
+    independent loop iterations among threads, so solution, coefficients and counts are the
+    parity build's, bit for bit."""
+    A = wl.dense_spd(96, 2, 0.0, 3.0) if dense else wl.poisson2d(12)
+    b = wl.rhs(A.n, 0)
+    U = wl.initial_block(A.n, 8, 1)
+    x1, c1, i1 = orc.mbpcg(A, b, U, tol=1e-10)
+    x2, c2, i2 = orc.mbpcg(A, b, U, tol=1e-10, omp=True)
+    assert np.array_equal(x1, x2) and np.array_equal(c1, c2) and i1 == i2
+    s1, _ = orc.mbpcg_state(A, b, U, 4)
+    s2, _ = orc.mbpcg_state(A, b, U, 4, omp=True)
+    for key in s1:
+        assert np.array_equal(s1[key], s2[key]), key
