@@ -43,6 +43,7 @@ constexpr size_t kAlign = 256;
 constexpr int kMixedRestarts = 12;       // refinement steps of the mixed-precision solve
 constexpr int kTuneVariants = 6;         // FP32 A P launch shapes tried by the autotuner
 constexpr double kMixedInnerTol = 1e-5;  // smallest relative tolerance asked of an FP32 inner solve
+constexpr int kBodyUnroll = 4;           // loop iterations per pass of the graph's WHILE node
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Dims {
@@ -51,6 +52,7 @@ struct Dims {
   int dense, algo, tc, sms;
   int mixed;  // MBPCG_MIXED_FP32: FP32 blocks and values in the inner solve
   int cg_fused;  // dense CG in one launch per iteration (k_cg_dense_iter)
+  int nb_cg;     // its CTAs (a multiple of the cluster size)
 };
 
 int num_sms() {
@@ -82,6 +84,8 @@ Dims make_dims(int n, long long nnz, int s, int algo, int dense, int sms) {
   d.mixed = 0;
   d.sms = sm;
   d.cg_fused = (dense && algo == MBPCG_ALGO_CG && cg_dense_fused_ok(n)) ? 1 : 0;
+  d.nb_cg = d.cg_fused ? cg_dense_grid(n, sm) : 0;
+  if (d.nb_cg > d.nbmax) d.nbmax = d.nb_cg;
   return d;
 }
 
@@ -177,8 +181,9 @@ Layout make_layout(const Dims& dm) {
     L.oz_a = take(oz_a_tiles_bytes(dm.n));
     L.oz_ea = take(n * sizeof(int));
     L.oz_p = take(oz_p_chunks_bytes(dm.n, dm.kp));
-    L.oz_ep = take(kMaxKP * sizeof(int));
-    L.oz_q = take((size_t)oz_ksplit(dm.n, dm.sms) * n * dm.kp * sizeof(double));
+    L.oz_ep = take(2 * kMaxKP * sizeof(int));  // the column exponents of P and the product's copy of them
+    // raw partial sums of the product's slices: int64 and FP32 per entry
+    L.oz_q = take((size_t)oz_ksplit(dm.n, dm.sms) * n * dm.kp * (sizeof(long long) + sizeof(float)));
     if (dm_uses_rowprod(dm)) L.rp3 = take(3 * n * dm.kp * sizeof(double));
   }
   L.part = take((size_t)dm.nbmax * dm.pstride * sizeof(double));
@@ -472,7 +477,7 @@ int finish_create(mbpcg_ctx* h) {
       if (rc) return rc;
     }
   }
-  if (h->dm.cg_fused) CUDA_TRY(cg_dense_configure(n, h->dm.nb_dense));
+  if (h->dm.cg_fused) CUDA_TRY(cg_dense_configure(n, h->dm.nb_cg));
   if (h->dm.tc) {
     oz_prepare_a(h->stream, n, h->A, h->oz_ea, h->oz_a);
     CUDA_TRY(cudaMemsetAsync(h->oz_p, 0, oz_p_chunks_bytes(n, h->dm.kp), h->stream));
@@ -638,7 +643,7 @@ void enqueue_cg_body(mbpcg_ctx* h) {
   const Dims& dm = h->dm;
   if (dm.cg_fused) {
     const CgVectors v = {{h->r, h->r2}, {h->w, h->w2}, {h->sv, h->sv2}, h->p, h->xb};
-    launch_cg_dense_iter(h->stream, dm.nb_dense, dm.n, h->A, v, h->wdiag, h->part, dm.pstride, h->cg_cnt, h->st,
+    launch_cg_dense_iter(h->stream, dm.nb_cg, dm.n, h->A, v, h->wdiag, h->part, dm.pstride, h->cg_cnt, h->st,
                          h->cond, h->use_cond);
     return;
   }
@@ -697,10 +702,15 @@ int build_graph(mbpcg_ctx* h) {
     if (e == cudaSuccess) {
       e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
+        // kBodyUnroll iterations per pass of the WHILE node: a pass costs ~3 us of its own on
+        // this GPU, on top of ~1 us per kernel; every loop kernel returns at once after the
+        // iteration in which the solve stopped, and the last one of a pass sets the condition
         h->use_cond = 1;
-        if (cg) enqueue_cg_body(h);
-        else if (h->dm.mixed) enqueue_mbpcg_body_f(h);
-        else enqueue_mbpcg_body(h);
+        for (int u = 0; u < kBodyUnroll; ++u) {
+          if (cg) enqueue_cg_body(h);
+          else if (h->dm.mixed) enqueue_mbpcg_body_f(h);
+          else enqueue_mbpcg_body(h);
+        }
         h->use_cond = 0;
         cudaGraph_t b2 = nullptr;
         e = cudaStreamEndCapture(h->stream, &b2);
@@ -1184,7 +1194,8 @@ size_t mbpcg_k_dense_tc_scratch_bytes(int32_t n, int32_t s) {
   if (n < 1 || s < 1 || s > 32) return 0;
   const int kp = padded_width(s), sms = num_sms() > 0 ? num_sms() : 1;
   return align_up(oz_a_tiles_bytes(n)) + align_up((size_t)n * sizeof(int)) + align_up(oz_p_chunks_bytes(n, kp)) +
-         align_up(kMaxKP * sizeof(int)) + align_up((size_t)oz_ksplit(n, sms) * n * kp * sizeof(double));
+         align_up(2 * kMaxKP * sizeof(int)) +
+         align_up((size_t)oz_ksplit(n, sms) * n * kp * (sizeof(long long) + sizeof(float)));
 }
 
 namespace {
@@ -1205,7 +1216,7 @@ TcScratch tc_scratch(void* scratch, int n, int kp) {
   t.pc = p;
   p += align_up(oz_p_chunks_bytes(n, kp));
   t.ep = reinterpret_cast<int*>(p);
-  p += align_up(kMaxKP * sizeof(int));
+  p += align_up(2 * kMaxKP * sizeof(int));
   t.qp = reinterpret_cast<double*>(p);
   return t;
 }

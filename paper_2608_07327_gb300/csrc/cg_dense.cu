@@ -39,7 +39,7 @@ constexpr int kCgThreads = 512;
 constexpr int kCgWarps = kCgThreads / 32;
 constexpr int kSegD2 = 8;              // double2 loads per lane per item
 constexpr int kSegCols = 64 * kSegD2;  // 512 columns per item
-constexpr int kBatch = 8;              // items per transposed warp reduction
+constexpr int kBatch = 8;              // row fragments per transposed warp reduction
 
 __device__ __forceinline__ double2 ld_stream(const double* p, uint64_t pol) {
   double2 v;
@@ -123,37 +123,26 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
   double2 bufA[kSegD2], bufB[kSegD2];
   if (c0 < c1) load_chunk(A, n, r0, cpr, c0, lane, pol, bufA);
 
-  // 1. updates of iteration j-1; u = r_j (double2 loads, four in flight per array and thread)
+  // 1. updates of iteration j-1; u = r_j (every CTA forms the whole vector: sharing the work
+  // across a cluster costs more than it saves, since clusters of one CTA per SM do not all fit on
+  // the GPU at once)
   const int n2 = n / 2;
   if (it == 0) {
     const double2* rv = reinterpret_cast<const double2*>(v.r[0]);
-    for (int q = tid; q < n2; q += kCgThreads) reinterpret_cast<double2*>(u)[q] = __ldcg(rv + q);
+    for (int e = tid; e < n2; e += kCgThreads) reinterpret_cast<double2*>(u)[e] = __ldcg(rv + e);
   } else {
     const double alpha = st->cg_alpha, beta = st->cg_beta;
     const double* ro = v.r[par ^ 1];
     const double* wo = v.w[par ^ 1];
     const double* so = v.s[par];
-    for (int q0 = tid; q0 < n2; q0 += 4 * kCgThreads) {
-      double2 rr[4], ww[4], ss[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int q = q0 + k * kCgThreads;
-        if (q < n2) {
-          rr[k] = __ldcg(reinterpret_cast<const double2*>(ro) + q);
-          ww[k] = __ldcg(reinterpret_cast<const double2*>(wo) + q);
-          ss[k] = __ldcg(reinterpret_cast<const double2*>(so) + q);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int q = q0 + k * kCgThreads;
-        if (q < n2) {
-          double2 r2;
-          r2.x = fma(-alpha, fma(beta, ss[k].x, ww[k].x), rr[k].x);
-          r2.y = fma(-alpha, fma(beta, ss[k].y, ww[k].y), rr[k].y);
-          reinterpret_cast<double2*>(u)[q] = r2;
-        }
-      }
+    for (int e = tid; e < n2; e += kCgThreads) {
+      const double2 rr = __ldcg(reinterpret_cast<const double2*>(ro) + e);
+      const double2 ww = __ldcg(reinterpret_cast<const double2*>(wo) + e);
+      const double2 ss = __ldcg(reinterpret_cast<const double2*>(so) + e);
+      double2 r2;
+      r2.x = fma(-alpha, fma(beta, ss.x, ww.x), rr.x);
+      r2.y = fma(-alpha, fma(beta, ss.y, ww.y), rr.y);
+      reinterpret_cast<double2*>(u)[e] = r2;
     }
     // own rows: p, s, x and r of iteration j (the same expressions as u above, so the same bits)
     double* rn = v.r[par];
@@ -227,21 +216,25 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
     dl = fma(w, ri, dl);
     nu = (wdiag != nullptr) ? fma(ri * wdiag[row], ri, nu) : fma(ri, ri, nu);
   }
+  // (FP64 instructions hold the unit for a whole warp slot: only warps that own rows reduce)
+  const int rwarps = min(kCgWarps, (r1 - r0 + 31) / 32);
+  if (warp < rwarps) {
 #pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    g += __shfl_xor_sync(0xffffffffu, g, off);
-    dl += __shfl_xor_sync(0xffffffffu, dl, off);
-    nu += __shfl_xor_sync(0xffffffffu, nu, off);
-  }
-  if (lane == 0) {
-    red[3 * warp] = g;
-    red[3 * warp + 1] = dl;
-    red[3 * warp + 2] = nu;
+    for (int off = 16; off; off >>= 1) {
+      g += __shfl_xor_sync(0xffffffffu, g, off);
+      dl += __shfl_xor_sync(0xffffffffu, dl, off);
+      nu += __shfl_xor_sync(0xffffffffu, nu, off);
+    }
+    if (lane == 0) {
+      red[3 * warp] = g;
+      red[3 * warp + 1] = dl;
+      red[3 * warp + 2] = nu;
+    }
   }
   __syncthreads();
   if (tid < 3) {
     double a = 0.0;
-    for (int w = 0; w < kCgWarps; ++w) a += red[3 * w + tid];
+    for (int w = 0; w < rwarps; ++w) a += red[3 * w + tid];
     part[(size_t)blockIdx.x * pstride + tid] = a;
   }
   __syncthreads();
@@ -304,6 +297,8 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
 }
 
 bool cg_dense_fused_ok(int n) { return n >= 2 && (n % 2) == 0 && n <= kCgDenseMaxN; }
+
+int cg_dense_grid(int n, int sms) { return max(1, min(sms > 0 ? sms : 1, (n + 7) / 8)); }
 
 size_t cg_dense_smem_bytes(int n, int nb) {
   return ((size_t)((n + 1) & ~1) + (size_t)kCgWarps * cg_dense_fragments(n, nb)) * sizeof(double);

@@ -155,6 +155,7 @@ struct CgVectors {
   double* x;
 };
 bool cg_dense_fused_ok(int n);  // n even and at most kCgDenseMaxN
+int cg_dense_grid(int n, int sms);  // CTAs of the fused launch (one per SM)
 __host__ __device__ int cg_dense_fragments(int n, int nb);
 size_t cg_dense_smem_bytes(int n, int nb);
 cudaError_t cg_dense_configure(int n, int nb);

@@ -1,4 +1,4 @@
-// FP64-accurate dense product Q = A P on the BF16 tensor cores (tcgen05), by exact splitting
+// FP64-accurate dense product Q = A P on the FP16 tensor cores (tcgen05), by exact splitting
 // (Ozaki et al., "Error-free transformations of matrix multiplication by using fast routines of
 // matrix multiplication and its applications", Numer. Algorithms 2012).
 //
@@ -6,7 +6,7 @@
 // largest binary exponent in the row, and the magnitude of every entry is written as 8 base-128
 // digits taken straight from its 53-bit significand (integer shifts, truncation below 2^-56 of the
 // row scale). Columns of P are split the same way with their own scales G_j. A digit is an integer
-// in [-127, 127], exact in BF16. Then
+// in [-127, 127], exact in FP16. Then
 //     (A P)_ij = 2^(F_i + G_j) * sum_{L=2..16} 2^(-7L) * S_L,   S_L = sum_{t+u=L} sum_l a^t_il b^u_lj
 // and the terms with t + u > 9 are below 2^-56 of the row/column scales and are dropped.
 //
@@ -17,13 +17,17 @@
 // The result has the accuracy of an FP64 product (error ~2^-53 |A||P|; an FP64 GEMM's bound is
 // n 2^-53 |A||P|).
 //
-// Data movement. Digits are stored in global memory already in the tensor-core operand layout
-// (K-major, no swizzle, 128 x 64 tiles of 16 KB for A, 8*KPT x 64 tiles for P), so whole tiles move
-// with 1-D TMA bulk copies into shared memory: the digits of one (M tile, chunk) are adjacent, and
-// one copy brings kOzDPS of them into a stage (5 stages of 32 KB, 2 P buffers). Fewer, larger
-// stages matter: each stage hand-off is a round trip through two mbarriers and two threads. The MMA for digit t of A
-// uses all needed digits of P at once (N = KPT * (9 - t)), writing levels t+1..9 of the
-// accumulator. Producer, MMA issuer and drain run in separate warps; every wait is bounded.
+// Data movement. The digits of A are made once per matrix and stored as bytes (digit + 128), 8 bytes
+// per entry of A -- as many as A itself in FP64 -- in blocks of 128 rows x 32 values of l (32 KB)
+// that one 1-D TMA bulk copy moves into shared memory. Converter warps turn each block into the
+// FP16 operand of the tensor cores and write it to tensor memory (tcgen05.st), where the MMA reads
+// A from (the A-in-TMEM form of tcgen05.mma); the digits of P come from shared memory (canonical
+// K-major tiles, 8*KPT x 64 per chunk of l, made by k_oz_slice_p every product). The MMA for digit
+// t of A uses all needed digits of P at once (N = KPT * (8 - t)), writing levels t..7 of the
+// accumulator. Producer, converters, MMA issuer and drain run in separate warps; every wait is
+// bounded.
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 #include "ozaki_digits.cuh"
 #include "tcgen05.cuh"
@@ -33,15 +37,14 @@ namespace mbpcg {
 namespace {
 
 constexpr int kOzMT = 128;                             // rows per M tile (= TMEM lanes)
-constexpr int kOzKC = 64;                              // reduction index per chunk
+constexpr int kOzKC = 64;                              // reduction index per chunk (P digits)
 constexpr int kOzWin = 2;                              // chunks per exact window (128 values of l)
-constexpr uint32_t kATileBytes = kOzMT * kOzKC * 2;    // 16 KB: one digit of one (M tile, chunk)
-constexpr int kOzDPS = 2;                              // A digits per shared-memory stage
-constexpr int kOzAStages = 5;                          // stages of kOzDPS digits (32 KB each)
-constexpr int kOzPBufs = 2;
-constexpr uint32_t kAStageBytes = kOzDPS * kATileBytes;
-constexpr int kOzStagesPerChunk = kOzDigits / kOzDPS;
-static_assert(kOzDigits % kOzDPS == 0, "a stage holds whole digits of one chunk");
+constexpr int kOzSetK = 32;                            // reduction index per block of A digits
+constexpr int kOzSetsPerChunk = kOzKC / kOzSetK;
+constexpr uint32_t kASetBytes = kOzMT * kOzSetK * kOzDigits;  // 32 KB: 128 rows x 32 l x 8 digit bytes
+constexpr int kOzAStages = 3;                          // A blocks in flight (shared memory)
+constexpr int kOzPBufs = 3;                            // P digit chunks in flight
+constexpr uint32_t kAColsPerSet = kOzDigits * kOzSetK / 2;  // TMEM columns of one converted block (128)
 
 }  // namespace
 
@@ -56,18 +59,27 @@ __global__ void k_oz_rowexp(int n, const double* __restrict__ A, int* __restrict
   if (lane == 0) emax[warp] = m;
 }
 
-// Digits of A into tiles [mtile][kchunk][digit] of 128 x 64 bf16 (canonical K-major layout).
-__global__ void k_oz_slice_a(int n, int nK, const double* __restrict__ A, const int* __restrict__ emax,
-                             uint16_t* __restrict__ tiles) {
+// Byte offset of digit t of (row r, value k of l) inside a block of A digits: row r owns 256
+// bytes, 16-byte slot 2t + k/16 of them holding k = 16 (slot % 2) .. +15 of digit t; the slot is
+// stored at position slot ^ (r % 8), so that the 32 rows a converter warp reads at once fall on
+// different shared-memory banks.
+__host__ __device__ inline uint32_t oz_a8_offset(int r, int k, int t) {
+  const int slot = 2 * t + (k >> 4);
+  return (uint32_t)(r * 256 + ((slot ^ (r & 7)) << 4) + (k & 15));
+}
+
+// Digits of A as bytes (digit + 128) into blocks [mtile][set][row][256 bytes] (see oz_a8_offset).
+// The blocks are preset to 128 (digit 0) so that rows and values of l past n contribute nothing.
+__global__ void k_oz_slice_a8(int n, int nS, const double* __restrict__ A, const int* __restrict__ emax,
+                              uint8_t* __restrict__ blocks) {
   const size_t total = (size_t)n * n;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(q / n), l = (int)(q % n);
     int d[kOzDigits];
     ozaki_digits(A[q], emax[i], d);  // A[i*n + l] = row i (symmetric)
-    const size_t tile0 = ((size_t)(i / kOzMT) * nK + l / kOzKC) * kOzDigits;
-    const uint32_t off = umma_kmajor_offset(i % kOzMT, l % kOzKC, kOzKC) / 2;
+    uint8_t* blk = blocks + ((size_t)(i / kOzMT) * nS + l / kOzSetK) * kASetBytes;
 #pragma unroll
-    for (int t = 0; t < kOzDigits; ++t) tiles[(tile0 + t) * (kATileBytes / 2) + off] = bf16_of_int(d[t]);
+    for (int t = 0; t < kOzDigits; ++t) blk[oz_a8_offset(i % kOzMT, l % kOzSetK, t)] = (uint8_t)(d[t] + 128);
   }
 }
 
@@ -89,7 +101,7 @@ __global__ void k_oz_colexp(int n, const double* __restrict__ P, int* __restrict
   if (threadIdx.x < KP) atomicMax(&emaxP[threadIdx.x], m[threadIdx.x]);
 }
 
-// Digits of P into chunks [kchunk] of (8 * KPT) x 64 bf16, row index KPT * t + j (canonical
+// Digits of P into chunks [kchunk] of (8 * KPT) x 64 fp16, row index KPT * t + j (canonical
 // K-major layout, so digit t of every column j is one contiguous N-range).
 template <int KP, int KPT>
 __global__ void k_oz_slice_p(int n, const double* __restrict__ P, const int* __restrict__ emaxP,
@@ -103,24 +115,28 @@ __global__ void k_oz_slice_p(int n, const double* __restrict__ P, const int* __r
     ozaki_digits(P[q], emaxP[j], d);
     uint16_t* ch = chunks + (size_t)(l / kOzKC) * kChunkElems;
 #pragma unroll
-    for (int t = 0; t < kOzDigits; ++t) ch[umma_kmajor_offset(KPT * t + j, l % kOzKC, kOzKC) / 2] = bf16_of_int(d[t]);
+    for (int t = 0; t < kOzDigits; ++t) ch[umma_kmajor_offset(KPT * t + j, l % kOzKC, kOzKC) / 2] = f16_of_int(d[t]);
   }
 }
 
 template <int KPT>
 struct OzCfg {
   static constexpr uint32_t kPChunkBytes = kOzDigits * KPT * kOzKC * 2;
-  static constexpr uint32_t kAccCols = 8 * KPT;                         // one accumulator set
-  static constexpr uint32_t kTmemCols = (2 * kAccCols <= 256) ? 256 : 512;  // two sets (double buffer)
-  static constexpr size_t kBarBytes = 1024;  // barriers + TMEM slot, keeps tiles 1024-aligned
-  static constexpr size_t kSmem = kBarBytes + (size_t)kOzAStages * kAStageBytes + (size_t)kOzPBufs * kPChunkBytes;
+  static constexpr uint32_t kAccCols = 8 * KPT;           // the accumulator: 8 levels x KPT columns
+  static constexpr uint32_t kTmemCols = 512;              // accumulator + two converted A blocks
+  static_assert(kAccCols + 2 * kAColsPerSet <= kTmemCols, "tensor memory of one CTA");
+  static constexpr size_t kBarBytes = 1024;  // barriers + TMEM slot, keeps the blocks 1024-aligned
+  static constexpr size_t kSmem = kBarBytes + (size_t)kOzAStages * kASetBytes + (size_t)kOzPBufs * kPChunkBytes;
 };
 static_assert(OzCfg<32>::kSmem <= 227 * 1024, "shared memory of one CTA");
 
-constexpr int kOzDrainWarps = 4;                      // warps 0..3: TMEM lane quarters 0..3
-constexpr int kOzProducerWarp = 4;                    // TMA issue
-constexpr int kOzMmaWarp = 5;                         // MMA issue
-constexpr int kOzTcThreads = 32 * 6;
+constexpr int kOzDrainWarps = 8;     // warps 0..7: lane quarter w % 4, column half w / 4 of the accumulator
+constexpr int kOzConvWarps = 4;      // warps 8..11: lane quarter w % 4, A digits -> FP16 in TMEM
+constexpr int kOzProducerWarp = 12;  // TMA issue of the A digit blocks
+constexpr int kOzMmaWarp = 13;       // MMA issue
+constexpr int kOzPProducerWarp = 14; // TMA issue of the P digit chunks (its own thread, so that a
+                                     // chunk is requested as soon as a buffer is free)
+constexpr int kOzTcThreads = 32 * 15;
 
 // Work split (stream-K over windows). The product is nM row tiles x nW windows of wl chunks each
 // (wl = 2: one exact window of 128 values of l; wl = 1 for small n). The U = nM nW windows, tile
@@ -135,33 +151,66 @@ __host__ __device__ __forceinline__ int oz_slices(int mt, int nW, int G, long lo
   return oz_cta_of((long long)(mt + 1) * nW - 1, G, U) - oz_cta_of((long long)mt * nW, G, U) + 1;
 }
 
+// Two digit bytes (digit + 128) of w, bytes j and j + 1, -> an FP16 pair (the lower k in the low
+// half): each byte is placed under the exponent of 1024 (an FP16 1024 + u, exact for u < 1024) and
+// 1024 + 128 is subtracted from both halves at once (exact: small integers).
+__device__ __forceinline__ uint32_t oz_f16_pair(uint32_t w, uint32_t sel) {
+  const uint32_t b = __byte_perm(w, 0x64646464u, sel);  // halves 0x64uu: 1024 + u
+  const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&b), __half2half2(__ushort_as_half(0x6480)));
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Raw partial sums of one slice of the product: int64 levels 0..4 (units 2^-42 of the row and
+// column scales) and FP32 levels 5..7 (units 2^-49), [slice][row][KP] each; the split sum turns
+// them into FP64 once per output (FP64 instructions are scarce on this GPU: converting in the
+// MMA kernel held its SMs' FP64 units for the last ~5 us of the product).
+struct OzPart {
+  long long* qi;
+  float* qf;
+};
+__host__ __device__ inline OzPart oz_part(double* Qpart, int n, int kp, int ksplit) {
+  OzPart p;
+  p.qi = reinterpret_cast<long long*>(Qpart);
+  p.qf = reinterpret_cast<float*>(p.qi + (size_t)ksplit * n * kp);
+  return p;
+}
+
 // Qpart[k][i][j] = the part of (A P)_ij over the K range of slice k of row i's tile, for j < KP.
-// Warp-specialised: a producer thread streams A-digit tiles and P-digit chunks into shared memory
-// (empty/full mbarriers), an MMA thread issues tcgen05.mma into one of two TMEM accumulator sets,
-// alternating per window, and four drain warps read a finished set (levels 2..6 exact in int64,
-// 7..9 in FP32) while the MMA thread fills the other.
+// Warp-specialised, all waits bounded:
+//   producers (one thread each): A digit blocks (32 KB, 32 values of l) into kOzAStages shared
+//     stages, and P digit chunks (64 values of l) into kOzPBufs buffers, by 1-D TMA bulk copies on
+//     mbarriers;
+//   converters (4 warps, thread = row): a block's bytes -> FP16 digits in one of two TMEM A buffers;
+//   MMA issuer (one thread): per block and digit t of A, two tcgen05.mma (K = 16 each) with A from
+//     TMEM and the P digits from shared memory into levels t..7 of the accumulator;
+//   drain (8 warps, thread = row, half of the columns each): after each window of 128 values of l,
+//     levels 0..4 exact into int64, 5..7 in FP32, then the accumulator is released to the next
+//     window (one accumulator: the tensor memory also holds the two A buffers).
 template <int KPT>
 __global__ void __launch_bounds__(kOzTcThreads, 1)
-k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Atiles, const int* __restrict__ emaxA,
-           const uint8_t* __restrict__ Pchunks, const int* __restrict__ emaxP, double* __restrict__ Qpart,
+k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ablocks, const int* __restrict__ emaxA,
+           const uint8_t* __restrict__ Pchunks, int* __restrict__ emaxP, double* __restrict__ Qpart, int ksplit,
            int* __restrict__ err, const SolveState* __restrict__ st, int dir) {
   using C = OzCfg<KPT>;
   if (st != nullptr && st->done) return;
   extern __shared__ __align__(1024) uint8_t osm[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(osm);
-  uint64_t* empty = full + kOzAStages;
-  uint64_t* pfull = empty + kOzAStages;
-  uint64_t* pempty = pfull + kOzPBufs;
-  uint64_t* accf = pempty + kOzPBufs;  // [2] accumulator set ready for draining
-  uint64_t* acce = accf + 2;           // [2] accumulator set drained
-  uint64_t* fin = acce + 2;
+  uint64_t* sfull = reinterpret_cast<uint64_t*>(osm);  // [kOzAStages] A block landed
+  uint64_t* sempty = sfull + kOzAStages;               // [kOzAStages] A block converted (stage free)
+  uint64_t* pfull = sempty + kOzAStages;               // [kOzPBufs] P chunk landed
+  uint64_t* pempty = pfull + kOzPBufs;                 // [kOzPBufs] P chunk used by its MMAs
+  uint64_t* afull = pempty + kOzPBufs;                 // [2] TMEM A buffer written
+  uint64_t* aempty = afull + 2;                        // [2] TMEM A buffer read by its MMAs
+  uint64_t* accf = aempty + 2;                         // accumulator ready for draining
+  uint64_t* acce = accf + 1;                           // accumulator drained
+  uint64_t* fin = acce + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint8_t* As = osm + C::kBarBytes;
-  uint8_t* Ps = As + (size_t)kOzAStages * kAStageBytes;
+  uint8_t* Ps = As + (size_t)kOzAStages * kASetBytes;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x, g = blockIdx.x;
+  const int nS = nK * kOzSetsPerChunk;
   const long long U = (long long)((n + kOzMT - 1) / kOzMT) * nW;
   const long long f0 = U * g / G;
   const int nwin = (int)(U * (g + 1) / G - f0);
@@ -172,17 +221,19 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ At
 
   if (tid == 0) {
     for (int q = 0; q < kOzAStages; ++q) {
-      mbar_init(&full[q], 1);
-      mbar_init(&empty[q], 1);
+      mbar_init(&sfull[q], 1);
+      mbar_init(&sempty[q], kOzConvWarps);
     }
     for (int q = 0; q < kOzPBufs; ++q) {
       mbar_init(&pfull[q], 1);
       mbar_init(&pempty[q], 1);
     }
     for (int q = 0; q < 2; ++q) {
-      mbar_init(&accf[q], 1);
-      mbar_init(&acce[q], kOzDrainWarps);
+      mbar_init(&afull[q], kOzConvWarps);
+      mbar_init(&aempty[q], 1);
     }
+    mbar_init(accf, 1);
+    mbar_init(acce, kOzDrainWarps);  // every drain warp arrives once per window
     mbar_init(fin, 1);
     *abort_flag = 0;
     mbar_fence_init();
@@ -192,32 +243,28 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ At
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t abuf0 = tmem + C::kAccCols;
+  // the split sum scales with this copy of the column exponents of P (it clears the live ones)
+  if (g == 0 && tid < KP) emaxP[kMaxKP + tid] = emaxP[tid];  // two A buffers of kAColsPerSet columns after the accumulator
   int issued_a = 0, issued_p = 0;  // copies issued (producer thread only)
 
   if (warp == kOzProducerWarp) {
     if (lane == 0) {
-      const uint64_t pol_stream = l2_policy_evict_first();  // A digits: 16 B per entry of A, read once
+      const uint64_t pol_stream = l2_policy_evict_first();  // A digits: 8 B per entry of A, read once
       bool ok = true;
-      int cc = 0;  // chunks of this CTA so far
+      int j = 0;  // A blocks of this CTA so far
       for (int w = 0; w < nwin && ok; ++w) {
         const long long f = f0 + (dir ? nwin - 1 - w : w);
         const int mt = (int)(f / nW), c0 = (int)(f % nW) * wl, c1 = min(nK, c0 + wl);
-        for (int c = c0; c < c1 && ok; ++c, ++cc) {
-          const int b = cc % kOzPBufs;
-          if (cc >= kOzPBufs) ok = mbar_wait_bounded(&pempty[b], (uint32_t)((cc / kOzPBufs - 1) & 1));
-          if (!ok) break;
-          mbar_arrive_expect_tx(&pfull[b], C::kPChunkBytes);
-          tma_load_1d(Ps + (size_t)b * C::kPChunkBytes, Pchunks + (size_t)c * C::kPChunkBytes, C::kPChunkBytes,
-                      &pfull[b]);
-          issued_p = cc + 1;
-          for (int u = 0; u < kOzStagesPerChunk && ok; ++u) {
-            const int j = cc * kOzStagesPerChunk + u, q = j % kOzAStages;
-            if (j >= kOzAStages) ok = mbar_wait_bounded(&empty[q], (uint32_t)((j / kOzAStages - 1) & 1));
+        for (int c = c0; c < c1 && ok; ++c) {
+          for (int u = 0; u < kOzSetsPerChunk && ok; ++u, ++j) {
+            const int q = j % kOzAStages;
+            if (j >= kOzAStages) ok = mbar_wait_bounded(&sempty[q], (uint32_t)((j / kOzAStages - 1) & 1));
             if (!ok) break;
-            mbar_arrive_expect_tx(&full[q], kAStageBytes);
-            tma_load_1d_hint(As + (size_t)q * kAStageBytes,
-                             Atiles + (((size_t)mt * nK + c) * kOzDigits + u * kOzDPS) * kATileBytes, kAStageBytes,
-                             &full[q], pol_stream);
+            mbar_arrive_expect_tx(&sfull[q], kASetBytes);
+            tma_load_1d_hint(As + (size_t)q * kASetBytes,
+                             Ablocks + ((size_t)mt * nS + (size_t)c * kOzSetsPerChunk + u) * kASetBytes, kASetBytes,
+                             &sfull[q], pol_stream);
             issued_a = j + 1;
           }
           if (*abort_flag) ok = false;
@@ -228,13 +275,79 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ At
         if (err != nullptr) atomicExch(err, 1);
       }
     }
+  } else if (warp == kOzPProducerWarp) {
+    if (lane == 0) {
+      bool ok = true;
+      int cc = 0;  // chunks of this CTA so far
+      for (int w = 0; w < nwin && ok; ++w) {
+        const long long f = f0 + (dir ? nwin - 1 - w : w);
+        const int c0 = (int)(f % nW) * wl, c1 = min(nK, c0 + wl);
+        for (int c = c0; c < c1 && ok; ++c, ++cc) {
+          const int b = cc % kOzPBufs;
+          if (cc >= kOzPBufs) ok = mbar_wait_bounded(&pempty[b], (uint32_t)((cc / kOzPBufs - 1) & 1));
+          if (!ok) break;
+          mbar_arrive_expect_tx(&pfull[b], C::kPChunkBytes);
+          tma_load_1d(Ps + (size_t)b * C::kPChunkBytes, Pchunks + (size_t)c * C::kPChunkBytes, C::kPChunkBytes,
+                      &pfull[b]);
+          issued_p = cc + 1;
+          if (*abort_flag) ok = false;
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (err != nullptr) atomicExch(err, 1);
+      }
+    }
+  } else if (warp >= kOzDrainWarps && warp < kOzDrainWarps + kOzConvWarps) {
+    // converters: thread = row 32 (warp % 4) + lane of the M tile (warps 8..11: quarters 0..3)
+    const int r = 32 * (warp & 3) + lane;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    bool ok = true;
+    int j = 0;
+    for (int w = 0; w < nwin && ok; ++w) {
+      const long long f = f0 + (dir ? nwin - 1 - w : w);
+      const int c0 = (int)(f % nW) * wl, nsets = (min(nK, c0 + wl) - c0) * kOzSetsPerChunk;
+      for (int u = 0; u < nsets && ok; ++u, ++j) {
+        const int q = j % kOzAStages, ab = j & 1;
+        ok = mbar_wait_bounded(&sfull[q], (uint32_t)((j / kOzAStages) & 1));
+        if (ok && j >= 2) ok = mbar_wait_bounded(&aempty[ab], (uint32_t)((j / 2 - 1) & 1));
+        ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // tcgen05.st needs the whole warp
+        if (!ok) break;
+        tc_fence_after_sync();
+        const uint8_t* row = As + (size_t)q * kASetBytes + r * 256;
+        const uint32_t dst = abuf0 + (uint32_t)ab * kAColsPerSet + lane_off;
+#pragma unroll
+        for (int t = 0; t < kOzDigits; ++t) {
+          const uint4 lo = *reinterpret_cast<const uint4*>(row + (((2 * t) ^ (r & 7)) << 4));
+          const uint4 hi = *reinterpret_cast<const uint4*>(row + (((2 * t + 1) ^ (r & 7)) << 4));
+          uint32_t v[16];
+          const uint32_t wd[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+          for (int q2 = 0; q2 < 8; ++q2) {
+            v[2 * q2] = oz_f16_pair(wd[q2], 0x4140u);      // bytes 0, 1
+            v[2 * q2 + 1] = oz_f16_pair(wd[q2], 0x4342u);  // bytes 2, 3
+          }
+          tmem_st16(dst + (uint32_t)(16 * t), v);  // digit t: columns 16 t .. 16 t + 15 (k pairs 0..15)
+        }
+        tmem_wait_st();
+        tc_fence_before_sync();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&afull[ab]);
+          mbar_arrive(&sempty[q]);
+        }
+      }
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      if (err != nullptr) atomicExch(err, 1);
+    }
   } else if (warp == kOzMmaWarp) {
     if (lane == 0) {
       bool ok = true;
-      int cc = 0;
+      int cc = 0, j = 0;
       for (int w = 0; w < nwin && ok; ++w) {
-        const int ab = w & 1;
-        if (w >= 2) ok = mbar_wait_bounded(&acce[ab], (uint32_t)((w / 2 - 1) & 1));
+        if (w >= 1) ok = mbar_wait_bounded(acce, (uint32_t)((w - 1) & 1));  // the previous window drained
         tc_fence_after_sync();
         const long long f = f0 + (dir ? nwin - 1 - w : w);
         const int c0 = (int)(f % nW) * wl, nc = min(nK, c0 + wl) - c0, cc0 = cc;
@@ -242,30 +355,31 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ At
           const int b = cc % kOzPBufs;
           ok = mbar_wait_bounded(&pfull[b], (uint32_t)((cc / kOzPBufs) & 1));
           const uint32_t b_base = smem_addr(Ps + (size_t)b * C::kPChunkBytes);
-          for (int u = 0; u < kOzStagesPerChunk && ok; ++u) {
-            const int j = cc * kOzStagesPerChunk + u, q = j % kOzAStages;
-            ok = mbar_wait_bounded(&full[q], (uint32_t)((j / kOzAStages) & 1));
+          for (int u = 0; u < kOzSetsPerChunk && ok; ++u, ++j) {
+            const int ab = j & 1;
+            ok = mbar_wait_bounded(&afull[ab], (uint32_t)((j / 2) & 1));
             if (!ok) break;
+            tc_fence_after_sync();
+            const uint32_t a_base = abuf0 + (uint32_t)ab * kAColsPerSet;
 #pragma unroll
-            for (int dd = 0; dd < kOzDPS; ++dd) {
-              const int t = u * kOzDPS + dd;
-              const uint32_t a_base = smem_addr(As + (size_t)q * kAStageBytes + (size_t)dd * kATileBytes);
-              const uint32_t idesc = umma_idesc_bf16_f32(kOzMT, KPT * (kOzDigits - t));
-              const uint32_t d = tmem + (uint32_t)(ab * C::kAccCols + KPT * t);
+            for (int t = 0; t < kOzDigits; ++t) {
+              const uint32_t idesc = umma_idesc_f16_f32(kOzMT, KPT * (kOzDigits - t));
+              const uint32_t d = tmem + (uint32_t)(KPT * t);
 #pragma unroll
-              for (int k4 = 0; k4 < kOzKC / 16; ++k4) {
-                const uint32_t first = (cc == cc0 && t == 0 && k4 == 0) ? 0u : 1u;
-                umma_bf16(d, umma_smem_desc(a_base + 256u * k4, 128, 1024),
-                          umma_smem_desc(b_base + 256u * k4, 128, 1024), idesc, first);
+              for (int kk = 0; kk < kOzSetK / 16; ++kk) {
+                const int k4 = u * (kOzSetK / 16) + kk;  // K step of 16 inside the P chunk
+                const uint32_t first = (cc == cc0 && u == 0 && t == 0 && kk == 0) ? 0u : 1u;
+                umma_tmem_a(d, a_base + (uint32_t)(16 * t + 8 * kk),
+                                 umma_smem_desc(b_base + 256u * k4, 128, 1024), idesc, first);
               }
             }
-            umma_commit(&empty[q]);
+            umma_commit(&aempty[ab]);
           }
           if (ok) umma_commit(&pempty[b]);
           if (*abort_flag) ok = false;
         }
         if (!ok) *abort_flag = 1;  // before the commit, so the drain warps see it
-        umma_commit(&accf[ab]);
+        umma_commit(accf);
       }
       if (!ok) {
         *abort_flag = 1;
@@ -274,73 +388,71 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ At
       umma_commit(fin);
       mbar_wait_bounded(fin, 0);
     }
-  } else {
-    // drain warps 0..3: warp w reads TMEM lanes 32w..32w+31 = rows of this M tile
-    long long acc_i[KPT];
-    float acc_f[KPT];
+  } else if (warp < kOzDrainWarps) {
+    // drain warps 0..7: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of this M tile) and the
+    // column half w / 4 (DC = KPT / 2 columns) of every level
+    constexpr int DC = KPT / 2;
+    const int half = warp >> 2;
+    long long acc_i[DC];
+    float acc_f[DC];
 #pragma unroll
-    for (int j = 0; j < KPT; ++j) {
-      acc_i[j] = 0;
-      acc_f[j] = 0.f;
+    for (int jj = 0; jj < DC; ++jj) {
+      acc_i[jj] = 0;
+      acc_f[jj] = 0.f;
     }
     bool ok = true;
     for (int w = 0; w < nwin; ++w) {
-      const int ab = w & 1;
-      if (!mbar_wait_bounded(&accf[ab], (uint32_t)((w / 2) & 1))) ok = false;
+      if (!mbar_wait_bounded(accf, (uint32_t)(w & 1))) ok = false;
       tc_fence_after_sync();
-      if (!ok || *abort_flag) {
-        ok = false;
-        break;
-      }
-      const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ab * C::kAccCols);
+      ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // tcgen05.ld needs the whole warp
+      if (!ok) break;
+      const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(DC * half);
+      // two rounds of four levels: the loads of a round are in flight together (one wait each)
 #pragma unroll
-      for (int L = 0; L < kOzDigits; ++L) {
-        float v[KPT];
-        if constexpr (KPT == 32) {
-          uint32_t r[32];
-          tmem_ld32(lane_base + (uint32_t)(KPT * L), r);
-          tmem_wait_ld();
+      for (int L0 = 0; L0 < kOzDigits; L0 += 4) {
+        uint32_t rr[4][DC];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-        } else {
-          uint32_t r[16];
-          tmem_ld16(lane_base + (uint32_t)(KPT * L), r);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+        for (int q = 0; q < 4; ++q) {
+          if constexpr (DC == 16) tmem_ld16(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
+          else tmem_ld8(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
         }
-        if (L < 5) {
-          const int sh = 7 * (4 - L);
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < KPT; ++j) acc_i[j] += (long long)__float2int_rn(v[j]) << sh;
-        } else {
-          const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : 0x1p-14f;
+        for (int q = 0; q < 4; ++q) {
+          const int L = L0 + q;
+          if (L < 5) {
+            const int sh = 7 * (4 - L);
 #pragma unroll
-          for (int j = 0; j < KPT; ++j) acc_f[j] = fmaf(v[j], sc, acc_f[j]);
+            for (int jj = 0; jj < DC; ++jj) acc_i[jj] += (long long)__float2int_rn(__uint_as_float(rr[q][jj])) << sh;
+          } else {
+            const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : 0x1p-14f;
+#pragma unroll
+            for (int jj = 0; jj < DC; ++jj) acc_f[jj] = fmaf(__uint_as_float(rr[q][jj]), sc, acc_f[jj]);
+          }
         }
       }
       tc_fence_before_sync();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[ab]);
+      if (lane == 0) mbar_arrive(acce);
       const long long f = f0 + (dir ? nwin - 1 - w : w);
       if (w == nwin - 1 || (dir ? f % nW == 0 : (f + 1) % nW == 0)) {  // end of a segment: its tile's rows
-        const int mt = (int)(f / nW), row = mt * kOzMT + 32 * warp + lane;
+        const int mt = (int)(f / nW), row = mt * kOzMT + 32 * (warp & 3) + lane;
         const int slice = g - oz_cta_of((long long)mt * nW, G, U);
         if (row < n) {
-          const int fa = emaxA[row] - 1022;
-          double* out = Qpart + ((size_t)slice * n + row) * KP;
+          const OzPart qp = oz_part(Qpart, n, KP, ksplit);
+          const size_t o = ((size_t)slice * n + row) * KP + DC * half;
 #pragma unroll
-          for (int j = 0; j < KPT; ++j) {
-            if (j < KP) {
-              const double v = (double)acc_i[j] * 0x1p-42 + (double)acc_f[j] * 0x1p-49;
-              out[j] = ldexp(v, fa + emaxP[j] - 1022);
+          for (int jj = 0; jj < DC; ++jj) {
+            if (DC * half + jj < KP) {
+              qp.qi[o + jj] = acc_i[jj];
+              qp.qf[o + jj] = acc_f[jj];
             }
           }
         }
 #pragma unroll
-        for (int j = 0; j < KPT; ++j) {
-          acc_i[j] = 0;
-          acc_f[j] = 0.f;
+        for (int jj = 0; jj < DC; ++jj) {
+          acc_i[jj] = 0;
+          acc_f[jj] = 0.f;
         }
       }
     }
@@ -350,34 +462,50 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ At
     }
   }
   __syncthreads();
-  if (*abort_flag && tid == 32 * kOzProducerWarp) {
-    // let the copies still in flight land before the shared memory is released (bounded waits);
-    // only the last issue into each stage or buffer can still be pending
+  // after an abort, let the copies still in flight land before the shared memory is released
+  // (bounded waits); only the last issue into each stage or buffer can still be pending
+  if (*abort_flag && tid == 32 * kOzProducerWarp)
     for (int j = max(0, issued_a - kOzAStages); j < issued_a; ++j)
-      mbar_wait_bounded(&full[j % kOzAStages], (uint32_t)((j / kOzAStages) & 1));  // stages of kOzDPS digits
+      mbar_wait_bounded(&sfull[j % kOzAStages], (uint32_t)((j / kOzAStages) & 1));
+  if (*abort_flag && tid == 32 * kOzPProducerWarp)
     for (int cc = max(0, issued_p - kOzPBufs); cc < issued_p; ++cc)
       mbar_wait_bounded(&pfull[cc % kOzPBufs], (uint32_t)((cc / kOzPBufs) & 1));
-  }
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
   if (warp == 0) tmem_dealloc(tmem, C::kTmemCols);
 }
 
-// Q[i][j] = sum over the slices of row i's tile of Qpart[k][i][j], in slice order. Block 0 then
-// clears the column exponents of P for the next product (they are rebuilt by the W/P update,
-// which writes P).
+// (A P)_ij from the raw partials of the slices of row i's tile: the int64 parts summed exactly, the
+// FP32 parts summed in FP64 in slice order, one FMA, then the scale 2^(F_i + G_j) (a product by a
+// power of two: exact wherever ldexp is, which takes the rest).
+__device__ __forceinline__ double oz_finish(long long si, double sf, int e) {
+  const double v = fma(sf, 0x1p-49, (double)si * 0x1p-42);
+  if (e >= -1022 && e <= 1023) return v * __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(v, e);
+}
+
+// Q[i][j] = the product from the slices of row i's tile (in slice order). Block 0 then clears the
+// column exponents of P for the next product (they are rebuilt by the W/P update, which writes
+// P); the scaling reads the copy the MMA kernel made of them.
 template <int KP>
 __global__ void k_oz_sum(int n, int nW, const double* __restrict__ Qpart, double* __restrict__ Q,
-                         int* __restrict__ emaxP, const SolveState* __restrict__ st, int nctas) {
+                         const int* __restrict__ emaxA, int* __restrict__ emaxP, const SolveState* __restrict__ st,
+                         int nctas, int ksplit) {
   if (st != nullptr && st->done) return;
+  const OzPart qp = oz_part(const_cast<double*>(Qpart), n, KP, ksplit);
   const size_t total = (size_t)n * KP;
   const long long U = (long long)((n + kOzMT - 1) / kOzMT) * nW;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-    const int ns = oz_slices((int)(q / KP) / kOzMT, nW, nctas, U);
-    double a = Qpart[q];
-    for (int k = 1; k < ns; ++k) a += Qpart[(size_t)k * total + q];
-    Q[q] = a;
+    const int i = (int)(q / KP), j = (int)(q % KP);
+    const int ns = oz_slices(i / kOzMT, nW, nctas, U);
+    long long si = 0;
+    double sf = 0.0;
+    for (int k = 0; k < ns; ++k) {
+      si += qp.qi[(size_t)k * total + q];
+      sf += (double)qp.qf[(size_t)k * total + q];
+    }
+    Q[q] = oz_finish(si, sf, emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
   }
   if (blockIdx.x == 0 && threadIdx.x < KP) emaxP[threadIdx.x] = 0;
 }
@@ -387,13 +515,15 @@ __global__ void k_oz_sum(int n, int nW, const double* __restrict__ Qpart, double
 template <int KP>
 __global__ void __launch_bounds__(kThreads)
 k_oz_sum_gram(int n, int nW, const double* __restrict__ Qpart, const double* __restrict__ P, double* __restrict__ Q,
-              int* __restrict__ emaxP, double* __restrict__ part, int pstride, const SolveState* __restrict__ st, int nctas) {
+              const int* __restrict__ emaxA, int* __restrict__ emaxP, double* __restrict__ part, int pstride,
+              const SolveState* __restrict__ st, int nctas, int ksplit) {
   using C = Cfg<KP>;
   using G = GramTile<KP>;
   if (st != nullptr && st->done) return;
   __shared__ __align__(16) double Xs[C::ROWS * KP];
   __shared__ __align__(16) double Ys[C::ROWS * KP];
   __shared__ __align__(16) double red[G::RED];
+  const OzPart qp = oz_part(const_cast<double*>(Qpart), n, KP, ksplit);
   const size_t total = (size_t)n * KP;
   const long long U = (long long)((n + kOzMT - 1) / kOzMT) * nW;
   int r0, r1;
@@ -409,14 +539,24 @@ k_oz_sum_gram(int n, int nW, const double* __restrict__ Qpart, const double* __r
     if (i < r1) {
       const size_t o = (size_t)i * KP + j0;
       ldv<C::CPT>(P + o, xv);
-      ldv<C::CPT>(Qpart + o, yv);
       const int ns = oz_slices(i / kOzMT, nW, nctas, U);
-      for (int k = 1; k < ns; ++k) {
-        double t[C::CPT];
-        ldv<C::CPT>(Qpart + (size_t)k * total + o, t);
+      long long si[C::CPT];
+      double sf[C::CPT];
 #pragma unroll
-        for (int c = 0; c < C::CPT; ++c) yv[c] += t[c];
+      for (int c = 0; c < C::CPT; ++c) {
+        si[c] = 0;
+        sf[c] = 0.0;
       }
+      for (int k = 0; k < ns; ++k) {
+#pragma unroll
+        for (int c = 0; c < C::CPT; ++c) {
+          si[c] += qp.qi[(size_t)k * total + o + c];
+          sf[c] += (double)qp.qf[(size_t)k * total + o + c];
+        }
+      }
+      const int fa = emaxA[i] - 1022;
+#pragma unroll
+      for (int c = 0; c < C::CPT; ++c) yv[c] = oz_finish(si[c], sf[c], fa + emaxP[kMaxKP + j0 + c] - 1022);
       stv<C::CPT>(Q + o, yv);
     }
 #pragma unroll
@@ -436,7 +576,7 @@ k_oz_sum_gram(int n, int nW, const double* __restrict__ Qpart, const double* __r
 
 size_t oz_a_tiles_bytes(int n) {
   const size_t nM = (n + kOzMT - 1) / kOzMT, nK = (n + kOzKC - 1) / kOzKC;
-  return nM * nK * kOzDigits * kATileBytes;
+  return nM * nK * kOzSetsPerChunk * kASetBytes;
 }
 size_t oz_p_chunks_bytes(int n, int kp) {
   const int kpt = kp < 16 ? 16 : kp;
@@ -472,10 +612,10 @@ int oz_ksplit(int n, int sms) {
 }
 
 void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* Atiles) {
-  cudaMemsetAsync(Atiles, 0, oz_a_tiles_bytes(n), s);
+  cudaMemsetAsync(Atiles, 0x80, oz_a_tiles_bytes(n), s);  // digit 0 everywhere (byte = digit + 128)
   k_oz_rowexp<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, A, emaxA);
-  const int nK = (n + kOzKC - 1) / kOzKC;
-  k_oz_slice_a<<<4096, 256, 0, s>>>(n, nK, A, emaxA, reinterpret_cast<uint16_t*>(Atiles));
+  const int nS = (n + kOzKC - 1) / kOzKC * kOzSetsPerChunk;
+  k_oz_slice_a8<<<4096, 256, 0, s>>>(n, nS, A, emaxA, Atiles);
 }
 
 template <int KP, int KPT>
@@ -495,10 +635,12 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
     k_oz_colexp<KP><<<g < 1024 ? g : 1024, 256, 0, s>>>(n, P, emaxP, st);
   }
   k_oz_slice_p<KP, KPT><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
+  const int ks = oz_ksplit(n, sms);
   k_dense_tc<KPT><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks, emaxP,
-                                                       Qpart, err, st, 0);
-  if (part != nullptr) k_oz_sum_gram<KP><<<nb, kThreads, 0, s>>>(n, sp.nW, Qpart, P, Q, emaxP, part, pstride, st, sp.G);
-  else k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, sp.nW, Qpart, Q, emaxP, st, sp.G);
+                                                       Qpart, ks, err, st, 0);
+  if (part != nullptr)
+    k_oz_sum_gram<KP><<<nb, kThreads, 0, s>>>(n, sp.nW, Qpart, P, Q, emaxA, emaxP, part, pstride, st, sp.G, ks);
+  else k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, sp.nW, Qpart, Q, emaxA, emaxP, st, sp.G, ks);
 }
 
 template <int KPT>
@@ -511,8 +653,9 @@ static void oz_mma_kp(cudaStream_t s, int n, int KP, int sms, const uint8_t* Ati
     attr = true;
   }
   const OzSplit sp(n, sms > 0 ? sms : 1);
-  k_dense_tc<KPT><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks, emaxP,
-                                                       Qpart, nullptr, nullptr, 0);
+  k_dense_tc<KPT><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks,
+                                                       const_cast<int*>(emaxP), Qpart, oz_ksplit(n, sms), nullptr,
+                                                       nullptr, 0);
 }
 
 void oz_mma(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const uint8_t* Pchunks,

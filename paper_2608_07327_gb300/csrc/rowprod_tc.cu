@@ -55,13 +55,6 @@ __device__ __forceinline__ double scale2(double v, int k) {
                                                             : ldexp(v, k);
 }
 
-// 8 consecutive 32-bit TMEM columns of this thread's lane (warp w reads lanes 32 (w % 4) .. + 31)
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr));
-}
-
 // 8 bf16 digits (16 bytes) for 8 consecutive values of the reduction index
 __device__ __forceinline__ uint4 pack8(const int (&d)[8]) {
   uint4 v;

@@ -585,8 +585,11 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
   cg::cluster_group cluster = cg::this_cluster();
   const int s = st->s, tid = threadIdx.x, c = (int)cluster.block_rank();
   const bool lead = (c == 0 && tid == 0);
-  if (st->done) {
-    if (lead && use_cond) cudaGraphSetConditional(cond, 0);
+  if (st->done) {  // the solve stopped in an earlier iteration: no W, P update in this one
+    if (lead) {
+      st->pw_skip = 1;
+      if (use_cond) cudaGraphSetConditional(cond, 0);
+    }
     return;
   }
   const bool ct = tid < CC::NT;
