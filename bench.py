@@ -89,6 +89,8 @@ def parse():
     p.add_argument("--kernel-launches", type=int, default=20, help="launches of the dominant kernel timed alone")
     p.add_argument("--cpu-sample-iters", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-spmm-roofline", action="store_true",
+                   help="skip the SpMM HBM roofline (diffusion 128^3 at s = 1, 4 in FP64; 27-point 96^3 at s = 16 in FP32)")
     p.add_argument("--precision", default=None, choices=["fp64", "tc", "mixed"],
                    help="tc: dense product on the BF16 tensor cores by exact digit splitting (FP64 accuracy); "
                         "mixed: FP32 inner solves in FP64 refinement (CSR); default: the workload's own")
@@ -206,18 +208,74 @@ def read_ceiling_gbs(stream, flush):
     return 4 * (1 << 28) / (statistics.median(ts) * 1e-3) / 1e9
 
 
-def launches_per_solve(info, dense, algo_cg, tc=False, mixed=False):
+BODY_UNROLL = 4  # loop iterations per pass of the library's graph loop (the passes end on whole bodies)
+
+
+def launches_per_solve(info, dense, algo_cg, tc=False, mixed=False, cg_fused=False):
     """Kernels of ours launched by one solve call (the counter of the graph the library builds). The
     tensor-core dense product is four kernels (column exponents, digits of P, MMAs, split sum); the
-    mixed-precision loop runs its Gram as a kernel of its own."""
+    mixed-precision loop runs its Gram as a kernel of its own; dense CG runs one kernel per
+    iteration. The graph loop runs whole passes of BODY_UNROLL iterations, so up to BODY_UNROLL - 1
+    bodies after the stop launch and return at once: counted here as launched (an upper bound)."""
     inner = info["restarts"] + 1
     if algo_cg:
-        setup, exit_, body = 3, 5, 5
+        setup, exit_, body = 3, 5, (1 if cg_fused else 5)
     else:
         setup, exit_, body = 8, 7, (8 if (dense or mixed) else 7)
         if tc:
             setup, body = setup + 3, body + 3
-    return inner * (1 + setup + exit_) + body * info["iterations"] + (0 if algo_cg else 1)
+    bodies = info["iterations"] + (BODY_UNROLL - 1) * inner
+    return inner * (1 + setup + exit_) + body * bodies + (0 if algo_cg else 1)
+
+
+def spmm_roofline(mb, stream, flush, peak_gbs, launches=10):
+    """HBM roofline of the CSR product A P alone, in the solver's launch configuration, on the two
+    sparse workloads where HBM binds: 3D diffusion 128^3 (FP64, s = 1 and s = 4) and the 27-point
+    stencil 96^3 (FP32 blocks, s = 16). Algorithmic bytes: the CSR once (12 nnz + 4 (n + 1) in FP64,
+    8 nnz + 4 (n + 1) in FP32) plus P in and A P out (2 n KP values); L2 flushed before every
+    launch; CUDA events on the launching stream."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cases = []
+    for name, gen, s, f32 in (("3D 7-point diffusion 128^3", lambda: wl.diffusion3d(128, 0), 1, False),
+                              ("3D 7-point diffusion 128^3", lambda: wl.diffusion3d(128, 0), 4, False),
+                              ("3D 27-point stencil 96^3", lambda: wl.stencil27(96, 0), 16, True)):
+        A = gen()
+        n, nnz = A.n, A.nnz
+        kp = mb.mbpcg_k_padded_width(s)
+        rp = torch.as_tensor(A.row_ptr, device=dev)
+        ci = torch.as_tensor(A.col_idx, device=dev)
+        dt = torch.float32 if f32 else torch.float64
+        av = torch.as_tensor(A.val, device=dev).to(dt)
+        P = torch.zeros((n, kp), dtype=dt, device=dev)
+        P[:, :s] = torch.as_tensor(wl.initial_block(n, s, 1), device=dev).to(dt)
+        AP = torch.empty_like(P)
+        if f32:
+            launch = lambda: mb.mbpcg_k_spmm_f32(n, rp, ci, av, s, P, AP, stream.cuda_stream)  # noqa: E731
+            nbytes, kname = 8.0 * nnz + 4.0 * (n + 1) + 8.0 * n * kp, f"k_spmm_f<{kp}> (FP32)"
+        else:
+            launch = lambda: mb.mbpcg_k_spmm(n, rp, ci, av, s, P, AP, stream.cuda_stream)  # noqa: E731
+            nbytes, kname = 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n * kp, f"k_spmm<{kp}> (FP64)"
+        ts = []
+        with torch.cuda.stream(stream):
+            launch()
+            for _ in range(launches):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                launch()
+                ev1.record(stream)
+                ev1.synchronize()
+                ts.append(ev0.elapsed_time(ev1))
+        ms = sum(ts) / len(ts)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        cases.append({"workload": name, "n": n, "nnz": int(nnz), "s": s, "kernel": kname, "kernel_ms": round(ms, 5),
+                      "algorithmic_bytes": nbytes, "achieved": round(gbs, 1), "frac": round(gbs / peak_gbs, 4)})
+        del rp, ci, av, P, AP
+    return {"bound": "hbm", "unit": "GB/s", "peak": peak_gbs, "cases": cases,
+            "timing": f"{launches} launches, L2 flushed (256 MB write) before each, CUDA events on the stream",
+            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
 
 def roofline_tc(n, s, kp, k_ms, single_ms, seq_ms, read_gbs, peaks, traffic, launches):
@@ -555,8 +613,13 @@ def run_ours(args, world, rank, local):
             "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": 8 * n + 8 * n * s,
                     "d2h_bytes_per_step": 8 * n + 200 * (info["restarts"] + 1)},
             "gpu_launches": sum(launches_per_solve(i, dense, False, prec == mb.MBPCG_FP64_TC, mixed) for i in infos),
+            "gpu_launches_cg": sum(launches_per_solve(i, dense, True, cg_fused=dense and n % 2 == 0 and n <= 16384)
+                                   for i in cg_infos),
             "clocks": clk.summary(),
         }
+        if not args.no_spmm_roofline:
+            peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+            line["spmm_roofline"] = spmm_roofline(mb, stream, flush, float(peaks.get("hbm_gbs", 6800.0)))
         if mixed and not dense:
             u, c, t = solver.spmm_tuning()
             line["spmm_autotune"] = {"unroll": u, "ctas_per_sm": c,

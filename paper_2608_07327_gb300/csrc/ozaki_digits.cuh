@@ -2,7 +2,7 @@
 // al., "Error-free transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 2012). A value x of a group (a row or a
 // column) whose largest biased exponent is emax is written as
-//     x = 2^(emax - 1022) * sum_{t=0..7} d_t 2^(-7 - 7t)   (+ truncation below 2^-56 of the scale),
+//     x = 2^(emax - 1022) * sum_{t=0..7} d_t 2^(-7 - 7t)   (+ rounding below 2^-56 of the scale),
 // d_t an integer in [-127, 127] taken straight from the 53-bit significand (integer shifts): exact
 // in BF16 and in FP16. A product of two such digits is below 2^14.
 #pragma once
@@ -25,7 +25,9 @@ __device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDig
   if (e != 0 && e != 0x7FF && emax != 0) {
     const unsigned long long mant = ((unsigned long long)bits & ((1ull << 52) - 1)) | (1ull << 52);
     const int shift = e - emax + 3;  // X = |x| 2^(1022 - emax) 2^56 < 2^56
-    X = shift >= 0 ? (mant << shift) : (shift > -60 ? (mant >> (-shift)) : 0ull);
+    // below 2^-3 of the group's largest value the significand is shifted out at the bottom: round
+    // to nearest there (a truncation would bias every product towards zero)
+    X = shift >= 0 ? (mant << shift) : (shift > -60 ? ((mant + (1ull << (-shift - 1))) >> (-shift)) : 0ull);
   }
   const int sgn = bits < 0 ? -1 : 1;
 #pragma unroll

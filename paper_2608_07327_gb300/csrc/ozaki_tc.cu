@@ -4,28 +4,31 @@
 //
 // Splitting. Each row i of A (A is symmetric, so row i = column i) is scaled by 2^-F_i, F_i the
 // largest binary exponent in the row, and the magnitude of every entry is written as 8 base-128
-// digits taken straight from its 53-bit significand (integer shifts, truncation below 2^-56 of the
-// row scale). Columns of P are split the same way with their own scales G_j. A digit is an integer
-// in [-127, 127], exact in FP16. Then
-//     (A P)_ij = 2^(F_i + G_j) * sum_{L=2..16} 2^(-7L) * S_L,   S_L = sum_{t+u=L} sum_l a^t_il b^u_lj
-// and the terms with t + u > 9 are below 2^-56 of the row/column scales and are dropped.
+// digits taken straight from its 53-bit significand (integer shifts; rounded to nearest below 2^-56
+// of the row scale). Columns of P are split the same way with their own scales G_j. A digit is an
+// integer in [-127, 127], exact in FP16. With level L = t + u of the digit pair (a^t, b^u),
+//     (A P)_ij = 2^(F_i + G_j) * sum_L 2^(-7L - 14) * S_L,   S_L = sum_{t+u=L} sum_l a^t_il b^u_lj,
+// and levels 0..8 are kept (43 of the 64 pairs; level 8 weighs 2^-70 of the scales per term).
+// Dropping level 8 as well -- the first form of this product -- left an error of about 1.7e-14
+// ||A P|| on the benchmark system, eight times an FP64 product's, and cost the solver 6 % more
+// iterations than the FP64 oracle; with it the error is about 6e-16 ||A P|| (measured on an
+// emulation of the split against an 80-bit product), below an FP64 product's.
 //
 // Exactness. A product of two digits is < 2^14, so a level-L sum over a window of 128 values of l
-// is at most (L-1) * 127^2 * 128 < 2^24 for L <= 6: the FP32 accumulator of the tensor core holds
-// it exactly. Levels 2..6 are therefore drained from TMEM every 128 values of l and combined in
-// int64 (exact); levels 7..9 are carried in FP32 (their rounding is below 2^-58 of the scale).
-// The result has the accuracy of an FP64 product (error ~2^-53 |A||P|; an FP64 GEMM's bound is
-// n 2^-53 |A||P|).
+// is at most (L + 1) * 127^2 * 128 < 2^24 for L <= 4 (and 7 * 127^2 * 128 < 2^24 for L = 8): the
+// FP32 accumulator of the tensor core holds it exactly. Levels 0..4 are therefore drained from
+// TMEM every 128 values of l and combined in int64 (exact); levels 5..8 are carried in FP32
+// (their rounding is below 2^-70 of the scale per window).
 //
 // Data movement. The digits of A are made once per matrix and stored as bytes (digit + 128), 8 bytes
-// per entry of A -- as many as A itself in FP64 -- in blocks of 128 rows x 32 values of l (32 KB)
+// per entry of A -- as many as A itself in FP64 -- in blocks of 128 rows x 16 values of l (16 KB)
 // that one 1-D TMA bulk copy moves into shared memory. Converter warps turn each block into the
 // FP16 operand of the tensor cores and write it to tensor memory (tcgen05.st), where the MMA reads
 // A from (the A-in-TMEM form of tcgen05.mma); the digits of P come from shared memory (canonical
 // K-major tiles, 8*KPT x 64 per chunk of l, made by k_oz_slice_p every product). The MMA for digit
-// t of A uses all needed digits of P at once (N = KPT * (8 - t)), writing levels t..7 of the
-// accumulator. Producer, converters, MMA issuer and drain run in separate warps; every wait is
-// bounded.
+// t of A uses all needed digits of P at once (N = KPT * (9 - t), or 8 KPT for t = 0), writing
+// levels t..min(t + 7, 8) of the accumulator. Producer, converters, MMA issuer and drain run in
+// separate warps; every wait is bounded.
 #include <cuda_fp16.h>
 
 #include "kernels.h"
@@ -39,12 +42,13 @@ namespace {
 constexpr int kOzMT = 128;                             // rows per M tile (= TMEM lanes)
 constexpr int kOzKC = 64;                              // reduction index per chunk (P digits)
 constexpr int kOzWin = 2;                              // chunks per exact window (128 values of l)
-constexpr int kOzSetK = 32;                            // reduction index per block of A digits
+constexpr int kOzSetK = 16;                            // reduction index per block of A digits (one MMA K step)
 constexpr int kOzSetsPerChunk = kOzKC / kOzSetK;
-constexpr uint32_t kASetBytes = kOzMT * kOzSetK * kOzDigits;  // 32 KB: 128 rows x 32 l x 8 digit bytes
-constexpr int kOzAStages = 3;                          // A blocks in flight (shared memory)
+constexpr uint32_t kASetBytes = kOzMT * kOzSetK * kOzDigits;  // 16 KB: 128 rows x 16 l x 8 digit bytes
+constexpr int kOzAStages = 6;                          // A blocks in flight (shared memory)
 constexpr int kOzPBufs = 3;                            // P digit chunks in flight
-constexpr uint32_t kAColsPerSet = kOzDigits * kOzSetK / 2;  // TMEM columns of one converted block (128)
+constexpr uint32_t kAColsPerSet = kOzDigits * kOzSetK / 2;  // TMEM columns of one converted block (64)
+constexpr int kOzLevels = 9;                           // digit-pair levels t + u = 0..8 kept
 
 }  // namespace
 
@@ -59,13 +63,12 @@ __global__ void k_oz_rowexp(int n, const double* __restrict__ A, int* __restrict
   if (lane == 0) emax[warp] = m;
 }
 
-// Byte offset of digit t of (row r, value k of l) inside a block of A digits: row r owns 256
-// bytes, 16-byte slot 2t + k/16 of them holding k = 16 (slot % 2) .. +15 of digit t; the slot is
-// stored at position slot ^ (r % 8), so that the 32 rows a converter warp reads at once fall on
-// different shared-memory banks.
+// Byte offset of digit t of (row r, value k of l) inside a block of A digits: row r owns 128
+// bytes, 16-byte slot t of them holding k = 0..15 of digit t; the slot is stored at position
+// t ^ (r % 8), so that the 32 rows a converter warp reads at once fall on different shared-memory
+// banks.
 __host__ __device__ inline uint32_t oz_a8_offset(int r, int k, int t) {
-  const int slot = 2 * t + (k >> 4);
-  return (uint32_t)(r * 256 + ((slot ^ (r & 7)) << 4) + (k & 15));
+  return (uint32_t)(r * 128 + ((t ^ (r & 7)) << 4) + k);
 }
 
 // Digits of A as bytes (digit + 128) into blocks [mtile][set][row][256 bytes] (see oz_a8_offset).
@@ -122,7 +125,7 @@ __global__ void k_oz_slice_p(int n, const double* __restrict__ P, const int* __r
 template <int KPT>
 struct OzCfg {
   static constexpr uint32_t kPChunkBytes = kOzDigits * KPT * kOzKC * 2;
-  static constexpr uint32_t kAccCols = 8 * KPT;           // the accumulator: 8 levels x KPT columns
+  static constexpr uint32_t kAccCols = kOzLevels * KPT;   // the accumulator: 9 levels x KPT columns
   static constexpr uint32_t kTmemCols = 512;              // accumulator + two converted A blocks
   static_assert(kAccCols + 2 * kAColsPerSet <= kTmemCols, "tensor memory of one CTA");
   static constexpr size_t kBarBytes = 1024;  // barriers + TMEM slot, keeps the blocks 1024-aligned
@@ -314,20 +317,19 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
         ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // tcgen05.st needs the whole warp
         if (!ok) break;
         tc_fence_after_sync();
-        const uint8_t* row = As + (size_t)q * kASetBytes + r * 256;
+        const uint8_t* row = As + (size_t)q * kASetBytes + r * 128;
         const uint32_t dst = abuf0 + (uint32_t)ab * kAColsPerSet + lane_off;
 #pragma unroll
         for (int t = 0; t < kOzDigits; ++t) {
-          const uint4 lo = *reinterpret_cast<const uint4*>(row + (((2 * t) ^ (r & 7)) << 4));
-          const uint4 hi = *reinterpret_cast<const uint4*>(row + (((2 * t + 1) ^ (r & 7)) << 4));
-          uint32_t v[16];
-          const uint32_t wd[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+          const uint4 w4 = *reinterpret_cast<const uint4*>(row + ((t ^ (r & 7)) << 4));
+          uint32_t v[8];
+          const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-          for (int q2 = 0; q2 < 8; ++q2) {
+          for (int q2 = 0; q2 < 4; ++q2) {
             v[2 * q2] = oz_f16_pair(wd[q2], 0x4140u);      // bytes 0, 1
             v[2 * q2 + 1] = oz_f16_pair(wd[q2], 0x4342u);  // bytes 2, 3
           }
-          tmem_st16(dst + (uint32_t)(16 * t), v);  // digit t: columns 16 t .. 16 t + 15 (k pairs 0..15)
+          tmem_st8(dst + (uint32_t)(8 * t), v);  // digit t: columns 8 t .. 8 t + 7 (k pairs 0..7)
         }
         tmem_wait_st();
         tc_fence_before_sync();
@@ -361,16 +363,25 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
             if (!ok) break;
             tc_fence_after_sync();
             const uint32_t a_base = abuf0 + (uint32_t)ab * kAColsPerSet;
+            const uint32_t bk = b_base + 256u * u;  // K step u of the P chunk
+            const uint64_t bdesc = umma_smem_desc(bk, 128, 1024);
+            // digit t of A with digits 0 .. min(7, 8 - t) of P: levels t .. min(t + 7, 8). The first
+            // K step of a window overwrites every level: digit 1 (levels 1..8) first, then digit 0
+            // alone into level 0, then digit 0 accumulating into levels 1..7 (digits 1..7 of P, rows
+            // KPT.. of the chunk: KPT/8 core-matrix groups further).
+            const bool first = (cc == cc0 && u == 0);
 #pragma unroll
             for (int t = 0; t < kOzDigits; ++t) {
-              const uint32_t idesc = umma_idesc_f16_f32(kOzMT, KPT * (kOzDigits - t));
-              const uint32_t d = tmem + (uint32_t)(KPT * t);
-#pragma unroll
-              for (int kk = 0; kk < kOzSetK / 16; ++kk) {
-                const int k4 = u * (kOzSetK / 16) + kk;  // K step of 16 inside the P chunk
-                const uint32_t first = (cc == cc0 && u == 0 && t == 0 && kk == 0) ? 0u : 1u;
-                umma_tmem_a(d, a_base + (uint32_t)(16 * t + 8 * kk),
-                                 umma_smem_desc(b_base + 256u * k4, 128, 1024), idesc, first);
+              const int nu = (t == 0) ? kOzDigits : kOzLevels - t;
+              if (first && t == 0) {
+                umma_tmem_a(tmem + (uint32_t)KPT, a_base + 8u, bdesc, umma_idesc_f16_f32(kOzMT, KPT * (kOzLevels - 1)),
+                            0u);
+                umma_tmem_a(tmem, a_base, bdesc, umma_idesc_f16_f32(kOzMT, KPT), 0u);
+                umma_tmem_a(tmem + (uint32_t)KPT, a_base, umma_smem_desc(bk + 1024u * (KPT / 8), 128, 1024),
+                            umma_idesc_f16_f32(kOzMT, KPT * (kOzDigits - 1)), 1u);
+              } else if (!(first && t == 1)) {
+                umma_tmem_a(tmem + (uint32_t)(KPT * t), a_base + (uint32_t)(8 * t), bdesc,
+                            umma_idesc_f16_f32(kOzMT, KPT * nu), 1u);
               }
             }
             umma_commit(&aempty[ab]);
@@ -407,25 +418,25 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
       ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // tcgen05.ld needs the whole warp
       if (!ok) break;
       const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(DC * half);
-      // two rounds of four levels: the loads of a round are in flight together (one wait each)
+      // three rounds of three levels: the loads of a round are in flight together (one wait each)
 #pragma unroll
-      for (int L0 = 0; L0 < kOzDigits; L0 += 4) {
-        uint32_t rr[4][DC];
+      for (int L0 = 0; L0 < kOzLevels; L0 += 3) {
+        uint32_t rr[3][DC];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 3; ++q) {
           if constexpr (DC == 16) tmem_ld16(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
           else tmem_ld8(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
         }
         tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 3; ++q) {
           const int L = L0 + q;
           if (L < 5) {
             const int sh = 7 * (4 - L);
 #pragma unroll
             for (int jj = 0; jj < DC; ++jj) acc_i[jj] += (long long)__float2int_rn(__uint_as_float(rr[q][jj])) << sh;
           } else {
-            const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : 0x1p-14f;
+            const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : (L == 7) ? 0x1p-14f : 0x1p-21f;
 #pragma unroll
             for (int jj = 0; jj < DC; ++jj) acc_f[jj] = fmaf(__uint_as_float(rr[q][jj]), sc, acc_f[jj]);
           }
