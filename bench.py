@@ -229,50 +229,63 @@ def launches_per_solve(info, dense, algo_cg, tc=False, mixed=False, cg_fused=Fal
 
 
 def spmm_roofline(mb, stream, flush, peak_gbs, launches=10):
-    """HBM roofline of the CSR product A P alone, in the solver's launch configuration, on the two
-    sparse workloads where HBM binds: 3D diffusion 128^3 (FP64, s = 1 and s = 4) and the 27-point
-    stencil 96^3 (FP32 blocks, s = 16). Algorithmic bytes: the CSR once (12 nnz + 4 (n + 1) in FP64,
-    8 nnz + 4 (n + 1) in FP32) plus P in and A P out (2 n KP values); L2 flushed before every
-    launch; CUDA events on the launching stream."""
+    """HBM roofline of the CSR product A P alone, by the solver's own product kernel (the one the
+    handle picked at create) through mbpcg_apply_dev, on the two sparse workloads
+    where HBM binds: 3D diffusion 128^3 (Jacobi, FP64, s = 1 and s = 4) and the 27-point stencil 96^3
+    (the FP32 product of the mixed inner solve, s = 16). Algorithmic bytes: the CSR once (12 nnz +
+    4 (n + 1) in FP64, 8 nnz + 4 (n + 1) in FP32) plus P in and A P out (2 n KP values), whichever
+    kernel runs (the tiled kernel reads 16-bit local column indices, 2 bytes per nonzero less); L2
+    flushed before every launch; CUDA events on the handle's stream."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
+    names = {mb.MBPCG_PRODUCT_CSR_GATHER: "k_spmm (gather)", mb.MBPCG_PRODUCT_CSR_TILED: "k_spmm_tiled",
+             mb.MBPCG_PRODUCT_CSR_WIDE: "k_spmm_wide_f"}
     cases = []
-    for name, gen, s, f32 in (("3D 7-point diffusion 128^3", lambda: wl.diffusion3d(128, 0), 1, False),
-                              ("3D 7-point diffusion 128^3", lambda: wl.diffusion3d(128, 0), 4, False),
-                              ("3D 27-point stencil 96^3", lambda: wl.stencil27(96, 0), 16, True)):
+    for name, gen, s, f32, precond in (("3D 7-point diffusion 128^3", lambda: wl.diffusion3d(128, 0), 1, False, 1),
+                                       ("3D 7-point diffusion 128^3", lambda: wl.diffusion3d(128, 0), 4, False, 1),
+                                       ("3D 27-point stencil 96^3", lambda: wl.stencil27(96, 0), 16, True, 0)):
         A = gen()
         n, nnz = A.n, A.nnz
         kp = mb.mbpcg_k_padded_width(s)
-        rp = torch.as_tensor(A.row_ptr, device=dev)
-        ci = torch.as_tensor(A.col_idx, device=dev)
-        dt = torch.float32 if f32 else torch.float64
-        av = torch.as_tensor(A.val, device=dev).to(dt)
-        P = torch.zeros((n, kp), dtype=dt, device=dev)
-        P[:, :s] = torch.as_tensor(wl.initial_block(n, s, 1), device=dev).to(dt)
-        AP = torch.empty_like(P)
-        if f32:
-            launch = lambda: mb.mbpcg_k_spmm_f32(n, rp, ci, av, s, P, AP, stream.cuda_stream)  # noqa: E731
-            nbytes, kname = 8.0 * nnz + 4.0 * (n + 1) + 8.0 * n * kp, f"k_spmm_f<{kp}> (FP32)"
-        else:
-            launch = lambda: mb.mbpcg_k_spmm(n, rp, ci, av, s, P, AP, stream.cuda_stream)  # noqa: E731
-            nbytes, kname = 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n * kp, f"k_spmm<{kp}> (FP64)"
-        ts = []
-        with torch.cuda.stream(stream):
-            launch()
-            for _ in range(launches):
-                flush.zero_()
-                ev0 = torch.cuda.Event(enable_timing=True)
-                ev1 = torch.cuda.Event(enable_timing=True)
-                ev0.record(stream)
-                launch()
-                ev1.record(stream)
-                ev1.synchronize()
-                ts.append(ev0.elapsed_time(ev1))
-        ms = sum(ts) / len(ts)
-        gbs = nbytes / (ms * 1e-3) / 1e9
-        cases.append({"workload": name, "n": n, "nnz": int(nnz), "s": s, "kernel": kname, "kernel_ms": round(ms, 5),
-                      "algorithmic_bytes": nbytes, "achieved": round(gbs, 1), "frac": round(gbs / peak_gbs, 4)})
-        del rp, ci, av, P, AP
+        sv = mb.Solver(A, s=s, precond=precond, precision=mb.MBPCG_MIXED_FP32 if f32 else mb.MBPCG_FP64)
+        try:
+            kernel, times64 = sv.product_kernel(fp32=f32)
+            dt = torch.float32 if f32 else torch.float64
+            P = torch.zeros((n, kp), dtype=dt, device=dev)
+            P[:, :s] = torch.as_tensor(wl.initial_block(n, s, 1), device=dev).to(dt)
+            AP = torch.empty_like(P)
+            if f32:
+                nbytes, prec = 8.0 * nnz + 4.0 * (n + 1) + 8.0 * n * kp, "FP32"
+                unroll, cps, tf = sv.spmm_tuning()
+                tuning = {"shape": [unroll, cps], "times_us": [round(t, 2) for t in tf]}
+            else:
+                nbytes, prec = 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n * kp, "FP64"
+                tuning = {"times_us_gather_tiled": [round(t, 2) for t in times64]}
+            ss = sv.stream
+            ss.wait_stream(torch.cuda.current_stream())
+            launch = lambda: mb.mbpcg_apply_dev(sv.h, 1 if f32 else 0, P, AP)  # noqa: E731
+            ts = []
+            with torch.cuda.stream(ss):
+                if launch() != 0:
+                    raise RuntimeError("mbpcg_apply_dev failed")
+                for _ in range(launches):
+                    flush.zero_()
+                    ev0 = torch.cuda.Event(enable_timing=True)
+                    ev1 = torch.cuda.Event(enable_timing=True)
+                    ev0.record(ss)
+                    launch()
+                    ev1.record(ss)
+                    ev1.synchronize()
+                    ts.append(ev0.elapsed_time(ev1))
+            ms = sum(ts) / len(ts)
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            cases.append({"workload": name, "n": n, "nnz": int(nnz), "s": s,
+                          "kernel": f"{names.get(kernel, kernel)}<{kp}> ({prec})", "autotune": tuning,
+                          "kernel_ms": round(ms, 5), "algorithmic_bytes": nbytes, "achieved": round(gbs, 1),
+                          "frac": round(gbs / peak_gbs, 4)})
+            del P, AP
+        finally:
+            sv.close()
     return {"bound": "hbm", "unit": "GB/s", "peak": peak_gbs, "cases": cases,
             "timing": f"{launches} launches, L2 flushed (256 MB write) before each, CUDA events on the stream",
             "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
@@ -281,25 +294,21 @@ def spmm_roofline(mb, stream, flush, peak_gbs, launches=10):
 def roofline_tc(n, s, kp, k_ms, single_ms, seq_ms, read_gbs, peaks, traffic, launches):
     """Roofline of k_dense_tc, the MMA kernel of the tensor-core product (k_ms: its average
     duration over `launches` back-to-back launches). Algorithmic bytes are those of the dense
-    product itself: FP64 A read once (8 n^2), P in and A P out (16 n KP). The kernel reads A as
-    8 BF16 digits per entry instead, 16 n^2 bytes: twice the algorithmic bytes, so its digit stream
-    is reported beside the roofline (bytes, GB/s, fraction of the read-only ceiling `read_gbs`)."""
+    product itself: FP64 A read once (8 n^2), P in and A P out (16 n KP). The kernel streams A as its
+    8 signed base-128 digits, one byte each (8 n^2 bytes, as many as the FP64 matrix), and the
+    digits of P; the fraction is reported against the measured copy bandwidth and against the
+    read-only ceiling `read_gbs` (a kernel that only reads)."""
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     nbytes = 8.0 * n * n + 16.0 * n * kp
-    stream_bytes = 16.0 * n * n + 16.0 * n * kp
     flops = 2.0 * n * n * s
     achieved_gbs = nbytes / (k_ms * 1e-3) / 1e9
-    stream_gbs = stream_bytes / (k_ms * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": f"k_dense_tc<{kp}> (digit stream of A + tcgen05 MMAs, the kernel alone)",
             "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved_gbs / hbm_peak, 4), "traffic": traffic,
             "kernel_ms": round(k_ms, 5), "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
             "fp64_equiv_tflops": round(flops / (k_ms * 1e-3) / 1e12, 3),
-            "digit_stream_bytes": stream_bytes, "digit_stream_gbs": round(stream_gbs, 1),
-            "digit_stream_frac_of_peak": round(stream_gbs / hbm_peak, 4),
-            "digit_stream_frac_of_read_ceiling": round(stream_gbs / read_gbs, 4),
-            "traffic_note": "DRAM bytes of one launch: the digit stream (16 B per entry of A), twice the "
-                            "algorithmic bytes by design, not re-reads",
+            "traffic_note": "DRAM bytes of one launch: A's digits (8 B per entry, the same as FP64 A) "
+                            "plus P's digits and the raw partials",
             "timing": f"{launches} back-to-back launches (digits of A > L2, no flush)",
             "kernel_ms_one_launch_l2_flushed": round(single_ms, 5),
             "product_call_ms": round(seq_ms, 5),
@@ -661,12 +670,17 @@ def oracle_sample(args, A, s, precond, iters):
     import oracle
     b = wl.rhs(A.n, 0)
     U = wl.initial_block(A.n, s, 1)
-    t0 = time.perf_counter()
-    oracle.mbpcg_state(A, b, U, 0, precond=precond, omp=True)
+    oracle.mbpcg_state(A, b, U, 1, precond=precond, omp=True)  # untimed: thread pool, first-touch pages
+    setups = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        oracle.mbpcg_state(A, b, U, 0, precond=precond, omp=True)
+        setups.append(time.perf_counter() - t0)
+    setup = min(setups)
     t1 = time.perf_counter()
     oracle.mbpcg_state(A, b, U, iters, precond=precond, omp=True)
     t2 = time.perf_counter()
-    return ((t2 - t1) - (t1 - t0)) / iters, (t1 - t0)
+    return max((t2 - t1) - setup, 0.0) / iters, setup
 
 
 def full_solve_iterations(workload, s):

@@ -163,15 +163,53 @@ typedef enum { MBPCG_RESIDUAL_EXPLICIT = 0, MBPCG_RESIDUAL_IMPLICIT = 1 } mbpcg_
 int mbpcg_set_residual_mode(mbpcg_handle h, int32_t mode);
 
 /* Autotuner of the mixed-precision inner solve (MBPCG_MIXED_FP32 CSR handles; MBPCG_ERR_INVALID
- * otherwise: the dense FP32 product has one launch shape). At create the FP32 product A P -- the dominant kernel of that solve -- is timed on the
- * handle's own matrix in six launch shapes (4 or 8 nonzeros of a row in flight per thread; 4, 8 or
- * 16 CTAs per SM; CUDA events, three launches each) and the fastest is kept. Every shape computes
- * each row the same way, so the shape changes the time, never the result.
- *   mbpcg_get_spmm_tuning: the kept shape and the six measured times (microseconds per launch, in
- *     the order (4,4) (4,8) (4,16) (8,4) (8,8) (8,16) of (unroll, ctas_per_sm); times_us may be NULL).
- *   mbpcg_set_spmm_shape: impose a shape (unroll 4 or 8, ctas_per_sm 4, 8 or 16). */
+ * otherwise: the dense FP32 product has one launch shape). At create the FP32 product A P -- the
+ * dominant kernel of that solve -- is timed on the handle's own matrix in eleven shapes, given as
+ * (variant, ctas_per_sm): the gather kernel (CTAs of 256 threads) with 4 or 8 nonzeros of a row in
+ * flight per thread and 4, 8 or 16 CTAs per SM, (4,4) (4,8) (4,16) (8,4) (8,8) (8,16); the tiled
+ * kernel, (0,2), when the matrix has a tiling plan; the wide-CTA kernel with 1024 threads, (1,1)
+ * (1,2), and with 512 threads, (2,2) (2,4) (see mbpcg_get_product_kernel). CUDA events, three
+ * launches each; the fastest is kept. Every shape sums each row the same way, so the shape changes
+ * the time, never the result.
+ *   mbpcg_get_spmm_tuning: the kept shape and the eleven measured times (microseconds per launch,
+ *     in the order above; 0 for a shape not timed; times_us may be NULL).
+ *   mbpcg_set_spmm_shape: impose one of the eleven shapes. */
 int mbpcg_get_spmm_tuning(mbpcg_handle h, int32_t* unroll, int32_t* ctas_per_sm, float* times_us);
 int mbpcg_set_spmm_shape(mbpcg_handle h, int32_t unroll, int32_t ctas_per_sm);
+
+/* The product Y = A X of the handle's matrix, as the loop applies it (Algorithm 1: the A P of each
+ * iteration). A is the stored operator: the matrix given at create, or D^-1/2 A D^-1/2 under
+ * MBPCG_PRECOND_JACOBI. X and Y are device blocks of n rows x w columns, row-major, w the padded
+ * block width (mbpcg_k_padded_width(s); 1 for MBPCG_ALGO_CG handles); FP64, or FP32 when fp32 != 0
+ * (MBPCG_MIXED_FP32 handles only: the product of the inner solve). The caller owns both; X and Y
+ * must not overlap. Enqueued on the handle's stream; returns without waiting. Uses the handle's
+ * scratch (not to be called while a solve of the same handle runs on another thread). */
+int mbpcg_apply_dev(mbpcg_handle h, int32_t fp32, const void* X, void* Y);
+
+/* Which kernel forms the product (fp32 = 0: the FP64 product; 1: the FP32 product of a mixed
+ * handle). CSR kernels: CSR_GATHER, each thread walks its row's nonzeros and gathers rows of P
+ * through the caches (the FP64 product of the loop); CSR_WIDE (FP32 only), the same with CTAs of
+ * 512 or 1024 threads, so that the rows an SM has in flight are few contiguous ranges whose rows of
+ * P stay in L1; CSR_TILED, for CSR matrices of at least 65,536 rows whose tiles' columns fit a
+ * shared-memory window (a plan built at create), the rows of P a tile reads are staged in shared
+ * memory once and the nonzeros address them by 16-bit local indices. All sum each row in the order
+ * of its nonzeros: A P is the same bits whichever runs; TILED groups the loop's Gram partials by
+ * tile (other rounding). For FP64, GATHER and (with a plan) TILED are timed at create on the
+ * handle's own matrix, with the loop's Gram, for the record -- times_us (may be NULL) receives the
+ * two measured microseconds per launch, 0 when not timed -- and GATHER is kept, so a solve's result
+ * never depends on a timing. For FP32 the autotuner of mbpcg_get_spmm_tuning picks among all.
+ * mbpcg_set_product_kernel imposes the FP64 kernel of a CSR handle (CSR_TILED needs a plan; mixed
+ * handles have none for FP64). */
+typedef enum {
+  MBPCG_PRODUCT_CSR_GATHER = 0,
+  MBPCG_PRODUCT_CSR_TILED = 1,
+  MBPCG_PRODUCT_CSR_WIDE = 2,
+  MBPCG_PRODUCT_DENSE = 3,
+  MBPCG_PRODUCT_DENSE_TC = 4,
+  MBPCG_PRODUCT_DENSE_FP32 = 5
+} mbpcg_product_kernel;
+int mbpcg_get_product_kernel(mbpcg_handle h, int32_t fp32, int32_t* kernel, float* times_us);
+int mbpcg_set_product_kernel(mbpcg_handle h, int32_t kernel);
 
 /* Release a handle (NULL is ignored). */
 void mbpcg_destroy(mbpcg_handle h);

@@ -18,7 +18,9 @@ from ._native import (  # noqa: F401  (re-exported C ABI names)
     MBPCG_ALGO_CG, MBPCG_FP64, MBPCG_FP64_TC, MBPCG_MIXED_FP32, MBPCG_LAUNCH_GRAPH, MBPCG_LAUNCH_EAGER,
     mbpcg_k_spmm_gram_f32, mbpcg_k_spmm_f32, mbpcg_k_dense_f32, mbpcg_k_dense_f32_bytes, mbpcg_k_dense_f32_prepare,
     mbpcg_set_residual_mode, MBPCG_RESIDUAL_EXPLICIT,
-    MBPCG_RESIDUAL_IMPLICIT, mbpcg_get_spmm_tuning, mbpcg_set_spmm_shape)
+    MBPCG_RESIDUAL_IMPLICIT, mbpcg_get_spmm_tuning, mbpcg_set_spmm_shape, mbpcg_apply_dev, mbpcg_get_product_kernel,
+    mbpcg_set_product_kernel, MBPCG_PRODUCT_CSR_GATHER, MBPCG_PRODUCT_CSR_TILED, MBPCG_PRODUCT_CSR_WIDE, MBPCG_PRODUCT_DENSE,
+    MBPCG_PRODUCT_DENSE_TC, MBPCG_PRODUCT_DENSE_FP32)
 
 from ._native import (  # noqa: F401,E402
     mbpcg_server_create, mbpcg_server_destroy, mbpcg_server_get_stats, mbpcg_server_submit_csr, mbpcg_server_wait)
@@ -143,6 +145,28 @@ class Solver:
         st = mbpcg_set_spmm_shape(self.h, unroll, ctas_per_sm)
         if st != MBPCG_OK:
             raise MBPCGError(st, "mbpcg_set_spmm_shape")
+
+    def product_kernel(self, fp32: bool = False):
+        """(kernel, [gather_us, tiled_us]): the MBPCG_PRODUCT_* kernel of the FP64 (or FP32) product
+        and the FP64 times measured at create."""
+        return mbpcg_get_product_kernel(self.h, 1 if fp32 else 0)
+
+    def set_product_kernel(self, kernel: int):
+        st = mbpcg_set_product_kernel(self.h, kernel)
+        if st != MBPCG_OK:
+            raise MBPCGError(st, "mbpcg_set_product_kernel")
+
+    def apply(self, X, fp32: bool = False):
+        """A X for a device block X (n x w, w the padded width), by the handle's own product kernel.
+        A is the stored operator (scaled under Jacobi). Waits for the result."""
+        import torch
+        Y = torch.empty_like(X)
+        self.stream.wait_stream(torch.cuda.current_stream(X.device))
+        st = mbpcg_apply_dev(self.h, 1 if fp32 else 0, X, Y)
+        if st != MBPCG_OK:
+            raise MBPCGError(st, "mbpcg_apply_dev")
+        self.stream.synchronize()
+        return Y
 
     def run_iterations(self, b, U, iters: int):
         """Diagnostic: the state of the scaled system after exactly `iters` iterations, as torch

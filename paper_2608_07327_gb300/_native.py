@@ -28,6 +28,12 @@ MBPCG_LAUNCH_GRAPH = 0
 MBPCG_LAUNCH_EAGER = 1
 MBPCG_RESIDUAL_EXPLICIT = 0
 MBPCG_RESIDUAL_IMPLICIT = 1
+MBPCG_PRODUCT_CSR_GATHER = 0
+MBPCG_PRODUCT_CSR_TILED = 1
+MBPCG_PRODUCT_CSR_WIDE = 2
+MBPCG_PRODUCT_DENSE = 3
+MBPCG_PRODUCT_DENSE_TC = 4
+MBPCG_PRODUCT_DENSE_FP32 = 5
 
 
 class Info(ctypes.Structure):
@@ -94,6 +100,9 @@ _SIGS = {
     "mbpcg_get_spmm_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                              ctypes.POINTER(ctypes.c_float)]),
     "mbpcg_set_spmm_shape": (ctypes.c_int, [_P, _I32, _I32]),
+    "mbpcg_apply_dev": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "mbpcg_get_product_kernel": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]),
+    "mbpcg_set_product_kernel": (ctypes.c_int, [_P, _I32]),
     "mbpcg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mbpcg_last_error": (ctypes.c_char_p, []),
     "mbpcg_k_padded_width": (_I32, [_I32]),
@@ -344,9 +353,11 @@ def mbpcg_set_residual_mode(h, mode):
 
 
 def mbpcg_get_spmm_tuning(h):
-    """(unroll, ctas_per_sm, [six measured microseconds]) of a mixed-precision handle's FP32 A P."""
+    """(variant, ctas_per_sm, [eleven measured microseconds]) of a mixed-precision handle's FP32 A P
+    (variant 4 or 8: the gather kernel; 0: the tiled kernel; 1, 2: the wide-CTA kernel with 1024 or
+    512 threads; 0 us: not timed)."""
     u, c = _I32(), _I32()
-    t = (ctypes.c_float * 6)()
+    t = (ctypes.c_float * 11)()
     st = lib().mbpcg_get_spmm_tuning(h, ctypes.byref(u), ctypes.byref(c), t)
     if st != MBPCG_OK:
         raise MBPCGError(st, "mbpcg_get_spmm_tuning")
@@ -355,3 +366,21 @@ def mbpcg_get_spmm_tuning(h):
 
 def mbpcg_set_spmm_shape(h, unroll, ctas_per_sm):
     return lib().mbpcg_set_spmm_shape(h, unroll, ctas_per_sm)
+
+
+def mbpcg_apply_dev(h, fp32, X, Y):
+    return lib().mbpcg_apply_dev(h, fp32, ptr(X), ptr(Y))
+
+
+def mbpcg_get_product_kernel(h, fp32=0):
+    """(kernel, [gather_us, tiled_us]) of a handle's product (MBPCG_PRODUCT_* codes)."""
+    k = _I32()
+    t = (ctypes.c_float * 2)()
+    st = lib().mbpcg_get_product_kernel(h, fp32, ctypes.byref(k), t)
+    if st != MBPCG_OK:
+        raise MBPCGError(st, "mbpcg_get_product_kernel")
+    return int(k.value), [float(x) for x in t]
+
+
+def mbpcg_set_product_kernel(h, kernel):
+    return lib().mbpcg_set_product_kernel(h, kernel)

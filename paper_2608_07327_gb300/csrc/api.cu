@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 #include <new>
 #include <string>
 
@@ -41,10 +42,14 @@ int set_err(int code, const char* fmt, ...) {
 
 constexpr size_t kAlign = 256;
 constexpr int kMixedRestarts = 12;       // refinement steps of the mixed-precision solve
-constexpr int kTuneVariants = 6;         // FP32 A P launch shapes tried by the autotuner
+constexpr int kTuneVariants = 11;        // FP32 A P launch shapes tried by the autotuner
+constexpr int kTiledMinRows = 65536;     // smaller systems sit in L2 and keep the gather kernel
 constexpr double kMixedInnerTol = 1e-5;  // smallest relative tolerance asked of an FP32 inner solve
 constexpr int kBodyUnroll = 4;           // loop iterations per pass of the graph's WHILE node
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+// Runs of staged rows the workspace holds for a CSR plan (a stencil needs a few per tile; a
+// matrix that needs more keeps the gather kernel).
+inline size_t plan_runs_cap(long long nnz) { return (size_t)(nnz / 8 > 1024 ? nnz / 8 : 1024); }
 
 struct Dims {
   int n, kp, nb, nb_dense, nbmax, pstride;
@@ -73,9 +78,13 @@ Dims make_dims(int n, long long nnz, int s, int algo, int dense, int sms) {
   // row kernels: at most 2 CTAs per SM, and at least 8 rows per CTA at KP = 32 (the FP64 block
   // updates are bound by the FP64 pipe and gain from more CTAs: dense n = 4096, s = 32, 157 against
   // 162 us per iteration) or 32 rows below (latency-bound: Poisson n = 4096, s = 4, 38 against 41)
+  // Sparse systems: up to 8 CTAs per SM -- the CSR product and the row passes of a large sparse
+  // system are bound by memory latency and bandwidth (diffusion 128^3, s = 1: the product takes 76 us
+  // with 2 CTAs per SM, a latency chain per row with 16 warps per SM).
   const int rows_per_cta = d.kp >= 32 ? 8 : 32;
+  const long long cap = dense ? 2LL * sm : 8LL * sm;
   long long want = ((long long)n + rows_per_cta - 1) / rows_per_cta;
-  d.nb = (int)(want < 2LL * sm ? (want > 0 ? want : 1) : 2LL * sm);
+  d.nb = (int)(want < cap ? (want > 0 ? want : 1) : cap);
   long long wd = ((long long)n + 7) / 8;
   d.nb_dense = (int)(wd < sm ? (wd > 0 ? wd : 1) : sm);
   d.nbmax = d.nb > d.nb_dense ? d.nb : d.nb_dense;
@@ -114,6 +123,7 @@ struct Layout {
   size_t A32;                            // mixed precision, dense A: FP32 tiles (dense_f32_tiles_bytes)
   size_t xbest;                          // mixed precision: best iterate of the refinement loop
   size_t rp3;                            // tensor-core k x k-row products: 3 blocks n x KP (KP >= 16)
+  size_t pl_cl, pl_rptr, pl_runs;        // CSR: the tiled product's plan (local columns, tiles, runs)
   size_t total;
 };
 
@@ -140,6 +150,9 @@ Layout make_layout(const Dims& dm) {
     L.rp = take((n + 1) * sizeof(int));
     L.ci = take((size_t)dm.nnz * sizeof(int));
     L.av = take((size_t)dm.nnz * sizeof(double));
+    L.pl_cl = take((size_t)dm.nnz * sizeof(uint16_t));
+    L.pl_rptr = take((n / 32 + 2) * sizeof(int));
+    L.pl_runs = take(2 * plan_runs_cap(dm.nnz) * sizeof(int));
     if (dm.mixed) {
       L.av32 = take((size_t)dm.nnz * sizeof(float));
       L.wd32 = take(n * sizeof(float));
@@ -232,8 +245,12 @@ struct mbpcg_ctx {
   int rfree;        // MBPCG_RESIDUAL_IMPLICIT: R = W Sigma is not formed inside the loop
   // launch shape of the FP32 A P of the mixed inner solve, picked by autotune_spmm_f at create
   int spmm_unroll, spmm_ctas_per_sm, spmm_nb;
-  float spmm_us[kTuneVariants];
+  float spmm_us[kTuneVariants];  // the measured shapes (0: not timed)
   int use_cond;     // 1 while the loop body is captured into the WHILE node
+  SpmmPlan plan;    // CSR: rows of P staged per tile (see spmm_tiled.cu)
+  int use_tiled;    // 1: the matrix has a tiling plan
+  int prod64;       // the FP64 CSR product kernel: MBPCG_PRODUCT_CSR_GATHER or _TILED
+  float spmm64_us[2];  // the FP64 product at create: gather and tiled kernels (0: not timed)
   cudaEvent_t e0, e1;
 };
 
@@ -407,21 +424,42 @@ int spmm_grid(const Dims& dm, int ctas_per_sm) {
   return (int)(tiles < cap ? tiles : cap);
 }
 
-// Autotuner of the FP32 A P (the dominant kernel of the mixed inner solve): times every launch shape
-// (unroll 4 or 8 nonzeros in flight, 4, 8 or 16 CTAs per SM) on this handle's own matrix, three
-// launches each after one untimed, and keeps the fastest. Every shape computes each row the same
-// way, so the choice changes the time, never the result.
-int autotune_spmm_f(mbpcg_ctx* h) {
+// FP32 A P launch shapes tried by the autotuner, as (variant, CTAs per SM): variant 4 or 8 is the
+// gather kernel (CTAs of 256 threads) with that many nonzeros of a row in flight per thread; 1 and
+// 2 the wide-CTA kernel (spmm_wide.cu) with 1024 and 512 threads per CTA; 0 the tiled kernel
+// (spmm_tiled.cu; rows of P staged per tile, two CTAs per SM, only with a tiling plan).
+constexpr int kShapeUnroll[kTuneVariants] = {4, 4, 4, 8, 8, 8, 0, 1, 1, 2, 2};
+constexpr int kShapeCtas[kTuneVariants] = {4, 8, 16, 4, 8, 16, 2, 1, 2, 2, 4};
+
+int shape_grid(const mbpcg_ctx* h, int unroll, int ctas_per_sm) {
+  if (unroll == 0) return std::min(h->plan.ntiles, 2 * h->dm.sms);
+  if (unroll <= 2) {  // wide CTAs: 4 or 2 times the rows of a 256-thread CTA's pass
+    const long long rows = (long long)rows_per_tile_f(h->dm.kp) * (unroll == 1 ? 4 : 2);
+    const long long want = (h->dm.n + rows - 1) / rows, cap = (long long)ctas_per_sm * h->dm.sms;
+    return (int)std::max(1LL, std::min(want, cap));
+  }
+  return spmm_grid(h->dm, ctas_per_sm);
+}
+
+void launch_spmm_f(mbpcg_ctx* h, int unroll, int nb, const float* X, float* Y, const SolveState* st) {
   const Dims& dm = h->dm;
-  const RowOpsF* ops = row_ops_f(dm.kp);
-  static const int unr[kTuneVariants] = {4, 4, 4, 8, 8, 8}, cps[kTuneVariants] = {4, 8, 16, 4, 8, 16};
+  if (unroll == 0) spmm_tiled_f(h->stream, dm.kp, nb, dm.n, h->rp, h->av32, h->plan, X, Y, st);
+  else if (unroll <= 2) spmm_wide_f(h->stream, dm.kp, unroll == 1 ? 1024 : 512, nb, dm.n, h->rp, h->ci, h->av32, X, Y, st);
+  else row_ops_f(dm.kp)->spmm(h->stream, nb, dm.n, h->rp, h->ci, h->av32, X, Y, nullptr, 0, st, 0, unroll);
+}
+
+// Autotuner of the FP32 A P (the dominant kernel of the mixed inner solve): times every shape above
+// on this handle's own matrix, three launches each after one untimed, and keeps the fastest. Every
+// shape sums each row in the order of its nonzeros, so the choice changes the time, never the result.
+int autotune_spmm_f(mbpcg_ctx* h) {
   float best = 1e30f;
   for (int v = 0; v < kTuneVariants; ++v) {
-    const int nb = spmm_grid(dm, cps[v]);
-    ops->spmm(h->stream, nb, dm.n, h->rp, h->ci, h->av32, h->fU, h->fQ, nullptr, 0, nullptr, 0, unr[v]);
+    h->spmm_us[v] = 0.f;
+    if (kShapeUnroll[v] == 0 && !h->use_tiled) continue;
+    const int nb = shape_grid(h, kShapeUnroll[v], kShapeCtas[v]);
+    launch_spmm_f(h, kShapeUnroll[v], nb, h->fU, h->fQ, nullptr);
     CUDA_TRY(cudaEventRecord(h->e0, h->stream));
-    for (int r = 0; r < 3; ++r)
-      ops->spmm(h->stream, nb, dm.n, h->rp, h->ci, h->av32, h->fU, h->fQ, nullptr, 0, nullptr, 0, unr[v]);
+    for (int r = 0; r < 3; ++r) launch_spmm_f(h, kShapeUnroll[v], nb, h->fU, h->fQ, nullptr);
     CUDA_TRY(cudaEventRecord(h->e1, h->stream));
     CUDA_TRY(cudaEventSynchronize(h->e1));
     float ms = 0.f;
@@ -429,11 +467,85 @@ int autotune_spmm_f(mbpcg_ctx* h) {
     h->spmm_us[v] = ms * 1e3f / 3.f;
     if (h->spmm_us[v] < best) {
       best = h->spmm_us[v];
-      h->spmm_unroll = unr[v];
-      h->spmm_ctas_per_sm = cps[v];
+      h->spmm_unroll = kShapeUnroll[v];
+      h->spmm_ctas_per_sm = kShapeCtas[v];
       h->spmm_nb = nb;
     }
   }
+  return MBPCG_OK;
+}
+
+// The tiled product's plan (spmm_tiled.cu) for a validated CSR matrix of at least kTiledMinRows
+// rows, when every tile's window fits and the runs fit the workspace; otherwise the handle keeps
+// the gather kernel. The structure is read on the host (copied back when it was given on the device).
+int build_plan(mbpcg_ctx* h, const int* row_ptr, const int* col_idx, int mem) {
+  const Dims& dm = h->dm;
+  h->use_tiled = 0;
+  if (dm.n < kTiledMinRows || dm.nnz < 1) return MBPCG_OK;
+  std::vector<int> rp_h, ci_h;
+  const int* rp = row_ptr;
+  const int* ci = col_idx;
+  if (mem) {
+    rp_h.resize((size_t)dm.n + 1);
+    ci_h.resize((size_t)dm.nnz);
+    CUDA_TRY(cudaMemcpyAsync(rp_h.data(), h->rp, rp_h.size() * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(ci_h.data(), h->ci, ci_h.size() * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    rp = rp_h.data();
+    ci = ci_h.data();
+  }
+  SpmmPlanHost ph;
+  if (!spmm_plan_build(dm.n, rp, ci, dm.kp, dm.mixed ? sizeof(float) : sizeof(double), &ph)) return MBPCG_OK;
+  if (ph.run_start.size() > plan_runs_cap(dm.nnz) || ph.ntiles + 1 > dm.n / 32 + 2) return MBPCG_OK;
+  int* rptr = at<int>(h, h->L.pl_rptr);
+  int* runs = at<int>(h, h->L.pl_runs);
+  uint16_t* cl = at<uint16_t>(h, h->L.pl_cl);
+  const size_t nr = ph.run_start.size();
+  CUDA_TRY(cudaMemcpyAsync(rptr, ph.run_ptr.data(), ph.run_ptr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(runs, ph.run_start.data(), nr * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(runs + nr, ph.run_len.data(), nr * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(cl, ph.cl.data(), ph.cl.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+  h->plan.R = ph.R;
+  h->plan.ntiles = ph.ntiles;
+  h->plan.wmax = ph.wmax;
+  h->plan.run_ptr = rptr;
+  h->plan.run_start = runs;
+  h->plan.run_len = runs + nr;
+  h->plan.cl = cl;
+  h->use_tiled = 1;
+  return MBPCG_OK;
+}
+
+// The FP64 CSR product of the loop (with the Gram partials for MBPCG, as the loop launches it) timed
+// with the gather kernel and, with a plan, the tiled kernel on the handle's own matrix, for the
+// record (mbpcg_get_product_kernel). Both sum each row of A P in the same order (the same bits); the
+// tiled kernel groups the Gram partials by tile (other rounding). The gather kernel stays the
+// loop's product -- it was the faster on every stencil measured, and a solve's result must not
+// depend on a timing -- and the tiled kernel runs only when imposed (mbpcg_set_product_kernel).
+void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y, int gram, const SolveState* st);
+
+int autotune_spmm64(mbpcg_ctx* h) {
+  const Dims& dm = h->dm;
+  const RowOps* ops = row_ops(dm.kp);
+  const int gram = h->algo == MBPCG_ALGO_MBPCG ? 1 : 0;
+  const double* X = gram ? h->P : h->r;
+  double* Y = gram ? h->Q : h->w;
+  CUDA_TRY(cudaMemsetAsync((void*)X, 0, (size_t)dm.n * dm.kp * sizeof(double), h->stream));
+  for (int v : {MBPCG_PRODUCT_CSR_GATHER, MBPCG_PRODUCT_CSR_TILED}) {
+    h->spmm64_us[v] = 0.f;
+    if (v == MBPCG_PRODUCT_CSR_TILED && !h->use_tiled) continue;
+    h->prod64 = v;
+    enqueue_product(h, ops, X, Y, gram, nullptr);
+    CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+    for (int r = 0; r < 3; ++r) enqueue_product(h, ops, X, Y, gram, nullptr);
+    CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    CUDA_TRY(cudaEventSynchronize(h->e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, h->e0, h->e1));
+    h->spmm64_us[v] = ms * 1e3f / 3.f;
+  }
+  h->prod64 = MBPCG_PRODUCT_CSR_GATHER;
   return MBPCG_OK;
 }
 
@@ -477,6 +589,11 @@ int finish_create(mbpcg_ctx* h) {
       if (rc) return rc;
     }
   }
+  // (a mixed handle's loop has no FP64 product: mbpcg_apply_dev alone reaches it, by the gather kernel)
+  if (!h->dm.dense && !h->dm.mixed) {
+    int rc = autotune_spmm64(h);
+    if (rc) return rc;
+  }
   if (h->dm.cg_fused) CUDA_TRY(cg_dense_configure(n, h->dm.nb_cg));
   if (h->dm.tc) {
     oz_prepare_a(h->stream, n, h->A, h->oz_ea, h->oz_a);
@@ -498,6 +615,8 @@ void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y
   } else if (dm.dense) {
     ops->dense(h->stream, dm.nb_dense, dm.n, h->A, X, Y, st, &h->st->kerr);
     if (gram) ops->gram(h->stream, dm.nb, dm.n, X, Y, h->part, dm.pstride, st);
+  } else if (h->prod64 == MBPCG_PRODUCT_CSR_TILED) {
+    spmm_tiled(h->stream, dm.kp, dm.nb, dm.n, h->rp, h->av, h->plan, X, Y, h->part, dm.pstride, st, gram);
   } else {
     ops->spmm(h->stream, dm.nb, dm.n, h->rp, h->ci, h->av, X, Y, h->part, dm.pstride, st, gram);
   }
@@ -585,7 +704,7 @@ void enqueue_mbpcg_exit(mbpcg_ctx* h) {
 void enqueue_product_f(mbpcg_ctx* h, const RowOpsF* ops, const float* X, float* Y, const SolveState* st) {
   const Dims& dm = h->dm;
   if (dm.dense) dense_f32_product(h->stream, dm.kp, dm.n, dm.sms, h->A32, X, Y, st);
-  else ops->spmm(h->stream, h->spmm_nb, dm.n, h->rp, h->ci, h->av32, X, Y, nullptr, 0, st, 0, h->spmm_unroll);
+  else launch_spmm_f(h, h->spmm_unroll, h->spmm_nb, X, Y, st);
 }
 
 void enqueue_mbpcg_setup_f(mbpcg_ctx* h) {
@@ -931,6 +1050,7 @@ int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* r
   int flag = 0;
   rc = read_flag(h, &flag);
   if (!rc && (flag & 1)) rc = set_err(MBPCG_ERR_INVALID, "malformed CSR (row_ptr or col_idx out of range)");
+  if (!rc) rc = build_plan(h, row_ptr, col_idx, mem);
   if (!rc) rc = finish_create(h);
   if (rc) {
     release(h);
@@ -1026,12 +1146,61 @@ int mbpcg_get_spmm_tuning(mbpcg_handle h, int32_t* unroll, int32_t* ctas_per_sm,
   return MBPCG_OK;
 }
 
+int mbpcg_apply_dev(mbpcg_handle h, int32_t fp32, const void* X, void* Y) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (!X || !Y) return set_err(MBPCG_ERR_INVALID, "null block");
+  if (fp32 && !h->dm.mixed) return set_err(MBPCG_ERR_INVALID, "the FP32 product belongs to MBPCG_MIXED_FP32 handles");
+  if (fp32) {
+    enqueue_product_f(h, row_ops_f(h->dm.kp), static_cast<const float*>(X), static_cast<float*>(Y), nullptr);
+  } else {
+    const Dims& dm = h->dm;
+    if (dm.dense && !dm.tc) row_ops(dm.kp)->dense(h->stream, dm.nb_dense, dm.n, h->A, static_cast<const double*>(X),
+                                                  static_cast<double*>(Y), nullptr, nullptr);
+    else enqueue_product(h, row_ops(dm.kp), static_cast<const double*>(X), static_cast<double*>(Y), 0, nullptr);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+int mbpcg_get_product_kernel(mbpcg_handle h, int32_t fp32, int32_t* kernel, float* times_us) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (fp32 && !h->dm.mixed) return set_err(MBPCG_ERR_INVALID, "the FP32 product belongs to MBPCG_MIXED_FP32 handles");
+  int k;
+  if (h->dm.dense) k = fp32 ? MBPCG_PRODUCT_DENSE_FP32 : (h->dm.tc ? MBPCG_PRODUCT_DENSE_TC : MBPCG_PRODUCT_DENSE);
+  else if (fp32) k = h->spmm_unroll == 0 ? MBPCG_PRODUCT_CSR_TILED
+                   : (h->spmm_unroll <= 2 ? MBPCG_PRODUCT_CSR_WIDE : MBPCG_PRODUCT_CSR_GATHER);
+  else k = h->prod64;
+  if (kernel) *kernel = k;
+  if (times_us)
+    for (int v = 0; v < 2; ++v) times_us[v] = h->spmm64_us[v];
+  return MBPCG_OK;
+}
+
+int mbpcg_set_product_kernel(mbpcg_handle h, int32_t kernel) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (h->dm.dense) return set_err(MBPCG_ERR_INVALID, "a dense handle has one FP64 product");
+  if (kernel != MBPCG_PRODUCT_CSR_GATHER && kernel != MBPCG_PRODUCT_CSR_TILED)
+    return set_err(MBPCG_ERR_INVALID, "kernel must be MBPCG_PRODUCT_CSR_GATHER or MBPCG_PRODUCT_CSR_TILED");
+  if (kernel == MBPCG_PRODUCT_CSR_TILED && (!h->use_tiled || h->dm.mixed))
+    return set_err(MBPCG_ERR_INVALID, "this handle's FP64 product has no tiling plan");
+  if (h->graph_ready && kernel != h->prod64) {  // the captured launches change
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->exec);
+    h->graph_ready = 0;
+  }
+  h->prod64 = kernel;
+  return MBPCG_OK;
+}
+
 int mbpcg_set_spmm_shape(mbpcg_handle h, int32_t unroll, int32_t ctas_per_sm) {
   if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
   if (!h->dm.mixed || h->dm.dense)
     return set_err(MBPCG_ERR_INVALID, "the FP32 sparse product is tuned for MBPCG_MIXED_FP32 CSR handles");
-  if ((unroll != 4 && unroll != 8) || (ctas_per_sm != 4 && ctas_per_sm != 8 && ctas_per_sm != 16))
-    return set_err(MBPCG_ERR_INVALID, "unroll must be 4 or 8 and ctas_per_sm 4, 8 or 16");
+  bool known = false;
+  for (int v = 0; v < kTuneVariants; ++v) known = known || (kShapeUnroll[v] == unroll && kShapeCtas[v] == ctas_per_sm);
+  if (!known)
+    return set_err(MBPCG_ERR_INVALID, "unroll 4, 8 (gather) or 1 (staged) with ctas_per_sm 4, 8 or 16; or 0 and 2 (tiled)");
+  if (unroll == 0 && !h->use_tiled) return set_err(MBPCG_ERR_INVALID, "this matrix has no tiling plan");
   if (h->graph_ready) {  // the captured launches change
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     cudaGraphExecDestroy(h->exec);
@@ -1039,7 +1208,7 @@ int mbpcg_set_spmm_shape(mbpcg_handle h, int32_t unroll, int32_t ctas_per_sm) {
   }
   h->spmm_unroll = unroll;
   h->spmm_ctas_per_sm = ctas_per_sm;
-  h->spmm_nb = spmm_grid(h->dm, ctas_per_sm);
+  h->spmm_nb = shape_grid(h, unroll, ctas_per_sm);
   return MBPCG_OK;
 }
 

@@ -1,6 +1,9 @@
 // Internal interface between the host runtime (api.cu) and the kernels.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
 
 #include "mbpcg_device.cuh"
 
@@ -143,6 +146,35 @@ __global__ void k_cg_dots(int n, const double* r, const double* w, const double*
 __global__ void k_cg_update(int n, double* r, const double* w, double* x, double* p, double* sv,
                             const SolveState* st);
 __global__ void k_cg_finish(int n, const double* xbar, const double* d, double* x);
+
+// CSR product with the rows of P each tile needs staged in shared memory (spmm_tiled.cu). A plan
+// cuts the rows into tiles of R rows; run q of tile t is rows [run_start[q], +run_len[q]) of P,
+// runs run_ptr[t] .. run_ptr[t+1]-1; cl[p] is the position of nonzero p's column in its tile's
+// window (wmax: the largest window, in rows).
+struct SpmmPlan {
+  int R, ntiles, wmax;
+  const int* run_ptr;
+  const int* run_start;
+  const int* run_len;
+  const uint16_t* cl;
+};
+struct SpmmPlanHost {
+  int R = 0, ntiles = 0, wmax = 0;
+  std::vector<int> run_ptr, run_start, run_len;
+  std::vector<uint16_t> cl;
+};
+size_t spmm_plan_window_rows(int kp, size_t elem);
+// Builds the plan from host CSR arrays (validated); 0 when no tile size lets every window fit.
+int spmm_plan_build(int n, const int* rp, const int* ci, int kp, size_t elem, SpmmPlanHost* out);
+size_t spmm_plan_smem(int kp, size_t elem, int wmax);
+// The FP32 product with CTAs of `threads` (512 or 1024) threads (spmm_wide.cu): the same bits as
+// the gather kernel.
+void spmm_wide_f(cudaStream_t s, int kp, int threads, int nb, int n, const int* rp, const int* ci, const float* av,
+                 const float* P, float* Q, const SolveState* st);
+void spmm_tiled(cudaStream_t s, int kp, int nb, int n, const int* rp, const double* av, const SpmmPlan& pl,
+                const double* P, double* Q, double* part, int pstride, const SolveState* st, int gram);
+void spmm_tiled_f(cudaStream_t s, int kp, int nb, int n, const int* rp, const float* av, const SpmmPlan& pl,
+                  const float* P, float* Q, const SolveState* st);
 
 // Chronopoulos-Gear CG on a dense A, one launch per iteration (cg_dense.cu). r, w and s in two
 // copies (by the parity of the iteration), p and x in one; counter: one zeroed unsigned int.

@@ -46,7 +46,7 @@ constexpr int kOzSetK = 16;                            // reduction index per bl
 constexpr int kOzSetsPerChunk = kOzKC / kOzSetK;
 constexpr uint32_t kASetBytes = kOzMT * kOzSetK * kOzDigits;  // 16 KB: 128 rows x 16 l x 8 digit bytes
 constexpr int kOzAStages = 6;                          // A blocks in flight (shared memory)
-constexpr int kOzPBufs = 3;                            // P digit chunks in flight
+constexpr int kOzPBufs = 4;                            // P digit chunks in flight
 constexpr uint32_t kAColsPerSet = kOzDigits * kOzSetK / 2;  // TMEM columns of one converted block (64)
 constexpr int kOzLevels = 9;                           // digit-pair levels t + u = 0..8 kept
 
@@ -133,13 +133,14 @@ struct OzCfg {
 };
 static_assert(OzCfg<32>::kSmem <= 227 * 1024, "shared memory of one CTA");
 
-constexpr int kOzDrainWarps = 8;     // warps 0..7: lane quarter w % 4, column half w / 4 of the accumulator
-constexpr int kOzConvWarps = 4;      // warps 8..11: lane quarter w % 4, A digits -> FP16 in TMEM
-constexpr int kOzProducerWarp = 12;  // TMA issue of the A digit blocks
-constexpr int kOzMmaWarp = 13;       // MMA issue
-constexpr int kOzPProducerWarp = 14; // TMA issue of the P digit chunks (its own thread, so that a
+constexpr int kOzDrainGroups = 4;    // drain warps per TMEM lane quarter (each a quarter of the columns)
+constexpr int kOzDrainWarps = 4 * kOzDrainGroups;  // warps 0..15: lane quarter w % 4, columns group w / 4
+constexpr int kOzConvWarps = 4;      // warps 16..19: lane quarter w % 4, A digits -> FP16 in TMEM
+constexpr int kOzProducerWarp = 20;  // TMA issue of the A digit blocks
+constexpr int kOzMmaWarp = 21;       // MMA issue
+constexpr int kOzPProducerWarp = 22; // TMA issue of the P digit chunks (its own thread, so that a
                                      // chunk is requested as soon as a buffer is free)
-constexpr int kOzTcThreads = 32 * 15;
+constexpr int kOzTcThreads = 32 * 23;
 
 // Work split (stream-K over windows). The product is nM row tiles x nW windows of wl chunks each
 // (wl = 2: one exact window of 128 values of l; wl = 1 for small n). The U = nM nW windows, tile
@@ -164,9 +165,10 @@ __device__ __forceinline__ uint32_t oz_f16_pair(uint32_t w, uint32_t sel) {
 }
 
 // Raw partial sums of one slice of the product: int64 levels 0..4 (units 2^-42 of the row and
-// column scales) and FP32 levels 5..7 (units 2^-49), [slice][row][KP] each; the split sum turns
-// them into FP64 once per output (FP64 instructions are scarce on this GPU: converting in the
-// MMA kernel held its SMs' FP64 units for the last ~5 us of the product).
+// column scales) and FP32 levels 5..8 (units 2^-49), [slice][column][row] each, so that the 32
+// rows of a drain warp store 32 consecutive values; the split sum turns them into FP64 once per
+// output (FP64 instructions are scarce on this GPU: converting in the MMA kernel held its SMs'
+// FP64 units for the last ~5 us of the product).
 struct OzPart {
   long long* qi;
   float* qf;
@@ -302,7 +304,7 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
       }
     }
   } else if (warp >= kOzDrainWarps && warp < kOzDrainWarps + kOzConvWarps) {
-    // converters: thread = row 32 (warp % 4) + lane of the M tile (warps 8..11: quarters 0..3)
+    // converters: thread = row 32 (warp % 4) + lane of the M tile (warps 16..19: quarters 0..3)
     const int r = 32 * (warp & 3) + lane;
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     bool ok = true;
@@ -402,8 +404,8 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
   } else if (warp < kOzDrainWarps) {
     // drain warps 0..7: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of this M tile) and the
     // column half w / 4 (DC = KPT / 2 columns) of every level
-    constexpr int DC = KPT / 2;
-    const int half = warp >> 2;
+    constexpr int DC = KPT / kOzDrainGroups;
+    const int half = warp >> 2;  // column group of this warp
     long long acc_i[DC];
     float acc_f[DC];
 #pragma unroll
@@ -418,45 +420,54 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
       ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // tcgen05.ld needs the whole warp
       if (!ok) break;
       const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(DC * half);
-      // three rounds of three levels: the loads of a round are in flight together (one wait each)
+      // two rounds (levels 0..4, then 5..8): the loads of a round are in flight together (one wait
+      // each); the accumulator is released as soon as the second round is in registers
 #pragma unroll
-      for (int L0 = 0; L0 < kOzLevels; L0 += 3) {
-        uint32_t rr[3][DC];
+      for (int rd = 0; rd < 2; ++rd) {
+        constexpr int kR = 5;
+        const int L0 = rd * kR, nl = rd == 0 ? kR : kOzLevels - kR;
+        uint32_t rr[kR][DC];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if constexpr (DC == 16) tmem_ld16(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
-          else tmem_ld8(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
+        for (int q = 0; q < kR; ++q) {
+          if (q < nl) {
+            if constexpr (DC == 16) tmem_ld16(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
+            else if constexpr (DC == 8) tmem_ld8(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
+            else tmem_ld4(lane_base + (uint32_t)(KPT * (L0 + q)), rr[q]);
+          }
         }
         tmem_wait_ld();
+        if (rd == 1) {
+          tc_fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce);
+        }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < kR; ++q) {
           const int L = L0 + q;
           if (L < 5) {
             const int sh = 7 * (4 - L);
 #pragma unroll
             for (int jj = 0; jj < DC; ++jj) acc_i[jj] += (long long)__float2int_rn(__uint_as_float(rr[q][jj])) << sh;
-          } else {
+          } else if (L < kOzLevels) {
             const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : (L == 7) ? 0x1p-14f : 0x1p-21f;
 #pragma unroll
             for (int jj = 0; jj < DC; ++jj) acc_f[jj] = fmaf(__uint_as_float(rr[q][jj]), sc, acc_f[jj]);
           }
         }
       }
-      tc_fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce);
       const long long f = f0 + (dir ? nwin - 1 - w : w);
       if (w == nwin - 1 || (dir ? f % nW == 0 : (f + 1) % nW == 0)) {  // end of a segment: its tile's rows
         const int mt = (int)(f / nW), row = mt * kOzMT + 32 * (warp & 3) + lane;
         const int slice = g - oz_cta_of((long long)mt * nW, G, U);
         if (row < n) {
           const OzPart qp = oz_part(Qpart, n, KP, ksplit);
-          const size_t o = ((size_t)slice * n + row) * KP + DC * half;
 #pragma unroll
           for (int jj = 0; jj < DC; ++jj) {
-            if (DC * half + jj < KP) {
-              qp.qi[o + jj] = acc_i[jj];
-              qp.qf[o + jj] = acc_f[jj];
+            const int j = DC * half + jj;
+            if (j < KP) {
+              const size_t o = ((size_t)slice * KP + j) * n + row;
+              qp.qi[o] = acc_i[jj];
+              qp.qf[o] = acc_f[jj];
             }
           }
         }
@@ -508,7 +519,7 @@ __global__ void k_oz_sum(int n, int nW, const double* __restrict__ Qpart, double
   const size_t total = (size_t)n * KP;
   const long long U = (long long)((n + kOzMT - 1) / kOzMT) * nW;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(q / KP), j = (int)(q % KP);
+    const int j = (int)(q / n), i = (int)(q % n);  // consecutive threads: consecutive rows of column j
     const int ns = oz_slices(i / kOzMT, nW, nctas, U);
     long long si = 0;
     double sf = 0.0;
@@ -516,7 +527,7 @@ __global__ void k_oz_sum(int n, int nW, const double* __restrict__ Qpart, double
       si += qp.qi[(size_t)k * total + q];
       sf += (double)qp.qf[(size_t)k * total + q];
     }
-    Q[q] = oz_finish(si, sf, emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
+    Q[(size_t)i * KP + j] = oz_finish(si, sf, emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
   }
   if (blockIdx.x == 0 && threadIdx.x < KP) emaxP[threadIdx.x] = 0;
 }
@@ -543,39 +554,39 @@ k_oz_sum_gram(int n, int nW, const double* __restrict__ Qpart, const double* __r
   G g;
   g.init(tid);
   for (int base = r0; base < r1; base += C::ROWS) {
-    const int i = base + rl;
-    double xv[C::CPT], yv[C::CPT];
+    // the tile's ROWS x KP outputs, thread e -> (row e % ROWS, column e / ROWS): the partials of a
+    // column are consecutive in memory
 #pragma unroll
-    for (int c = 0; c < C::CPT; ++c) xv[c] = yv[c] = 0.0;
-    if (i < r1) {
-      const size_t o = (size_t)i * KP + j0;
-      ldv<C::CPT>(P + o, xv);
-      const int ns = oz_slices(i / kOzMT, nW, nctas, U);
-      long long si[C::CPT];
-      double sf[C::CPT];
-#pragma unroll
-      for (int c = 0; c < C::CPT; ++c) {
-        si[c] = 0;
-        sf[c] = 0.0;
-      }
-      for (int k = 0; k < ns; ++k) {
-#pragma unroll
-        for (int c = 0; c < C::CPT; ++c) {
-          si[c] += qp.qi[(size_t)k * total + o + c];
-          sf[c] += (double)qp.qf[(size_t)k * total + o + c];
+    for (int e = tid; e < C::ROWS * KP; e += kThreads) {
+      const int rr = e % C::ROWS, j = e / C::ROWS, i = base + rr;
+      double y = 0.0;
+      if (i < r1) {
+        const int ns = oz_slices(i / kOzMT, nW, nctas, U);
+        long long si = 0;
+        double sf = 0.0;
+        for (int k = 0; k < ns; ++k) {
+          const size_t o = ((size_t)k * KP + j) * n + i;
+          si += qp.qi[o];
+          sf += (double)qp.qf[o];
         }
+        y = oz_finish(si, sf, emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
       }
-      const int fa = emaxA[i] - 1022;
-#pragma unroll
-      for (int c = 0; c < C::CPT; ++c) yv[c] = oz_finish(si[c], sf[c], fa + emaxP[kMaxKP + j0 + c] - 1022);
-      stv<C::CPT>(Q + o, yv);
+      Ys[rr * KP + j] = y;
     }
+    const int i = base + rl;
+    double xv[C::CPT];
 #pragma unroll
-    for (int c = 0; c < C::CPT; ++c) {
-      Xs[rl * KP + j0 + c] = xv[c];
-      Ys[rl * KP + j0 + c] = yv[c];
-    }
+    for (int c = 0; c < C::CPT; ++c) xv[c] = 0.0;
+    if (i < r1) ldv<C::CPT>(P + (size_t)i * KP + j0, xv);
+#pragma unroll
+    for (int c = 0; c < C::CPT; ++c) Xs[rl * KP + j0 + c] = xv[c];
     __syncthreads();
+    if (i < r1) {
+      double yv[C::CPT];
+#pragma unroll
+      for (int c = 0; c < C::CPT; ++c) yv[c] = Ys[rl * KP + j0 + c];
+      stv<C::CPT>(Q + (size_t)i * KP + j0, yv);
+    }
     g.accumulate(Xs, Ys, min(C::ROWS, r1 - base));
     __syncthreads();
   }
@@ -595,10 +606,9 @@ size_t oz_p_chunks_bytes(int n, int kp) {
   return nK * (size_t)kOzDigits * kpt * kOzKC * 2;
 }
 namespace {
-// The work split of k_dense_tc for n rows on `sms` SMs: at most one CTA per SM and per window;
-// windows of two chunks unless that leaves SMs idle. When the row tiles fit on the SMs, the CTA
-// count is the largest multiple of the tile count, so that every CTA works on one tile: the
-// product is bound by HBM reads, and at n = 4096 (32 tiles) 128 CTAs beat 152 by 8 %.
+// The work split of k_dense_tc for n rows on `sms` SMs: one CTA per SM (at most one per window);
+// windows of two chunks unless that leaves SMs idle. Every SM takes part: each CTA's time is set
+// by its own MMA and drain pipeline rather than by HBM, so more CTAs finish sooner.
 struct OzSplit {
   int nM, nK, wl, nW, G;
   long long U;
@@ -609,7 +619,6 @@ struct OzSplit {
     nW = (nK + wl - 1) / wl;
     U = (long long)nM * nW;
     G = (int)(U < sms ? U : sms);
-    if (nM <= G) G = nM * (G / nM);
   }
 };
 }  // namespace

@@ -186,16 +186,19 @@ def test_spmm_autotuner_picks_the_fastest_shape_and_never_changes_results(mb):
     sv = mb.Solver(A, s=s, precision=mb.MBPCG_MIXED_FP32)
     try:
         unroll, cps, times = sv.spmm_tuning()
-        assert unroll in (4, 8) and cps in (4, 8, 16) and len(times) == 6 and min(times) > 0.0
-        order = [(4, 4), (4, 8), (4, 16), (8, 4), (8, 8), (8, 16)]
-        assert times[order.index((unroll, cps))] == min(times)
+        order = [(4, 4), (4, 8), (4, 16), (8, 4), (8, 8), (8, 16), (0, 2), (1, 1), (1, 2), (2, 2), (2, 4)]
+        assert (unroll, cps) in order and len(times) == 11
+        assert times[6] == 0.0  # 13,824 rows: no tiling plan
+        timed = [t for t in times if t > 0.0]
+        assert len(timed) == 10 and times[order.index((unroll, cps))] == min(timed)
         x0, i0 = sv.solve(b, U, tol=1e-10, maxit=100000)
-        for shape in ((4, 4), (8, 16)):
+        for shape in ((4, 4), (8, 16), (1, 2), (2, 2)):
             sv.set_spmm_shape(*shape)
             x, info = sv.solve(b, U, tol=1e-10, maxit=100000)
             assert np.array_equal(x, x0) and info["iterations"] == i0["iterations"]
-        with pytest.raises(mb.MBPCGError):
-            sv.set_spmm_shape(3, 8)
+        for bad in ((3, 8), (0, 2)):  # an unknown shape; the tiled kernel without a plan
+            with pytest.raises(mb.MBPCGError):
+                sv.set_spmm_shape(*bad)
     finally:
         sv.close()
     for other in (mb.Solver(A, s=s), mb.Solver(wl.dense_spd(64, 0), s=4, precision=mb.MBPCG_MIXED_FP32)):
