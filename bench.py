@@ -80,7 +80,8 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="dense4096", choices=sorted(WORKLOADS) + ["serving"])
+    p.add_argument("--workload", default="dense4096", choices=sorted(WORKLOADS) + ["serving", "batch"])
+    p.add_argument("--batch-size", type=int, default=32, help="batch: uneven systems solved per step")
     p.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     p.add_argument("--slots", type=int, default=8, help="serving: solves admitted at once")
     p.add_argument("--compare-requests", type=int, default=400,
@@ -185,6 +186,15 @@ def recorded_traffic(kernel, workload, s):
     return rec.get("dram_bytes_per_launch")
 
 
+def l2_flush(flush):
+    """Leave L2 cold and clean: write the first half of `flush` (each half larger than L2), then read
+    the second half, so that the written lines are evicted -- and written back -- before the timed
+    region instead of during it."""
+    h = flush.numel() // 2
+    flush[:h].zero_()
+    flush[h:].sum()
+
+
 def read_ceiling_gbs(stream, flush):
     """HBM read-only bandwidth of this GPU right now: a sum over a 1 GiB FP32 tensor (torch's own
     reduction), L2 flushed before each run. A read-only stream does not reach the copy bandwidth
@@ -195,7 +205,7 @@ def read_ceiling_gbs(stream, flush):
     ts = []
     with torch.cuda.stream(stream):
         for i in range(6):
-            flush.zero_()
+            l2_flush(flush)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
@@ -269,7 +279,7 @@ def spmm_roofline(mb, stream, flush, peak_gbs, launches=10):
                 if launch() != 0:
                     raise RuntimeError("mbpcg_apply_dev failed")
                 for _ in range(launches):
-                    flush.zero_()
+                    l2_flush(flush)
                     ev0 = torch.cuda.Event(enable_timing=True)
                     ev1 = torch.cuda.Event(enable_timing=True)
                     ev0.record(ss)
@@ -287,7 +297,8 @@ def spmm_roofline(mb, stream, flush, peak_gbs, launches=10):
         finally:
             sv.close()
     return {"bound": "hbm", "unit": "GB/s", "peak": peak_gbs, "cases": cases,
-            "timing": f"{launches} launches, L2 flushed (256 MB write) before each, CUDA events on the stream",
+            "timing": f"{launches} launches, L2 flushed before each (256 MB written, then another 256 MB read, so "
+                      "no write-back falls in the timed launch), CUDA events on the stream",
             "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
 
@@ -344,7 +355,7 @@ def bench_config(args, cfg, A, s, pname, world):
     return {"workload": cfg.get("mixed_desc", cfg["desc"]) if mixed else cfg["desc"], "n": int(A.n),
             "nnz": int(A.nnz), "s": s, "precond": cfg["precond"],
             "tol": cfg.get("mixed_tol", cfg["tol"]) if mixed else cfg["tol"],
-            "l2": "flushed before every step (256 MB write)", "launch_mode": args.launch_mode, "precision": pname,
+            "l2": "flushed before every step (256 MB written, then 256 MB read)", "launch_mode": args.launch_mode, "precision": pname,
             "residual": args.residual, "parallelism": "replicas only" if world > 1 else "single GPU"}
 
 
@@ -380,13 +391,13 @@ def run_ours(args, world, rank, local):
     stream = solver.stream
     bd = torch.as_tensor(b, device=dev)
     Ud = torch.as_tensor(np.asfortranarray(U).ravel(order="F"), device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = torch.zeros(2 * L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def timed(sv, Uarg, k):
         times, infos, xs = [], [], None
         for _ in range(k):
             with torch.cuda.stream(sv.stream):
-                flush.zero_()
+                l2_flush(flush)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(sv.stream)
@@ -493,7 +504,7 @@ def run_ours(args, world, rank, local):
             launch()
         k_ms = []
         for _ in range(args.kernel_launches):
-            flush.zero_()
+            l2_flush(flush)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
@@ -521,7 +532,7 @@ def run_ours(args, world, rank, local):
         with torch.cuda.stream(stream):
             q_ms = []
             for _ in range(max(3, args.kernel_launches // 2)):
-                flush.zero_()
+                l2_flush(flush)
                 ev0 = torch.cuda.Event(enable_timing=True)
                 ev1 = torch.cuda.Event(enable_timing=True)
                 ev0.record(stream)
@@ -535,7 +546,7 @@ def run_ours(args, world, rank, local):
         with torch.cuda.stream(stream):
             g_ms = []
             for _ in range(max(3, args.kernel_launches // 2)):
-                flush.zero_()
+                l2_flush(flush)
                 ev0 = torch.cuda.Event(enable_timing=True)
                 ev1 = torch.cuda.Event(enable_timing=True)
                 ev0.record(stream)
@@ -863,10 +874,89 @@ def run_serving(args, world, rank):
     return line if rank == 0 else None
 
 
+BATCH_DESC = ("batch of uneven systems: the first K requests of the serving stream's generator with n "
+              "log-uniform in [1e3, 1e5] (2D/3D Poisson, 3D diffusion with Jacobi), s in {1, 4, 8, 16}, tol 1e-8, "
+              "FP64; one step solves all K")
+
+
+def run_batch(args, world, rank):
+    """K uneven systems per step, solved (a) one after another on their own handles and (b) as one
+    batch (mbpcg_batch_*: one graph launch whose chains run concurrently). value = (b) per step;
+    each member's result is compared bit for bit with (a). Device synchronised on both sides of
+    every timed call; host wall clock (the calls are synchronous and span many streams)."""
+    import torch
+    import paper_2608_07327_gb300 as mb
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mb.lib()
+    reqs = wl.serving_requests(args.batch_size, 0, n_lo=1e3, n_hi=1e5)
+    cache = MatrixCache()
+    solvers = [mb.Solver(cache.get(r["kind"], r["m"]), s=r["s"], precond=r["precond"]) for r in reqs]
+    rhs = [wl.rhs(r["n"], r["rhs_seed"]) for r in reqs]
+    batch = mb.Batch(solvers)
+
+    def solo():
+        return [sv.solve(b, tol=1e-8) for sv, b in zip(solvers, rhs)]
+
+    def batched():
+        return batch.solve(rhs, tol=1e-8)
+
+    for _ in range(args.warmup):
+        ref = solo()
+        got = batched()
+    times = {"solo": [], "batch": []}
+    clk = ClockSampler(local)
+    with clk:
+        for _ in range(args.steps):
+            for name, fn in (("solo", solo), ("batch", batched)):
+                torch.cuda.synchronize()
+                if world > 1:
+                    torch.distributed.barrier()
+                t0 = time.perf_counter()
+                out = fn()
+                torch.cuda.synchronize()
+                times[name].append((time.perf_counter() - t0) * 1e3)
+                if name == "batch":
+                    got = out
+                else:
+                    ref = out
+    ms_batch, ms_solo = max_over_ranks([float(np.median(times["batch"])), float(np.median(times["solo"]))], world, dev)
+    same = all(np.array_equal(a[0], b[0]) and a[1]["iterations"] == b[1]["iterations"] for a, b in zip(ref, got))
+    iters = sum(info["iterations"] for _, info in got)
+    launches = sum(launches_per_solve(info, False, False) for _, info in got)
+    h2d = sum(r["n"] * 8 for r in reqs)
+    batch.close()
+    for sv in solvers:
+        sv.close()
+    line = {
+        "metric": "batch of uneven systems: time per step (all K solved), one graph launch", "value": round(ms_batch, 3),
+        "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_batch, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH_DESC, "K": len(reqs), "n_total": int(sum(r["n"] for r in reqs)),
+                   "parallelism": "replicas only" if world > 1 else "single GPU",
+                   "l2": "inputs of the K systems differ; no flush"},
+        "solo_sequential_ms": round(ms_solo, 3), "speedup_vs_solo": round(ms_solo / ms_batch, 3),
+        "identical_results": bool(same), "iterations_total": int(iters),
+        "max_relres_true": max(info["relres_true"] for _, info in got),
+        "e2e": {"value": round(ms_batch, 3), "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)},
+        "gpu_launches": int(launches) * args.steps, "clocks": clk.summary(),
+    }
+    return line if rank == 0 else None
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
-    if args.workload == "serving":
+    if args.workload == "batch":
+        line = None if args.impl == "reference" else run_batch(args, world, rank)
+        if args.impl == "reference":
+            line = {"impl": "reference", "unavailable": "the oracle solves one system at a time; the batch "
+                    "workload has no CPU reference arm"} if rank == 0 else None
+    elif args.workload == "serving":
         line = None if args.impl == "reference" else run_serving(args, world, rank)
         if args.impl == "reference":
             line = {"impl": "reference", "unavailable": "the oracle solves one system at a time; the serving "

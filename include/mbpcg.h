@@ -67,13 +67,19 @@ typedef enum { MBPCG_ALGO_MBPCG = 0, MBPCG_ALGO_CG = 1 } mbpcg_algo;
  * itself are FP64: the true-residual restarts are an FP64 iterative refinement loop (at most 12
  * correction solves, each asked for at most 1e-5 relative reduction). Results therefore differ from
  * the FP64 path; the requested tol is still checked on the FP64 true residual.
- * FP64_TC (dense A, MBPCG only): the same FP64 solve, but the product A P runs on the BF16 tensor
- * cores by exact splitting of A and P into 8 base-128 digits (Ozaki scheme); its result has the
- * accuracy of an FP64 product. The digits of A take 16 bytes per entry of workspace. At s > 8
- * the k x k-row products of the block update and of the W/P update (P T, (AP) T, (AP) Xi,
- * V zeta^-1, P zeta^T) run on the tensor cores the same way (3 more n x KP blocks of workspace);
- * the Grams, the norms and the k x k steps stay FP64. */
-typedef enum { MBPCG_FP64 = 0, MBPCG_MIXED_FP32 = 1, MBPCG_FP64_TC = 2 } mbpcg_precision;
+ * MIXED_BF16 (2): reserved for a BF16 tensor-core inner solve of dense A; not built -- every
+ * create call with it returns MBPCG_ERR_INVALID. A BF16 copy of A loses SPD-ness wherever
+ * kappa(A) * 2^-8 is not small (kappa = 1e6 here), and at the condition numbers this library is
+ * measured on the FP64 tensor-core product below is the faster dense solve.
+ * FP64_TC (3; dense A, MBPCG only): the same FP64 solve, but the product A P runs on the tensor
+ * cores by exact splitting of A and P into 8 signed base-128 digits (Ozaki scheme), FP16 operands
+ * and FP32 accumulation in windows whose sums stay exact; every digit-pair level that can reach
+ * 2^-60 of a row scale of A times a column scale of P is kept, so the result is at least as
+ * accurate as an FP64 product (bound 1e-14 |A||P| entry by entry, tested). The digits of A take 8
+ * bytes per entry of workspace. At s > 8 the k x k-row products of the block update and of the W/P
+ * update (P T, (AP) T, (AP) Xi, V zeta^-1, P zeta^T) run on the tensor cores the same way (3 more
+ * n x KP blocks of workspace); the Grams, the norms and the k x k steps stay FP64. */
+typedef enum { MBPCG_FP64 = 0, MBPCG_MIXED_FP32 = 1, MBPCG_MIXED_BF16 = 2, MBPCG_FP64_TC = 3 } mbpcg_precision;
 
 typedef struct {
   int32_t iterations;        /* inner iterations summed over restarts */
@@ -210,6 +216,27 @@ typedef enum {
 } mbpcg_product_kernel;
 int mbpcg_get_product_kernel(mbpcg_handle h, int32_t fp32, int32_t* kernel, float* times_us);
 int mbpcg_set_product_kernel(mbpcg_handle h, int32_t kernel);
+
+/* Batches of uneven systems (NEXT row "batching"; not in the paper). A batch binds count existing
+ * handles -- any mix of CSR and dense matrices, sizes, block widths, algorithms and precisions,
+ * each created with MBPCG_LAUNCH_GRAPH -- and captures one inner solve of each (set-up, the
+ * device-side WHILE loop, the exit) as an independent chain of ONE CUDA graph, built once at
+ * mbpcg_batch_create. mbpcg_batch_solve_dev copies each member's b (and U) in on the member's
+ * stream, launches the batch graph once on the batch's stream (the stream given at create, or one
+ * of its own), so that the members' kernels run concurrently on the device, then runs each
+ * member's true-residual restarts (or refinement steps) on the member's own graph and stream.
+ * Every member runs the same kernels in the same order as a solo mbpcg_solve_dev, so its x and info
+ * are bit-identical to a solo solve. b, U and x_out: arrays of count device pointers laid out as
+ * for mbpcg_solve_dev (U may be NULL, or hold NULL entries: drawn from the handle's seed). info:
+ * NULL or count entries. Returns MBPCG_OK when every member met tol, else the status of the first
+ * member that did not (each member's own status is in info[i].status); errors as mbpcg_solve_dev.
+ * A handle may belong to several batches, but two solves of one handle must not run at the same
+ * time. mbpcg_batch_destroy releases the graph, not the handles. */
+typedef struct mbpcg_batch_ctx* mbpcg_batch;
+int mbpcg_batch_create(mbpcg_batch* out, const mbpcg_handle* handles, int32_t count, void* stream);
+int mbpcg_batch_solve_dev(mbpcg_batch batch, const double* const* b, const double* const* U, double tol,
+                          int32_t maxit, double* const* x_out, mbpcg_info* info);
+void mbpcg_batch_destroy(mbpcg_batch batch);
 
 /* Release a handle (NULL is ignored). */
 void mbpcg_destroy(mbpcg_handle h);

@@ -39,9 +39,10 @@ int mbpcg_k_spmm_gram(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
  * mbpcg_k_spmm_gram without any device allocation. The paper has no counterpart: this exists for
  * callers that cannot call cudaMalloc (a host framework or plugin that owns all device memory,
  * a real-time loop that cannot afford cudaMalloc's device synchronisation, a process with no
- * device memory left to give). Its scratch is a fixed array of about 400 KB compiled into the
+ * device memory left to give). Its scratch is a fixed array of about 1.5 MB compiled into the
  * library, which every GPU that loads the library holds until the process exits; nothing is
- * allocated or freed. Limits: s <= 16 and at most 320 CTAs of partial sums (a GB300 uses 304);
+ * allocated or freed. Limits: s <= 16 and at most 1216 CTAs of partial sums (a GB300 uses up to
+ * 1216: 8 per SM);
  * larger requests return MBPCG_ERR_INVALID with a message. The first call in each CUDA context (per
  * device, and again after a device reset) looks up the array's device address, so make that first
  * call before any stream capture. All calls share

@@ -73,6 +73,49 @@ class Server:
         self.close()
 
 
+class Batch:
+    """Several Solvers (any mix of matrices, sizes, s, algorithms and precisions, all in graph launch
+    mode) whose inner solves run as independent chains of one CUDA graph, launched once per solve
+    (mbpcg_batch_*). Each member's result is bit-identical to a solo solve of the same Solver."""
+
+    def __init__(self, solvers):
+        import torch
+        self.solvers = list(solvers)
+        self.stream = torch.cuda.Stream()
+        self.b = _native.mbpcg_batch_create([sv.h for sv in self.solvers], self.stream.cuda_stream)
+
+    def solve(self, bs, Us=None, tol: float = 1e-8, maxit: int = 100000):
+        """bs (and Us, each None or n x s column-major): numpy arrays, one per member. Returns a
+        list of (x, info dict)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        bd = [torch.as_tensor(np.ascontiguousarray(b, dtype=np.float64), device=dev) for b in bs]
+        Ud = None
+        if Us is not None:
+            Ud = [None if U is None else torch.as_tensor(np.asarray(U, dtype=np.float64).T.copy(), device=dev)
+                  for U in Us]  # row-major s x n = column-major n x s
+        xs = [torch.empty(sv.n, dtype=torch.float64, device=dev) for sv in self.solvers]
+        cur = torch.cuda.current_stream()
+        for sv in self.solvers:
+            sv.stream.wait_stream(cur)
+        self.stream.wait_stream(cur)
+        st, infos = _native.mbpcg_batch_solve_dev(self.b, bd, Ud, tol, maxit, xs)
+        if st not in (MBPCG_OK, MBPCG_NOT_CONVERGED, MBPCG_BREAKDOWN):
+            raise MBPCGError(st, "mbpcg_batch_solve_dev")
+        return [(x.cpu().numpy(), info.as_dict()) for x, info in zip(xs, infos)]
+
+    def close(self):
+        if self.b is not None:
+            _native.mbpcg_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Solver:
     """One handle of the library for a fixed matrix and number of copies s.
 

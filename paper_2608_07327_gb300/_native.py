@@ -23,7 +23,8 @@ MBPCG_ALGO_MBPCG = 0
 MBPCG_ALGO_CG = 1
 MBPCG_FP64 = 0
 MBPCG_MIXED_FP32 = 1
-MBPCG_FP64_TC = 2
+MBPCG_MIXED_BF16 = 2
+MBPCG_FP64_TC = 3
 MBPCG_LAUNCH_GRAPH = 0
 MBPCG_LAUNCH_EAGER = 1
 MBPCG_RESIDUAL_EXPLICIT = 0
@@ -101,6 +102,10 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_float)]),
     "mbpcg_set_spmm_shape": (ctypes.c_int, [_P, _I32, _I32]),
     "mbpcg_apply_dev": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "mbpcg_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I32, _P]),
+    "mbpcg_batch_solve_dev": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I32,
+                                             ctypes.POINTER(_P), ctypes.POINTER(Info)]),
+    "mbpcg_batch_destroy": (None, [_P]),
     "mbpcg_get_product_kernel": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]),
     "mbpcg_set_product_kernel": (ctypes.c_int, [_P, _I32]),
     "mbpcg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -370,6 +375,30 @@ def mbpcg_set_spmm_shape(h, unroll, ctas_per_sm):
 
 def mbpcg_apply_dev(h, fp32, X, Y):
     return lib().mbpcg_apply_dev(h, fp32, ptr(X), ptr(Y))
+
+
+def mbpcg_batch_create(handles, stream=None):
+    arr = (_P * len(handles))(*handles)
+    b = _P()
+    st = lib().mbpcg_batch_create(ctypes.byref(b), arr, len(handles), stream)
+    if st != MBPCG_OK:
+        raise MBPCGError(st, "mbpcg_batch_create")
+    return b
+
+
+def mbpcg_batch_solve_dev(batch, bs, Us, tol, maxit, xs):
+    """bs, xs: lists of device tensors; Us: None or a list of device tensors / None (column-major)."""
+    k = len(bs)
+    pb = (_P * k)(*[ptr(t) for t in bs])
+    px = (_P * k)(*[ptr(t) for t in xs])
+    pu = None if Us is None else (_P * k)(*[ptr(t) for t in Us])
+    infos = (Info * k)()
+    st = lib().mbpcg_batch_solve_dev(batch, pb, pu, tol, maxit, px, infos)
+    return st, list(infos)
+
+
+def mbpcg_batch_destroy(batch):
+    lib().mbpcg_batch_destroy(batch)
 
 
 def mbpcg_get_product_kernel(h, fp32=0):

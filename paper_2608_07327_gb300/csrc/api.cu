@@ -254,6 +254,16 @@ struct mbpcg_ctx {
   cudaEvent_t e0, e1;
 };
 
+// A set of handles whose inner solves run as independent chains of one CUDA graph (one launch).
+struct mbpcg_batch_ctx {
+  std::vector<mbpcg_ctx*> h;
+  cudaStream_t stream = nullptr;
+  int own_stream = 0;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ready;  // one per member: its inputs are in place
+  cudaEvent_t done = nullptr;      // the batch graph has finished
+};
+
 namespace {
 
 template <typename T>
@@ -347,6 +357,8 @@ int check_common(int n, int s, int precond, int algo, int precision, int mem) {
   if (algo == MBPCG_ALGO_MBPCG && (s < 1 || s > 32)) return set_err(MBPCG_ERR_INVALID, "s must be in [1, 32] (got %d)", s);
   if (precond != MBPCG_PRECOND_NONE && precond != MBPCG_PRECOND_JACOBI)
     return set_err(MBPCG_ERR_INVALID, "unknown precond %d", precond);
+  if (precision == MBPCG_MIXED_BF16)
+    return set_err(MBPCG_ERR_INVALID, "MBPCG_MIXED_BF16 is reserved and not built (use MBPCG_FP64_TC for dense A)");
   if (precision != MBPCG_FP64 && precision != MBPCG_FP64_TC && precision != MBPCG_MIXED_FP32)
     return set_err(MBPCG_ERR_INVALID, "unsupported precision %d", precision);
   if (precision == MBPCG_MIXED_FP32 && algo != MBPCG_ALGO_MBPCG)
@@ -780,14 +792,14 @@ void enqueue_cg_exit(mbpcg_ctx* h) {
   enqueue_true_residual(h);
 }
 
-int build_graph(mbpcg_ctx* h) {
-  cudaGraph_t g = nullptr;
-  CUDA_TRY(cudaGraphCreate(&g, 0));
-  cudaError_t e = cudaGraphConditionalHandleCreate(&h->cond, g, 1, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(g);
-    return set_err(MBPCG_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
-  }
+// Captures one inner solve of the handle -- set-up, a WHILE node over the loop body, exit -- into
+// g, as a chain of its own (no dependency on what g already holds). The loop condition is created
+// on g and stored in *cond; the captured kernels carry it.
+cudaError_t capture_solve(mbpcg_ctx* h, cudaGraph_t g, cudaGraphConditionalHandle* cond) {
+  cudaError_t e = cudaGraphConditionalHandleCreate(cond, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  const cudaGraphConditionalHandle own = h->cond;
+  h->cond = *cond;
   const bool cg = h->algo == MBPCG_ALGO_CG;
   e = cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
@@ -802,7 +814,7 @@ int build_graph(mbpcg_ctx* h) {
     cudaGraph_t body = nullptr;
     if (e == cudaSuccess) {
       cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
-      np.conditional.handle = h->cond;
+      np.conditional.handle = *cond;
       np.conditional.type = cudaGraphCondTypeWhile;
       np.conditional.size = 1;
       e = cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &np);
@@ -836,12 +848,22 @@ int build_graph(mbpcg_ctx* h) {
       }
     }
   }
+  h->cond = own;
+  return e;
+}
+
+int build_graph(mbpcg_ctx* h) {
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond{};
+  cudaError_t e = capture_solve(h, g, &cond);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_err(MBPCG_ERR_CUDA, "building the solve graph failed: %s", cudaGetErrorString(e));
   }
+  h->cond = cond;
   h->graph_ready = 1;
   return MBPCG_OK;
 }
@@ -874,10 +896,18 @@ int run_eager(mbpcg_ctx* h, int maxit_inner) {
   return MBPCG_OK;
 }
 
-// Copies b and U in (host or device memory), runs the inner solves with true-residual restarts,
-// and copies x out. mem: 0 host, 1 device for b, U and x.
-int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int maxit, double* x_out,
-               mbpcg_info* info, int mem, int no_test) {
+// The host side of one solve: the true-residual restart loop (FP64) or the refinement loop (mixed
+// precision) around the inner solves.
+struct SolveLoop {
+  double tol = 0.0, tol_rel = 0.0, best_relres = INFINITY;  // best_relres: mixed precision, of xbest
+  int maxit = 0, no_test = 0, total = 0, restarts = 0, max_restarts = 0, status = MBPCG_OK;
+  SolveState s{};
+};
+
+// Checks the arguments, builds the graph if needed, copies b and U in (mem: 0 host, 1 device) and
+// sets up the loop's variables.
+int solve_begin(mbpcg_ctx* h, const double* b, const double* U, double tol, int maxit, const double* x_out,
+                int mem, int no_test, SolveLoop* L) {
   if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
   if (!b || (!x_out && !no_test)) return set_err(MBPCG_ERR_INVALID, "b and x_out must not be NULL");
   if (!(tol > 0.0) || tol != tol) return set_err(MBPCG_ERR_INVALID, "tol must be a positive number");
@@ -885,7 +915,6 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
   const int n = h->dm.n;
   const size_t nb = (size_t)n * sizeof(double);
   const cudaMemcpyKind in_kind = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  const cudaMemcpyKind out_kind = mem ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (!h->graph_ready && h->launch_mode == MBPCG_LAUNCH_GRAPH) {
     int rc = build_graph(h);
     if (rc) return rc;
@@ -916,71 +945,101 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
     }
     CUDA_TRY(cudaGetLastError());
   }
-  int total = 0, restarts = 0, status = MBPCG_OK;
-  double best_relres = INFINITY;  // mixed precision: true relative residual of xbest
   // FP64 inner solves: at most 3 true-residual restarts. Mixed precision: the restarts are the FP64
   // refinement loop (correction solves in FP32), at most kMixedRestarts, and an inner solve is not
   // asked for more than kMixedInnerTol relative reduction, which FP32 blocks can deliver.
-  const int max_restarts = h->dm.mixed ? kMixedRestarts : 3;
-  double tol_rel = h->dm.mixed ? (tol > kMixedInnerTol ? tol : kMixedInnerTol) : tol;
-  SolveState s;
-  for (;;) {
-    const int maxit_inner = no_test ? maxit : (maxit - total);
-    k_params<<<1, 1, 0, h->stream>>>(h->st, tol_rel, maxit_inner, no_test, restarts, h->s,
-                                     h->dm.mixed && !no_test ? 1 : 0);
-    CUDA_TRY(cudaGetLastError());
-    if (h->launch_mode == MBPCG_LAUNCH_EAGER) {
-      int rc = run_eager(h, maxit_inner);
-      if (rc) return rc;
-    } else {
-      CUDA_TRY(cudaGraphLaunch(h->exec, h->stream));
-    }
-    CUDA_TRY(cudaMemcpyAsync(h->st_host, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaStreamSynchronize(h->stream));
-    std::memcpy(&s, h->st_host, sizeof(s));
-    if (s.kerr) return set_err(MBPCG_ERR_TIMEOUT, "a bounded device-side wait timed out");
-    total += s.it;
-    if (no_test) {
-      status = s.status;
-      break;
-    }
-    const double relres = (s.b_norm > 0.0) ? s.true_res / s.b_norm : 0.0;
-    if (h->dm.mixed) {
-      // The refinement loop keeps its best iterate: a correction from an FP32 inner solve that
-      // made the FP64 residual larger (possible when kappa(A) u_fp32 is not small) ends the loop
-      // with the best x found.
-      if (relres < best_relres) {
-        best_relres = relres;
-        CUDA_TRY(cudaMemcpyAsync(h->xbest, h->x, nb, cudaMemcpyDeviceToDevice, h->stream));
-      } else {
-        CUDA_TRY(cudaMemcpyAsync(h->x, h->xbest, nb, cudaMemcpyDeviceToDevice, h->stream));
-        s.true_res = best_relres * s.b_norm;
-        status = best_relres <= tol ? MBPCG_OK : MBPCG_NOT_CONVERGED;
-        break;
-      }
-    }
-    if (relres <= tol) {
-      status = MBPCG_OK;
-      break;
-    }
-    if (restarts >= max_restarts || total >= maxit || s.status == MBPCG_NOT_CONVERGED) {
-      status = (s.status == MBPCG_OK) ? MBPCG_NOT_CONVERGED : s.status;
-      break;
-    }
-    ++restarts;
-    tol_rel = 0.5 * tol * s.b_norm / s.true_res;
-    if (h->dm.mixed && tol_rel < kMixedInnerTol) tol_rel = kMixedInnerTol;
+  *L = SolveLoop{};
+  L->tol = tol;
+  L->maxit = maxit;
+  L->no_test = no_test;
+  L->max_restarts = h->dm.mixed ? kMixedRestarts : 3;
+  L->tol_rel = h->dm.mixed ? (tol > kMixedInnerTol ? tol : kMixedInnerTol) : tol;
+  return MBPCG_OK;
+}
+
+// The parameters of the next inner solve (tolerance, iteration budget, restart count).
+int enqueue_inner_params(mbpcg_ctx* h, const SolveLoop& L) {
+  const int maxit_inner = L.no_test ? L.maxit : (L.maxit - L.total);
+  k_params<<<1, 1, 0, h->stream>>>(h->st, L.tol_rel, maxit_inner, L.no_test, L.restarts, h->s,
+                                   h->dm.mixed && !L.no_test ? 1 : 0);
+  CUDA_TRY(cudaGetLastError());
+  return MBPCG_OK;
+}
+
+// One inner solve on the handle's own stream: its parameters, then the graph (or eager launches).
+int launch_inner(mbpcg_ctx* h, const SolveLoop& L) {
+  int rc = enqueue_inner_params(h, L);
+  if (rc) return rc;
+  if (h->launch_mode == MBPCG_LAUNCH_EAGER) return run_eager(h, L.no_test ? L.maxit : (L.maxit - L.total));
+  CUDA_TRY(cudaGraphLaunch(h->exec, h->stream));
+  return MBPCG_OK;
+}
+
+// Starts the copy of the solve state to the host after an inner solve.
+int fetch_state(mbpcg_ctx* h) {
+  CUDA_TRY(cudaMemcpyAsync(h->st_host, h->st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
+  return MBPCG_OK;
+}
+
+// Reads the state of the inner solve just finished and decides: *more = 1 when another inner solve
+// (a restart, or a refinement step) is needed, with the loop's variables updated for it.
+int after_inner(mbpcg_ctx* h, SolveLoop* L, int* more) {
+  *more = 0;
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  SolveState& s = L->s;
+  std::memcpy(&s, h->st_host, sizeof(s));
+  if (s.kerr) return set_err(MBPCG_ERR_TIMEOUT, "a bounded device-side wait timed out");
+  L->total += s.it;
+  if (L->no_test) {
+    L->status = s.status;
+    return MBPCG_OK;
   }
-  if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, h->x, nb, out_kind, h->stream));
+  const size_t nb = (size_t)h->dm.n * sizeof(double);
+  const double relres = (s.b_norm > 0.0) ? s.true_res / s.b_norm : 0.0;
+  if (h->dm.mixed) {
+    // The refinement loop keeps its best iterate: a correction from an FP32 inner solve that
+    // made the FP64 residual larger (possible when kappa(A) u_fp32 is not small) ends the loop
+    // with the best x found.
+    if (relres < L->best_relres) {
+      L->best_relres = relres;
+      CUDA_TRY(cudaMemcpyAsync(h->xbest, h->x, nb, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(h->x, h->xbest, nb, cudaMemcpyDeviceToDevice, h->stream));
+      s.true_res = L->best_relres * s.b_norm;
+      L->status = L->best_relres <= L->tol ? MBPCG_OK : MBPCG_NOT_CONVERGED;
+      return MBPCG_OK;
+    }
+  }
+  if (relres <= L->tol) {
+    L->status = MBPCG_OK;
+    return MBPCG_OK;
+  }
+  if (L->restarts >= L->max_restarts || L->total >= L->maxit || s.status == MBPCG_NOT_CONVERGED) {
+    L->status = (s.status == MBPCG_OK) ? MBPCG_NOT_CONVERGED : s.status;
+    return MBPCG_OK;
+  }
+  ++L->restarts;
+  L->tol_rel = 0.5 * L->tol * s.b_norm / s.true_res;
+  if (h->dm.mixed && L->tol_rel < kMixedInnerTol) L->tol_rel = kMixedInnerTol;
+  *more = 1;
+  return MBPCG_OK;
+}
+
+// Copies x out (mem: 0 host, 1 device), waits for the handle's stream and fills info.
+int solve_end(mbpcg_ctx* h, const SolveLoop& L, double* x_out, int mem, mbpcg_info* info) {
+  const size_t nb = (size_t)h->dm.n * sizeof(double);
+  if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, h->x, nb, mem ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                      h->stream));
   CUDA_TRY(cudaEventRecord(h->e1, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (info) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->e0, h->e1);
-    const double bn = s.b_norm, rn = s.rhs_norm;
-    info->iterations = total;
-    info->restarts = restarts;
-    info->status = status;
+    const SolveState& s = L.s;
+    const double bn = s.b_norm;
+    info->iterations = L.total;
+    info->restarts = L.restarts;
+    info->status = L.status;
     info->best_col = s.best_col;
     info->ls_fallback = s.ls_fallback;
     info->reserved = 0;
@@ -988,10 +1047,24 @@ int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int m
     info->relres_ls = (bn > 0.0) ? s.ls_res / bn : 0.0;
     info->relres_true = (bn > 0.0) ? s.true_res / bn : 0.0;
     info->seconds = ms * 1e-3;
-    (void)rn;
   }
+  return MBPCG_OK;
+}
+
+// One solve: b and U in, the inner solves with their restarts, x out.
+int solve_impl(mbpcg_ctx* h, const double* b, const double* U, double tol, int maxit, double* x_out,
+               mbpcg_info* info, int mem, int no_test) {
+  SolveLoop L;
+  int rc = solve_begin(h, b, U, tol, maxit, x_out, mem, no_test, &L);
+  for (int more = 1; !rc && more;) {
+    rc = launch_inner(h, L);
+    if (!rc) rc = fetch_state(h);
+    if (!rc) rc = after_inner(h, &L, &more);
+  }
+  if (!rc) rc = solve_end(h, L, x_out, mem, info);
+  if (rc) return rc;
   g_err.clear();
-  return status;
+  return L.status;
 }
 
 }  // namespace
@@ -1229,6 +1302,107 @@ int mbpcg_set_residual_mode(mbpcg_handle h, int32_t mode) {
 }
 
 void mbpcg_destroy(mbpcg_handle h) { release(h); }
+
+void mbpcg_batch_destroy(mbpcg_batch b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaEvent_t e : b->ready)
+    if (e) cudaEventDestroy(e);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int mbpcg_batch_create(mbpcg_batch* out, const mbpcg_handle* handles, int32_t count, void* stream) {
+  if (!out) return set_err(MBPCG_ERR_INVALID, "null output pointer");
+  *out = nullptr;
+  if (!handles || count < 1) return set_err(MBPCG_ERR_INVALID, "a batch needs at least one handle");
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i]) return set_err(MBPCG_ERR_INVALID, "handle %d is NULL", i);
+    if (handles[i]->launch_mode != MBPCG_LAUNCH_GRAPH)
+      return set_err(MBPCG_ERR_INVALID, "handle %d is in eager launch mode (a batch is one graph)", i);
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return set_err(MBPCG_ERR_INVALID, "handle %d appears twice", i);
+  }
+  mbpcg_batch_ctx* b = new (std::nothrow) mbpcg_batch_ctx;
+  if (!b) return set_err(MBPCG_ERR_OOM, "host allocation failed");
+  b->h.assign(handles, handles + count);
+  b->ready.assign(count, nullptr);
+  int rc = MBPCG_OK;
+  cudaError_t e = cudaSuccess;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = e == cudaSuccess ? 1 : 0;
+  }
+  for (int i = 0; e == cudaSuccess && i < count; ++i) e = cudaEventCreateWithFlags(&b->ready[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+  for (int i = 0; e == cudaSuccess && i < count; ++i) {
+    cudaGraphConditionalHandle cond{};
+    e = capture_solve(handles[i], g, &cond);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    rc = set_err(MBPCG_ERR_CUDA, "building the batch graph failed: %s", cudaGetErrorString(e));
+    mbpcg_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return MBPCG_OK;
+}
+
+int mbpcg_batch_solve_dev(mbpcg_batch bt, const double* const* b, const double* const* U, double tol, int32_t maxit,
+                          double* const* x_out, mbpcg_info* info) {
+  if (!bt) return set_err(MBPCG_ERR_INVALID, "null batch");
+  if (!b || !x_out) return set_err(MBPCG_ERR_INVALID, "b and x_out must not be NULL");
+  const int K = (int)bt->h.size();
+  std::vector<SolveLoop> L(K);
+  // every member: inputs in, parameters of its first inner solve, then the one batch launch
+  for (int i = 0; i < K; ++i) {
+    mbpcg_ctx* h = bt->h[i];
+    int rc = solve_begin(h, b[i], U ? U[i] : nullptr, tol, maxit, x_out[i], 1, 0, &L[i]);
+    if (!rc) rc = enqueue_inner_params(h, L[i]);
+    if (rc) return rc;
+    CUDA_TRY(cudaEventRecord(bt->ready[i], h->stream));
+    CUDA_TRY(cudaStreamWaitEvent(bt->stream, bt->ready[i], 0));
+  }
+  CUDA_TRY(cudaGraphLaunch(bt->exec, bt->stream));
+  CUDA_TRY(cudaEventRecord(bt->done, bt->stream));
+  for (int i = 0; i < K; ++i) {
+    CUDA_TRY(cudaStreamWaitEvent(bt->h[i]->stream, bt->done, 0));
+    int rc = fetch_state(bt->h[i]);
+    if (rc) return rc;
+  }
+  // restarts (or refinement steps) run on each member's own graph, concurrently on their streams
+  std::vector<int> active(K, 1);
+  for (bool any = true; any;) {
+    any = false;
+    for (int i = 0; i < K; ++i) {
+      if (!active[i]) continue;
+      int more = 0;
+      int rc = after_inner(bt->h[i], &L[i], &more);
+      if (!rc && more) rc = launch_inner(bt->h[i], L[i]);
+      if (!rc && more) rc = fetch_state(bt->h[i]);
+      if (rc) return rc;
+      active[i] = more;
+      any = any || more;
+    }
+  }
+  int status = MBPCG_OK;
+  for (int i = 0; i < K; ++i) {
+    int rc = solve_end(bt->h[i], L[i], x_out[i], 1, info ? &info[i] : nullptr);
+    if (rc) return rc;
+    if (status == MBPCG_OK && L[i].status != MBPCG_OK) status = L[i].status;
+  }
+  g_err.clear();
+  return status;
+}
 
 const char* mbpcg_status_string(int status) {
   switch (status) {

@@ -20,7 +20,7 @@
 // Roofline: 2 n^2 FP64 flop and 8 n^2 bytes of A per iteration. On GB300 the FP64 pipe (2 DFMA per
 // clock per SM) binds: n = 4096 takes 26.7 us at 2.07 GHz; A at the HBM read rate takes about 24 us.
 // Work split: each CTA owns a balanced range of rows (one CTA per SM). Its rows are cut into chunks
-// of 512 columns (8 double2 loads per lane), and the flat list of its chunks into 8 equal
+// of 512 columns (8 double2 loads per lane), and the flat list of its chunks into 16 equal
 // contiguous ranges, one per warp, so every warp streams the same number of bytes; the next chunk's
 // loads are in flight while the current one is multiplied (two independent FMA chains per lane).
 // A warp's range covers a few rows: each row fragment leaves one lane partial, and the partials of

@@ -23,11 +23,12 @@
 
 namespace {
 
-// Capacity: s <= 16 (partial-slot stride npack(16) + 16 + 1 = 153 -> 156 doubles) and up to 320
-// CTAs (2 per SM on a 152-SM GB300 needs 304), plus one slot for the reduced sums:
-// 321 * 156 doubles = 400 608 bytes, held by every GPU that loads the library until exit.
+// Capacity: s <= 16 (partial-slot stride npack(16) + 16 + 1 = 153 -> 156 doubles) and up to 1216
+// CTAs (a sparse product launches up to 8 per SM: 1216 on a 152-SM GB300), plus one slot for the
+// reduced sums: 1217 * 156 doubles = 1 518 816 bytes, held by every GPU that loads the library
+// until exit.
 constexpr int kMaxS = 16;
-constexpr int kMaxCtas = 320;
+constexpr int kMaxCtas = 1216;
 constexpr int kSlot = 156;
 constexpr size_t kScratchDoubles = (size_t)(kMaxCtas + 1) * kSlot;
 
@@ -113,7 +114,7 @@ extern "C" int mbpcg_k_spmm_gram_noalloc(int32_t n, const int32_t* row_ptr, cons
   if (nb > kMaxCtas || pstride > kSlot)
     return mbpcg::set_last_error(MBPCG_ERR_INVALID,
                                  "mbpcg_k_spmm_gram_noalloc: launch needs more partial slots than its static "
-                                 "scratch holds (more than 320 CTAs)");
+                                 "scratch holds (more than 1216 CTAs)");
   double* scratch = nullptr;
   const int rc = scratch_address(&scratch);
   if (rc != MBPCG_OK) return rc;

@@ -380,6 +380,10 @@ def test_invalid_inputs_fail_loudly(mb):
     with pytest.raises(mb.MBPCGError) as e:
         mb.Solver(D, s=2)
     assert e.value.status == 1
+    for M in (A, wl.dense_spd(40, 0)):  # the reserved precision value is refused, not mapped elsewhere
+        with pytest.raises(mb.MBPCGError) as e:
+            mb.Solver(M, s=2, precision=mb._native.MBPCG_MIXED_BF16)
+        assert e.value.status == 1 and "reserved" in mb.last_error()
 
 
 # ------------------------------------------------------------------ full-size workloads
@@ -483,8 +487,8 @@ RFREE_CASES = [
     ("diffusion10_s1_jacobi", lambda: wl.diffusion3d(10, 1), 1, 1, 0),
     ("stencil27_8_s16", lambda: wl.stencil27(8, 0), 16, 0, 0),
     ("dense200_s8", lambda: wl.dense_spd(200, 0), 8, 0, 0),
-    ("dense257_s3_jacobi_tc", lambda: wl.dense_spd(257, 1, 0.0, 3.0), 3, 1, 2),
-    ("dense300_s32_tc", lambda: wl.dense_spd(300, 2, 0.0, 4.0), 32, 0, 2),
+    ("dense257_s3_jacobi_tc", lambda: wl.dense_spd(257, 1, 0.0, 3.0), 3, 1, "tc"),
+    ("dense300_s32_tc", lambda: wl.dense_spd(300, 2, 0.0, 4.0), 32, 0, "tc"),
 ]
 
 
@@ -497,6 +501,7 @@ def test_implicit_residual_matches_oracle_and_explicit(mb, orc, name, factory, s
     n = A.n
     b = wl.rhs(n, 0)
     U = wl.initial_block(n, s, 1)
+    precision = mb.MBPCG_FP64_TC if precision == "tc" else precision
     sv = mb.Solver(A, s=s, precond=precond, precision=precision, residual_mode=mb.MBPCG_RESIDUAL_IMPLICIT)
     ex = mb.Solver(A, s=s, precond=precond, precision=precision)
     try:

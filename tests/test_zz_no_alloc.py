@@ -2,8 +2,8 @@
 cudaMalloc): two calls in a row through the C ABI must reproduce the scratch-taking entry point's
 output bit for bit (the same kernels run in the same launch shape, only the scratch differs), on the
 default stream and on a stream of the caller's, and oversize requests must be rejected.
-The rejection of launches wider than 320 CTAs cannot be reached on a GB300 (152 SMs give at most
-304); it is not exercised here. Collected last on purpose (file name), so a stop at the first
+The rejection of launches wider than 1216 CTAs cannot be reached on a GB300 (152 SMs give at most
+1216, 8 per SM); it is not exercised here. Collected last on purpose (file name), so a stop at the first
 failure has run every other test."""
 import numpy as np
 import pytest
