@@ -445,6 +445,7 @@ def run_ours(args, world, rank, local):
     AP = torch.empty_like(P)
     tc = dense and prec == mb.MBPCG_FP64_TC
     launch_gram = None
+    kstream = stream
     if dense and mixed:
         Ad = torch.as_tensor(np.asfortranarray(A.a).ravel(order="F"), device=dev)
         ftb = mb.mbpcg_k_dense_f32_bytes(n)
@@ -482,8 +483,10 @@ def run_ours(args, world, rank, local):
         av = torch.as_tensor(A.val.astype(np.float32), device=dev)
         P = P.float()
         AP = torch.empty_like(P)
-        launch = lambda: mb.mbpcg_k_spmm_f32(n, rp, ci, av, s, P, AP, stream.cuda_stream)  # noqa: E731
-        kname = "k_spmm_f"
+        # the solver's own FP32 product (the shape its autotuner kept), on the solver's stream
+        kstream = solver.stream
+        launch = lambda: mb.mbpcg_apply_dev(solver.h, 1, P, AP)  # noqa: E731
+        kname = "k_spmm_wide_f" if solver.product_kernel(fp32=True)[0] == mb.MBPCG_PRODUCT_CSR_WIDE else "k_spmm_f"
         flops = 2.0 * A.nnz * s
         nbytes = 8.0 * A.nnz + 4.0 * (n + 1) + 8.0 * n * kp  # FP32 values + int32 indices, P in, AP out
         gb = mb.mbpcg_k_scratch_bytes(n, s)
@@ -492,14 +495,14 @@ def run_ours(args, world, rank, local):
         launch_gram = lambda: mb.mbpcg_k_spmm_gram_f32(n, rp, ci, av, s, P, AP, Gd, gscr, gb,  # noqa: E731
                                                        stream.cuda_stream)
     else:
-        rp = torch.as_tensor(A.row_ptr, device=dev)
-        ci = torch.as_tensor(A.col_idx, device=dev)
-        av = torch.as_tensor(A.val, device=dev)
-        launch = lambda: mb.mbpcg_k_spmm(n, rp, ci, av, s, P, AP, stream.cuda_stream)  # noqa: E731
+        # the solver's own FP64 product (the scaled matrix under Jacobi), on the solver's stream
+        kstream = solver.stream
+        launch = lambda: mb.mbpcg_apply_dev(solver.h, 0, P, AP)  # noqa: E731
         kname = "k_spmm"
         flops = 2.0 * A.nnz * s
         nbytes = 12.0 * A.nnz + 4.0 * (n + 1) + 16.0 * n * kp
-    with torch.cuda.stream(stream):
+    kstream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(kstream):
         for _ in range(3):
             launch()
         k_ms = []
@@ -507,9 +510,9 @@ def run_ours(args, world, rank, local):
             l2_flush(flush)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
+            ev0.record(kstream)
             launch()
-            ev1.record(stream)
+            ev1.record(kstream)
             ev1.synchronize()
             k_ms.append(ev0.elapsed_time(ev1))
     k_avg = sum(k_ms) / len(k_ms)
@@ -593,6 +596,17 @@ def run_ours(args, world, rank, local):
         peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
         roofline = roofline_tc(n, s, kp, k_avg, single_ms, seq_ms, read_gbs, peaks,
                                recorded_traffic(kname, args.workload, s), args.kernel_launches)
+    elif not dense and (nbytes / (float(json.load(open(PEAKS_FILE)).get("hbm_gbs", 6800.0)) if os.path.exists(PEAKS_FILE)
+                                  else 6800.0) / 1e9 > flops / FP64_PEAK_TFLOPS / 1e12):
+        # a sparse FP64 product whose HBM floor exceeds its FP64-pipe floor (s = 1): bound by HBM
+        hbm_peak = float(json.load(open(PEAKS_FILE)).get("hbm_gbs", 6800.0)) if os.path.exists(PEAKS_FILE) else 6800.0
+        gbs = nbytes / (k_avg * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"{kname}<{kp}> (the solver's FP64 CSR product alone)",
+                    "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                    "traffic": recorded_traffic(kname, args.workload, s), "kernel_ms": round(k_avg, 5),
+                    "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if os.path.exists(PEAKS_FILE)
+                    else "fallback"}
     else:
         roofline = {"bound": "alu", "kernel": f"{kname}<{kp}> (FP64 pipe)", "achieved": round(achieved_tflops, 4),
                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
@@ -643,8 +657,9 @@ def run_ours(args, world, rank, local):
         if mixed and not dense:
             u, c, t = solver.spmm_tuning()
             line["spmm_autotune"] = {"unroll": u, "ctas_per_sm": c,
-                                     "times_us_(unroll,ctas_per_sm)": dict(zip(
-                                         ["4,4", "4,8", "4,16", "8,4", "8,8", "8,16"], [round(v, 2) for v in t]))}
+                                     "times_us_(variant,ctas_per_sm)": dict(zip(
+                                         ["4,4", "4,8", "4,16", "8,4", "8,8", "8,16", "0,2 tiled", "1,1 wide1024",
+                                          "1,2 wide1024", "2,2 wide512", "2,4 wide512"], [round(v, 2) for v in t]))}
         if fp64 is not None:
             f_ms = sum(f_times) / len(f_times)
             xfh = xf.cpu().numpy()

@@ -498,6 +498,36 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
   if (warp == 0) tmem_dealloc(tmem, C::kTmemCols);
 }
 
+// Sums of the raw partials of output o over the ns slices of its tile (slice stride `stride`
+// entries): the int64 parts exactly, the FP32 parts in FP64 in slice order. The first kOzSliceBatch
+// slices are loaded at once (predicated), so their L2 latencies overlap.
+constexpr int kOzSliceBatch = 8;
+__device__ __forceinline__ void oz_slice_sums(const OzPart& qp, size_t o, size_t stride, int ns, long long& si,
+                                              double& sf) {
+  long long vi[kOzSliceBatch];
+  float vf[kOzSliceBatch];
+#pragma unroll
+  for (int k = 0; k < kOzSliceBatch; ++k) {
+    vi[k] = 0;
+    vf[k] = 0.f;
+    if (k < ns) {
+      vi[k] = qp.qi[(size_t)k * stride + o];
+      vf[k] = qp.qf[(size_t)k * stride + o];
+    }
+  }
+  si = 0;
+  sf = 0.0;
+#pragma unroll
+  for (int k = 0; k < kOzSliceBatch; ++k) {
+    si += vi[k];
+    sf += (double)vf[k];
+  }
+  for (int k = kOzSliceBatch; k < ns; ++k) {
+    si += qp.qi[(size_t)k * stride + o];
+    sf += (double)qp.qf[(size_t)k * stride + o];
+  }
+}
+
 // (A P)_ij from the raw partials of the slices of row i's tile: the int64 parts summed exactly, the
 // FP32 parts summed in FP64 in slice order, one FMA, then the scale 2^(F_i + G_j) (a product by a
 // power of two: exact wherever ldexp is, which takes the rest).
@@ -521,12 +551,9 @@ __global__ void k_oz_sum(int n, int nW, const double* __restrict__ Qpart, double
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(q / n), i = (int)(q % n);  // consecutive threads: consecutive rows of column j
     const int ns = oz_slices(i / kOzMT, nW, nctas, U);
-    long long si = 0;
-    double sf = 0.0;
-    for (int k = 0; k < ns; ++k) {
-      si += qp.qi[(size_t)k * total + q];
-      sf += (double)qp.qf[(size_t)k * total + q];
-    }
+    long long si;
+    double sf;
+    oz_slice_sums(qp, q, total, ns, si, sf);
     Q[(size_t)i * KP + j] = oz_finish(si, sf, emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
   }
   if (blockIdx.x == 0 && threadIdx.x < KP) emaxP[threadIdx.x] = 0;
@@ -562,13 +589,9 @@ k_oz_sum_gram(int n, int nW, const double* __restrict__ Qpart, const double* __r
       double y = 0.0;
       if (i < r1) {
         const int ns = oz_slices(i / kOzMT, nW, nctas, U);
-        long long si = 0;
-        double sf = 0.0;
-        for (int k = 0; k < ns; ++k) {
-          const size_t o = ((size_t)k * KP + j) * n + i;
-          si += qp.qi[o];
-          sf += (double)qp.qf[o];
-        }
+        long long si;
+        double sf;
+        oz_slice_sums(qp, (size_t)j * n + i, total, ns, si, sf);
         y = oz_finish(si, sf, emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
       }
       Ys[rr * KP + j] = y;
