@@ -4,7 +4,7 @@
 // column) whose largest biased exponent is emax is written as
 //     x = 2^(emax - 1022) * sum_{t=0..7} d_t 2^(-7 - 7t)   (+ rounding below 2^-56 of the scale),
 // d_t an integer in [-127, 127] taken straight from the 53-bit significand (integer shifts): exact
-// in BF16 and in FP16. A product of two such digits is below 2^14.
+// in FP16. A product of two such digits is below 2^14.
 #pragma once
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -33,9 +33,6 @@ __device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDig
 #pragma unroll
   for (int t = 0; t < kOzDigits; ++t) d[t] = sgn * (int)((X >> (49 - 7 * t)) & 127ull);
 }
-
-// BF16 bit pattern of a small integer (exact: |v| <= 127 needs 7 significand bits).
-__device__ __forceinline__ uint16_t bf16_of_int(int v) { return (uint16_t)(__float_as_uint((float)v) >> 16); }
 
 // FP16 bit pattern of a small integer (exact: |v| <= 127).
 __device__ __forceinline__ uint16_t f16_of_int(int v) { return __half_as_ushort(__int2half_rn(v)); }

@@ -48,6 +48,7 @@ constexpr uint32_t kASetBytes = kOzMT * kOzSetK * kOzDigits;  // 16 KB: 128 rows
 constexpr int kOzAStages = 6;                          // A blocks in flight (shared memory)
 constexpr int kOzPBufs = 4;                            // P digit chunks in flight
 constexpr uint32_t kAColsPerSet = kOzDigits * kOzSetK / 2;  // TMEM columns of one converted block (64)
+constexpr int kOzABufs = 3;  // converted A blocks in TMEM: a conversion has two MMA steps of slack
 constexpr int kOzLevels = 9;                           // digit-pair levels t + u = 0..8 kept
 
 }  // namespace
@@ -126,8 +127,8 @@ template <int KPT>
 struct OzCfg {
   static constexpr uint32_t kPChunkBytes = kOzDigits * KPT * kOzKC * 2;
   static constexpr uint32_t kAccCols = kOzLevels * KPT;   // the accumulator: 9 levels x KPT columns
-  static constexpr uint32_t kTmemCols = 512;              // accumulator + two converted A blocks
-  static_assert(kAccCols + 2 * kAColsPerSet <= kTmemCols, "tensor memory of one CTA");
+  static constexpr uint32_t kTmemCols = 512;              // accumulator + kOzABufs converted A blocks
+  static_assert(kAccCols + kOzABufs * kAColsPerSet <= kTmemCols, "tensor memory of one CTA");
   static constexpr size_t kBarBytes = 1024;  // barriers + TMEM slot, keeps the blocks 1024-aligned
   static constexpr size_t kSmem = kBarBytes + (size_t)kOzAStages * kASetBytes + (size_t)kOzPBufs * kPChunkBytes;
 };
@@ -203,9 +204,9 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
   uint64_t* sempty = sfull + kOzAStages;               // [kOzAStages] A block converted (stage free)
   uint64_t* pfull = sempty + kOzAStages;               // [kOzPBufs] P chunk landed
   uint64_t* pempty = pfull + kOzPBufs;                 // [kOzPBufs] P chunk used by its MMAs
-  uint64_t* afull = pempty + kOzPBufs;                 // [2] TMEM A buffer written
-  uint64_t* aempty = afull + 2;                        // [2] TMEM A buffer read by its MMAs
-  uint64_t* accf = aempty + 2;                         // accumulator ready for draining
+  uint64_t* afull = pempty + kOzPBufs;                 // [kOzABufs] TMEM A buffer written
+  uint64_t* aempty = afull + kOzABufs;                 // [kOzABufs] TMEM A buffer read by its MMAs
+  uint64_t* accf = aempty + kOzABufs;                  // accumulator ready for draining
   uint64_t* acce = accf + 1;                           // accumulator drained
   uint64_t* fin = acce + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
@@ -233,7 +234,7 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
       mbar_init(&pfull[q], 1);
       mbar_init(&pempty[q], 1);
     }
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kOzABufs; ++q) {
       mbar_init(&afull[q], kOzConvWarps);
       mbar_init(&aempty[q], 1);
     }
@@ -250,7 +251,7 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
   const uint32_t tmem = *tmem_slot;
   const uint32_t abuf0 = tmem + C::kAccCols;
   // the split sum scales with this copy of the column exponents of P (it clears the live ones)
-  if (g == 0 && tid < KP) emaxP[kMaxKP + tid] = emaxP[tid];  // two A buffers of kAColsPerSet columns after the accumulator
+  if (g == 0 && tid < KP) emaxP[kMaxKP + tid] = emaxP[tid];
   int issued_a = 0, issued_p = 0;  // copies issued (producer thread only)
 
   if (warp == kOzProducerWarp) {
@@ -313,9 +314,9 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
       const long long f = f0 + (dir ? nwin - 1 - w : w);
       const int c0 = (int)(f % nW) * wl, nsets = (min(nK, c0 + wl) - c0) * kOzSetsPerChunk;
       for (int u = 0; u < nsets && ok; ++u, ++j) {
-        const int q = j % kOzAStages, ab = j & 1;
+        const int q = j % kOzAStages, ab = j % kOzABufs;
         ok = mbar_wait_bounded(&sfull[q], (uint32_t)((j / kOzAStages) & 1));
-        if (ok && j >= 2) ok = mbar_wait_bounded(&aempty[ab], (uint32_t)((j / 2 - 1) & 1));
+        if (ok && j >= kOzABufs) ok = mbar_wait_bounded(&aempty[ab], (uint32_t)((j / kOzABufs - 1) & 1));
         ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // tcgen05.st needs the whole warp
         if (!ok) break;
         tc_fence_after_sync();
@@ -360,8 +361,8 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
           ok = mbar_wait_bounded(&pfull[b], (uint32_t)((cc / kOzPBufs) & 1));
           const uint32_t b_base = smem_addr(Ps + (size_t)b * C::kPChunkBytes);
           for (int u = 0; u < kOzSetsPerChunk && ok; ++u, ++j) {
-            const int ab = j & 1;
-            ok = mbar_wait_bounded(&afull[ab], (uint32_t)((j / 2) & 1));
+            const int ab = j % kOzABufs;
+            ok = mbar_wait_bounded(&afull[ab], (uint32_t)((j / kOzABufs) & 1));
             if (!ok) break;
             tc_fence_after_sync();
             const uint32_t a_base = abuf0 + (uint32_t)ab * kAColsPerSet;

@@ -1,6 +1,6 @@
 // FP64-accurate products Y = X M of an n x K block X by a K x K matrix M (K = 32 or 16, the padded
-// width) on the BF16 tensor cores (tcgen05), by the exact digit splitting of ozaki_digits.cuh: X
-// split row by row (scale of the row), M column by column. These are the k x k-row products of the block update and of the W/P
+// width) on the FP16 tensor cores (tcgen05), by the exact digit splitting of ozaki_digits.cuh: X
+// split row by row (scale of the row), M column by column; a digit is exact in FP16. These are the k x k-row products of the block update and of the W/P
 // update of Algorithm 1 (P T, (AP) T, (AP) Xi; V zeta^{-1}, P zeta^T), which on the FP64 pipe of
 // this GPU (2 FMA per clock per SM) cost more than the A P product's digit stream.
 //
@@ -13,7 +13,7 @@
 //
 // One CTA of 256 threads per (128-row tile, product, 16 output columns: K / 16 CTAs): M is staged
 // in shared memory by one coalesced load; two threads per row write the 8 digits of their K / 2
-// values of X into shared memory (K-major, no swizzle: 8 tiles of 128 x K bf16; 16-byte stores of 8
+// values of X into shared memory (K-major, no swizzle: 8 tiles of 128 x K FP16; 16-byte stores of 8
 // consecutive digits; the row scale is combined by one shuffle), 2 K threads the 8 digits of the
 // CTA's 16 columns of M (128 x K: row 16 u + j holds digit u of column j); one thread issues
 // 8 K / 16 MMAs (digit t of X against digits 0..7-t of M, N = 16 (8 - t), into TMEM columns
@@ -55,13 +55,22 @@ __device__ __forceinline__ double scale2(double v, int k) {
                                                             : ldexp(v, k);
 }
 
-// 8 bf16 digits (16 bytes) for 8 consecutive values of the reduction index
+// Two digits (|d| <= 127) as an FP16 pair (the first in the low half), with integer operations and
+// one half-precision subtraction: 1024 + (d + 128) is an FP16 with bits 0x6400 + d + 128 (exact for
+// 0 <= d + 128 < 1024), and subtracting 1024 + 128 from both halves at once leaves d exactly.
+__device__ __forceinline__ uint32_t f16_pair_of_ints(int d0, int d1) {
+  const uint32_t b = (uint32_t)(0x6480 + d0) | ((uint32_t)(0x6480 + d1) << 16);
+  const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&b), __half2half2(__ushort_as_half(0x6480)));
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// 8 FP16 digits (16 bytes) for 8 consecutive values of the reduction index
 __device__ __forceinline__ uint4 pack8(const int (&d)[8]) {
   uint4 v;
-  v.x = (uint32_t)bf16_of_int(d[0]) | ((uint32_t)bf16_of_int(d[1]) << 16);
-  v.y = (uint32_t)bf16_of_int(d[2]) | ((uint32_t)bf16_of_int(d[3]) << 16);
-  v.z = (uint32_t)bf16_of_int(d[4]) | ((uint32_t)bf16_of_int(d[5]) << 16);
-  v.w = (uint32_t)bf16_of_int(d[6]) | ((uint32_t)bf16_of_int(d[7]) << 16);
+  v.x = f16_pair_of_ints(d[0], d[1]);
+  v.y = f16_pair_of_ints(d[2], d[3]);
+  v.z = f16_pair_of_ints(d[4], d[5]);
+  v.w = f16_pair_of_ints(d[6], d[7]);
   return v;
 }
 
@@ -156,10 +165,10 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
     const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
 #pragma unroll
     for (int t = 0; t < kOzDigits; ++t) {
-      const uint32_t idesc = umma_idesc_bf16_f32(kRpRows, kRpN * (kOzDigits - t));
+      const uint32_t idesc = umma_idesc_f16_f32(kRpRows, kRpN * (kOzDigits - t));
 #pragma unroll
       for (int k = 0; k < K / 16; ++k)
-        umma_bf16(tmem + (uint32_t)(kRpN * t), umma_smem_desc(a0 + (uint32_t)t * C::ATile + 256u * k, 128, C::Sbo),
+        umma_ss(tmem + (uint32_t)(kRpN * t), umma_smem_desc(a0 + (uint32_t)t * C::ATile + 256u * k, 128, C::Sbo),
                   umma_smem_desc(b0 + 256u * k, 128, C::Sbo), idesc, (t == 0 && k == 0) ? 0u : 1u);
     }
     umma_commit(bar);
@@ -178,19 +187,20 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
       acc_f[j] = 0.f;
     }
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q4) << 16);
+    uint32_t rv[kOzDigits][kDn];  // all levels' loads in flight together, one wait
+#pragma unroll
+    for (int L = 0; L < kOzDigits; ++L) tmem_ld8(lane_base + (uint32_t)(kRpN * L + c0), rv[L]);
+    tmem_wait_ld();
 #pragma unroll
     for (int L = 0; L < kOzDigits; ++L) {
-      uint32_t rv[kDn];
-      tmem_ld8(lane_base + (uint32_t)(kRpN * L + c0), rv);
-      tmem_wait_ld();
       if (L < 5) {
         const int sh = 7 * (4 - L);
 #pragma unroll
-        for (int j = 0; j < kDn; ++j) acc_i[j] += (long long)__float2int_rn(__uint_as_float(rv[j])) << sh;
+        for (int j = 0; j < kDn; ++j) acc_i[j] += (long long)__float2int_rn(__uint_as_float(rv[L][j])) << sh;
       } else {
         const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : 0x1p-14f;
 #pragma unroll
-        for (int j = 0; j < kDn; ++j) acc_f[j] = fmaf(__uint_as_float(rv[j]), sc, acc_f[j]);
+        for (int j = 0; j < kDn; ++j) acc_f[j] = fmaf(__uint_as_float(rv[L][j]), sc, acc_f[j]);
       }
     }
     // Y = 2^(e + f - 2100) (acc_i 2^14 + round(acc_f 2^7)): exact in int64 (|acc_i| < 2^48; the

@@ -1,8 +1,8 @@
 // 5th-generation tensor-core (tcgen05) building blocks for sm_103a, as inline PTX: tensor-memory
-// allocation, the shared-memory matrix descriptor, the instruction descriptor of kind::f16 with BF16
+// allocation, the shared-memory matrix descriptor, the instruction descriptor of kind::f16 with FP16
 // inputs and an FP32 accumulator, MMA issue, commit to an mbarrier, and accumulator loads.
 //
-// Operand layout used with these descriptors: K-major, no swizzle. A tile of R rows x K bf16 is
+// Operand layout used with these descriptors: K-major, no swizzle. A tile of R rows x K 16-bit values is
 // stored as "core matrices" of 8 rows x 16 bytes (8 elements), each core matrix 128 contiguous
 // bytes (row r at byte 16 r). Core matrices adjacent along K are LBO = 128 bytes apart, groups of
 // 8 rows are SBO = (K / 8) * 128 bytes apart. One MMA consumes K = 16 (two core matrices along K);
@@ -14,7 +14,7 @@
 
 namespace mbpcg {
 
-// Canonical K-major no-swizzle byte offset of element (r, k) inside an R x K bf16 tile.
+// Canonical K-major no-swizzle byte offset of element (r, k) inside an R x K tile of 16-bit values.
 __host__ __device__ inline uint32_t umma_kmajor_offset(int r, int k, int K) {
   return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
@@ -31,14 +31,9 @@ __device__ inline uint64_t umma_smem_desc(uint32_t smem_byte_addr, uint32_t lbo,
   return d;
 }
 
-// Instruction descriptor of tcgen05.mma kind::f16: D format F32 (bits 4-5 = 1), A and B format BF16
-// (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in
-// bits 24-28.
-__host__ __device__ inline uint32_t umma_idesc_bf16_f32(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// The same for kind::f16 with FP16 inputs (A and B format 0) and an FP32 accumulator.
+// Instruction descriptor of tcgen05.mma kind::f16 with FP16 inputs (A and B format 0) and an FP32
+// accumulator: D format F32 (bits 4-5 = 1), both operands K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
 __host__ __device__ inline uint32_t umma_idesc_f16_f32(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -62,8 +57,9 @@ __device__ __forceinline__ void tc_fence_after_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// D[tmem] (+)= A * B^T over K = 16, M = 128, N given by idesc. accumulate = 0 overwrites D.
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+// D[tmem] (+)= A * B^T over K = 16, M = 128, N and the operand types given by idesc, both operands
+// in shared memory. accumulate = 0 overwrites D.
+__device__ __forceinline__ void umma_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -74,7 +70,7 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
 }
 
 // The same with A read from tensor memory: a_tmem is the column of A's first K pair (lane i = row i;
-// each 32-bit column holds two consecutive bf16 of K, the lower K in the low half; K = 16 takes
+// each 32-bit column holds two consecutive 16-bit values of K, the lower K in the low half; K = 16 takes
 // 8 columns).
 __device__ __forceinline__ void umma_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
                                                  uint32_t accumulate) {

@@ -227,3 +227,38 @@ def test_small_systems_have_no_plan_and_dense_handles_one_product(mb):
             sv.set_product_kernel(mb.MBPCG_PRODUCT_CSR_GATHER)
     finally:
         sv.close()
+
+
+@pytest.mark.parametrize("form", ["fp64", "tc", "mixed"])
+def test_dense_apply_matches_the_oracle(mb, form):
+    """mbpcg_apply_dev on dense handles: the FP64 product (rounding of an FP64 row sum), the
+    tensor-core product (1e-14 |A||P|, the bound of the digit-split product) and the FP32 product of a
+    mixed handle (FP32 rounding of the oracle's product of the same FP32 data); n = 1031 spans several
+    128-row tiles and a ragged last one."""
+    A = wl.dense_spd(1031, 3, 0.0, 4.0)
+    n, s = A.n, 16
+    prec = {"fp64": mb.MBPCG_FP64, "tc": mb.MBPCG_FP64_TC, "mixed": mb.MBPCG_MIXED_FP32}[form]
+    sv = mb.Solver(A, s=s, precision=prec)
+    try:
+        kernel = sv.product_kernel(fp32=form == "mixed")[0]
+        assert kernel == {"fp64": mb.MBPCG_PRODUCT_DENSE, "tc": mb.MBPCG_PRODUCT_DENSE_TC,
+                          "mixed": mb.MBPCG_PRODUCT_DENSE_FP32}[form]
+        X = torch.as_tensor(wl.initial_block(n, s, 4)).reshape(n, s).contiguous().cuda()
+        absA = np.abs(np.asarray(A.a))
+        if form == "mixed":
+            Xf = X.to(torch.float32).contiguous()
+            Y = sv.apply(Xf, fp32=True).cpu().numpy().astype(np.float64)
+            A32 = wl.Dense(n, np.asfortranarray(np.asarray(A.a).astype(np.float32).astype(np.float64)))
+            Xh = Xf.cpu().numpy().astype(np.float64)
+            ref = oracle.matmat(A32, Xh)
+            bound = 2.0 * n * 2.0 ** -24 * (absA @ np.abs(Xh)) + 1e-300
+        else:
+            Y = sv.apply(X).cpu().numpy()
+            Xh = X.cpu().numpy()
+            ref = oracle.matmat(A, Xh)
+            u = 2.0 ** -53 if form == "fp64" else 1e-14 / (2.0 * n)
+            bound = 2.0 * n * u * (absA @ np.abs(Xh)) + 1e-300
+        err = np.abs(Y - ref)
+        assert np.all(err <= bound), float((err / bound).max())
+    finally:
+        sv.close()
