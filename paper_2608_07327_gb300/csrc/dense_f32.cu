@@ -205,11 +205,7 @@ k_dense_f(int n, const float* __restrict__ At, const float* __restrict__ P, floa
 template <int KP>
 void dense_f32_kp(cudaStream_t s, int n, int sms, const float* At, const float* P, float* Q, const SolveState* st) {
   using C = DfCfg<KP>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_dense_f<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    attr = true;
-  }
+  ensure_dynamic_smem(k_dense_f<KP>, C::SMEM);
   const int mt = (n + kDfBM - 1) / kDfBM, nKc = (n + kDfBK - 1) / kDfBK;
   int ks = sms / mt;
   ks = ks < 1 ? 1 : (ks > kDfMaxCluster ? kDfMaxCluster : ks);

@@ -9,6 +9,19 @@
 
 namespace mbpcg {
 
+// Opt-in dynamic shared memory of a kernel: set when the kernel's attribute on the current device is
+// below `bytes`. Checked on every launch -- the attribute belongs to the device's context, which
+// another device, another thread's first launch or a device reset does not share with a flag.
+template <typename K>
+inline cudaError_t ensure_dynamic_smem(K* func, size_t bytes) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, (const void*)func);
+  if (e != cudaSuccess) return e;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute((const void*)func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+
 // Host launchers of the row kernels for one padded width KP (defined in inst_kp*.cu).
 struct RowOps {
   int kp;

@@ -667,11 +667,7 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
                           uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st,
                           double* part, int pstride, int nb, int exp_ready) {
   using C = OzCfg<KPT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_dense_tc<KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
-    attr = true;
-  }
+  ensure_dynamic_smem(k_dense_tc<KPT>, C::kSmem);
   const OzSplit sp(n, sms > 0 ? sms : 1);
   const int g = (int)(((size_t)n * KP + 255) / 256);
   if (!exp_ready) {
@@ -691,11 +687,7 @@ template <int KPT>
 static void oz_mma_kp(cudaStream_t s, int n, int KP, int sms, const uint8_t* Atiles, const int* emaxA,
                       const uint8_t* Pchunks, const int* emaxP, double* Qpart) {
   using C = OzCfg<KPT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_dense_tc<KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
-    attr = true;
-  }
+  ensure_dynamic_smem(k_dense_tc<KPT>, C::kSmem);
   const OzSplit sp(n, sms > 0 ? sms : 1);
   k_dense_tc<KPT><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks,
                                                        const_cast<int*>(emaxP), Qpart, oz_ksplit(n, sms), nullptr,

@@ -231,11 +231,7 @@ template <int K>
 static void rowprod_tc_k(cudaStream_t s, int n, const RowProdJobs& jobs, int njobs, const SolveState* st,
                          int skip_on_pw, int* err) {
   using C = RpCfg<K>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_rowprod_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::Smem);
-    attr = true;
-  }
+  ensure_dynamic_smem(k_rowprod_tc<K>, C::Smem);
   k_rowprod_tc<K><<<dim3((n + kRpRows - 1) / kRpRows, C::Halves * njobs), kRpThreads, C::Smem, s>>>(n, jobs, st,
                                                                                                     skip_on_pw, err);
 }

@@ -202,12 +202,8 @@ template <int KP>
 void tiled_kp(cudaStream_t s, int nb, int n, const int* rp, const double* av, const SpmmPlan& pl, const double* P,
               double* Q, double* part, int pstride, const SolveState* st, int gram) {
   const size_t smem = spmm_plan_smem(KP, sizeof(double), pl.wmax);
-  static bool attr = false;  // the opt-in shared-memory size is a property of the kernels
-  if (!attr) {
-    cudaFuncSetAttribute(k_spmm_tiled<KP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWindowBytes);
-    cudaFuncSetAttribute(k_spmm_tiled<KP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWindowBytes);
-    attr = true;
-  }
+  ensure_dynamic_smem(k_spmm_tiled<KP, true>, kWindowBytes);
+  ensure_dynamic_smem(k_spmm_tiled<KP, false>, kWindowBytes);
   if (gram) k_spmm_tiled<KP, true><<<nb, kThreads, smem, s>>>(n, rp, av, pl, P, Q, part, pstride, st);
   else k_spmm_tiled<KP, false><<<nb, kThreads, smem, s>>>(n, rp, av, pl, P, Q, part, pstride, st);
 }
@@ -216,11 +212,7 @@ template <int KP>
 void tiled_f_kp(cudaStream_t s, int nb, int n, const int* rp, const float* av, const SpmmPlan& pl, const float* P,
                 float* Q, const SolveState* st) {
   const size_t smem = spmm_plan_smem(KP, sizeof(float), pl.wmax);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_spmm_tiled_f<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWindowBytes);
-    attr = true;
-  }
+  ensure_dynamic_smem(k_spmm_tiled_f<KP>, kWindowBytes);
   k_spmm_tiled_f<KP><<<nb, kThreads, smem, s>>>(n, rp, av, pl, P, Q, st);
 }
 
