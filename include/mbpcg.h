@@ -217,7 +217,20 @@ typedef enum {
 int mbpcg_get_product_kernel(mbpcg_handle h, int32_t fp32, int32_t* kernel, float* times_us);
 int mbpcg_set_product_kernel(mbpcg_handle h, int32_t kernel);
 
-/* Batches of uneven systems (NEXT row "batching"; not in the paper). A batch binds count existing
+/* Rounding of the tensor-core product (MBPCG_FP64_TC handles; MBPCG_ERR_INVALID otherwise). The
+ * product's digit-pair levels 0..4 are always summed exactly (int64); levels 5..8 (below 2^-49 of
+ * the row and column scales) are, by default, carried in FP32 per window of 128 values of the
+ * reduction index (MBPCG_ROUND_FP32_TAIL: error about 6e-16 ||A P|| on the benchmark system, and
+ * iteration counts inside the band of the FP64 oracle). MBPCG_ROUND_ONCE keeps them as exact
+ * integers too, so the product is rounded once, at the end (16 instead of 12 bytes of scratch per
+ * partial, no FP32 rounding). Not in the paper: on a dense SPD system of n = 4096, kappa = 1e6,
+ * s = 32, the solve then took 2144 iterations against 2354 with the default and 2388-2406 for the
+ * FP64 method the paper describes -- its own product rounding slows that method there. Takes
+ * effect at the next solve. */
+typedef enum { MBPCG_ROUND_FP32_TAIL = 0, MBPCG_ROUND_ONCE = 1 } mbpcg_product_rounding;
+int mbpcg_set_product_rounding(mbpcg_handle h, int32_t mode);
+
+/* Batches of uneven systems/* Batches of uneven systems (NEXT row "batching"; not in the paper). A batch binds count existing
  * handles -- any mix of CSR and dense matrices, sizes, block widths, algorithms and precisions,
  * each created with MBPCG_LAUNCH_GRAPH -- and captures one inner solve of each (set-up, the
  * device-side WHILE loop, the exit) as an independent chain of ONE CUDA graph, built once at

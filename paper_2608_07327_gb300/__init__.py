@@ -20,7 +20,8 @@ from ._native import (  # noqa: F401  (re-exported C ABI names)
     mbpcg_set_residual_mode, MBPCG_RESIDUAL_EXPLICIT,
     MBPCG_RESIDUAL_IMPLICIT, mbpcg_get_spmm_tuning, mbpcg_set_spmm_shape, mbpcg_apply_dev, mbpcg_get_product_kernel,
     mbpcg_set_product_kernel, MBPCG_PRODUCT_CSR_GATHER, MBPCG_PRODUCT_CSR_TILED, MBPCG_PRODUCT_CSR_WIDE, MBPCG_PRODUCT_DENSE,
-    MBPCG_PRODUCT_DENSE_TC, MBPCG_PRODUCT_DENSE_FP32)
+    MBPCG_PRODUCT_DENSE_TC, MBPCG_PRODUCT_DENSE_FP32, mbpcg_set_product_rounding, MBPCG_ROUND_FP32_TAIL,
+    MBPCG_ROUND_ONCE)
 
 from ._native import (  # noqa: F401,E402
     mbpcg_server_create, mbpcg_server_destroy, mbpcg_server_get_stats, mbpcg_server_submit_csr, mbpcg_server_wait)
@@ -193,6 +194,12 @@ class Solver:
         """(kernel, [gather_us, tiled_us]): the MBPCG_PRODUCT_* kernel of the FP64 (or FP32) product
         and the FP64 times measured at create."""
         return mbpcg_get_product_kernel(self.h, 1 if fp32 else 0)
+
+    def set_product_rounding(self, mode: int):
+        """MBPCG_ROUND_FP32_TAIL (default) or MBPCG_ROUND_ONCE for the tensor-core product."""
+        st = mbpcg_set_product_rounding(self.h, mode)
+        if st != MBPCG_OK:
+            raise MBPCGError(st, "mbpcg_set_product_rounding")
 
     def set_product_kernel(self, kernel: int):
         st = mbpcg_set_product_kernel(self.h, kernel)

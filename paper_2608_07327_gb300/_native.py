@@ -29,6 +29,8 @@ MBPCG_LAUNCH_GRAPH = 0
 MBPCG_LAUNCH_EAGER = 1
 MBPCG_RESIDUAL_EXPLICIT = 0
 MBPCG_RESIDUAL_IMPLICIT = 1
+MBPCG_ROUND_FP32_TAIL = 0
+MBPCG_ROUND_ONCE = 1
 MBPCG_PRODUCT_CSR_GATHER = 0
 MBPCG_PRODUCT_CSR_TILED = 1
 MBPCG_PRODUCT_CSR_WIDE = 2
@@ -108,6 +110,7 @@ _SIGS = {
     "mbpcg_batch_destroy": (None, [_P]),
     "mbpcg_get_product_kernel": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]),
     "mbpcg_set_product_kernel": (ctypes.c_int, [_P, _I32]),
+    "mbpcg_set_product_rounding": (ctypes.c_int, [_P, _I32]),
     "mbpcg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mbpcg_last_error": (ctypes.c_char_p, []),
     "mbpcg_k_padded_width": (_I32, [_I32]),
@@ -413,3 +416,7 @@ def mbpcg_get_product_kernel(h, fp32=0):
 
 def mbpcg_set_product_kernel(h, kernel):
     return lib().mbpcg_set_product_kernel(h, kernel)
+
+
+def mbpcg_set_product_rounding(h, mode):
+    return lib().mbpcg_set_product_rounding(h, mode)

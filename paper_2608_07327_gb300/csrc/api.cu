@@ -196,7 +196,7 @@ Layout make_layout(const Dims& dm) {
     L.oz_p = take(oz_p_chunks_bytes(dm.n, dm.kp));
     L.oz_ep = take(2 * kMaxKP * sizeof(int));  // the column exponents of P and the product's copy of them
     // raw partial sums of the product's slices: int64 and FP32 per entry
-    L.oz_q = take((size_t)oz_ksplit(dm.n, dm.sms) * n * dm.kp * (sizeof(long long) + sizeof(float)));
+    L.oz_q = take((size_t)oz_ksplit(dm.n, dm.sms) * n * dm.kp * 2 * sizeof(long long));
     if (dm_uses_rowprod(dm)) L.rp3 = take(3 * n * dm.kp * sizeof(double));
   }
   L.part = take((size_t)dm.nbmax * dm.pstride * sizeof(double));
@@ -250,6 +250,7 @@ struct mbpcg_ctx {
   SpmmPlan plan;    // CSR: rows of P staged per tile (see spmm_tiled.cu)
   int use_tiled;    // 1: the matrix has a tiling plan
   int prod64;       // the FP64 CSR product kernel: MBPCG_PRODUCT_CSR_GATHER or _TILED
+  int round_once;   // tensor-core product: MBPCG_ROUND_ONCE (levels 5..8 exact) instead of the FP32 carry
   float spmm64_us[2];  // the FP64 product at create: gather and tiled kernels (0: not timed)
   cudaEvent_t e0, e1;
 };
@@ -623,7 +624,7 @@ void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y
   if (dm.dense && dm.tc) {
     // the loop's product reads P, whose column exponents the W/P update has already formed
     oz_product(h->stream, dm.n, dm.kp, dm.sms, h->oz_a, h->oz_ea, X, h->oz_p, h->oz_ep, h->oz_q, Y, &h->st->kerr, st,
-               gram ? h->part : nullptr, dm.pstride, dm.nb, X == h->P ? 1 : 0);
+               gram ? h->part : nullptr, dm.pstride, dm.nb, X == h->P ? 1 : 0, h->round_once);
   } else if (dm.dense) {
     ops->dense(h->stream, dm.nb_dense, dm.n, h->A, X, Y, st, &h->st->kerr);
     if (gram) ops->gram(h->stream, dm.nb, dm.n, X, Y, h->part, dm.pstride, st);
@@ -1249,6 +1250,21 @@ int mbpcg_get_product_kernel(mbpcg_handle h, int32_t fp32, int32_t* kernel, floa
   return MBPCG_OK;
 }
 
+int mbpcg_set_product_rounding(mbpcg_handle h, int32_t mode) {
+  if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
+  if (!h->dm.tc) return set_err(MBPCG_ERR_INVALID, "the rounding mode belongs to MBPCG_FP64_TC handles");
+  if (mode != MBPCG_ROUND_FP32_TAIL && mode != MBPCG_ROUND_ONCE)
+    return set_err(MBPCG_ERR_INVALID, "mode must be MBPCG_ROUND_FP32_TAIL or MBPCG_ROUND_ONCE");
+  const int once = mode == MBPCG_ROUND_ONCE ? 1 : 0;
+  if (h->graph_ready && once != h->round_once) {  // the captured launches change
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->exec);
+    h->graph_ready = 0;
+  }
+  h->round_once = once;
+  return MBPCG_OK;
+}
+
 int mbpcg_set_product_kernel(mbpcg_handle h, int32_t kernel) {
   if (!h) return set_err(MBPCG_ERR_INVALID, "null handle");
   if (h->dm.dense) return set_err(MBPCG_ERR_INVALID, "a dense handle has one FP64 product");
@@ -1538,7 +1554,7 @@ size_t mbpcg_k_dense_tc_scratch_bytes(int32_t n, int32_t s) {
   const int kp = padded_width(s), sms = num_sms() > 0 ? num_sms() : 1;
   return align_up(oz_a_tiles_bytes(n)) + align_up((size_t)n * sizeof(int)) + align_up(oz_p_chunks_bytes(n, kp)) +
          align_up(2 * kMaxKP * sizeof(int)) +
-         align_up((size_t)oz_ksplit(n, sms) * n * kp * (sizeof(long long) + sizeof(float)));
+         align_up((size_t)oz_ksplit(n, sms) * n * kp * 2 * sizeof(long long));
 }
 
 namespace {
@@ -1607,7 +1623,7 @@ int mbpcg_k_dense_tc_product(int32_t n, int32_t s, const double* P, double* AP, 
   const int kp = padded_width(s);
   const TcScratch t = tc_scratch(scratch, n, kp);
   oz_product((cudaStream_t)stream, n, kp, num_sms(), t.at, t.ea, P, t.pc, t.ep, t.qp, AP, nullptr, nullptr, nullptr, 0,
-             0, 0);
+             0, 0, 0);
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

@@ -241,9 +241,12 @@ void rowprod_tc(cudaStream_t s, int n, int kp, const RowProdJobs& jobs, int njob
 // The MMA kernel alone (k_dense_tc) on P digits already in Pchunks: partial slices into Qpart.
 void oz_mma(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const uint8_t* Pchunks,
             const int* emaxP, double* Qpart);
+// The whole product: column exponents and digits of P (unless exp_ready), the MMA kernel, the split
+// sum (with the Gram partials when part != NULL). once = 1: levels 5..8 exact too, the product
+// rounded once at the end; 0: levels 5..8 carried in FP32 per window (the default).
 void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
                 uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st, double* part,
-                int pstride, int nb, int exp_ready);
+                int pstride, int nb, int exp_ready, int once);
 
 // single-warp k x k steps of the loop (small_warp.cu)
 void launch_small_sigma(cudaStream_t s, int kp, SolveState* st, const double* Gp, double* Sigma, double* SigmaInv);

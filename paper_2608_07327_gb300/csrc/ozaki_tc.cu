@@ -31,6 +31,8 @@
 // separate warps; every wait is bounded.
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 #include "ozaki_digits.cuh"
 #include "tcgen05.cuh"
@@ -172,12 +174,14 @@ __device__ __forceinline__ uint32_t oz_f16_pair(uint32_t w, uint32_t sel) {
 // FP64 units for the last ~5 us of the product).
 struct OzPart {
   long long* qi;
-  float* qf;
+  float* qf;      // levels 5..8 carried in FP32 (the default rounding)
+  long long* ql;  // levels 5..8 as exact integers in units of 2^-70 (rounded once: same storage)
 };
 __host__ __device__ inline OzPart oz_part(double* Qpart, int n, int kp, int ksplit) {
   OzPart p;
   p.qi = reinterpret_cast<long long*>(Qpart);
-  p.qf = reinterpret_cast<float*>(p.qi + (size_t)ksplit * n * kp);
+  p.ql = p.qi + (size_t)ksplit * n * kp;
+  p.qf = reinterpret_cast<float*>(p.ql);
   return p;
 }
 
@@ -192,7 +196,7 @@ __host__ __device__ inline OzPart oz_part(double* Qpart, int n, int kp, int kspl
 //   drain (8 warps, thread = row, half of the columns each): after each window of 128 values of l,
 //     levels 0..4 exact into int64, 5..7 in FP32, then the accumulator is released to the next
 //     window (one accumulator: the tensor memory also holds the two A buffers).
-template <int KPT>
+template <int KPT, bool ONCE>
 __global__ void __launch_bounds__(kOzTcThreads, 1)
 k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ablocks, const int* __restrict__ emaxA,
            const uint8_t* __restrict__ Pchunks, int* __restrict__ emaxP, double* __restrict__ Qpart, int ksplit,
@@ -408,11 +412,12 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
     constexpr int DC = KPT / kOzDrainGroups;
     const int half = warp >> 2;  // column group of this warp
     long long acc_i[DC];
-    float acc_f[DC];
+    using Lo = typename std::conditional<ONCE, long long, float>::type;
+    Lo acc_f[DC];
 #pragma unroll
     for (int jj = 0; jj < DC; ++jj) {
       acc_i[jj] = 0;
-      acc_f[jj] = 0.f;
+      acc_f[jj] = 0;
     }
     bool ok = true;
     for (int w = 0; w < nwin; ++w) {
@@ -450,9 +455,15 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
 #pragma unroll
             for (int jj = 0; jj < DC; ++jj) acc_i[jj] += (long long)__float2int_rn(__uint_as_float(rr[q][jj])) << sh;
           } else if (L < kOzLevels) {
-            const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : (L == 7) ? 0x1p-14f : 0x1p-21f;
+            if constexpr (ONCE) {  // exact: a window's level sum is an integer below 2^24
+              const int sh = 7 * (kOzLevels - 1 - L);
 #pragma unroll
-            for (int jj = 0; jj < DC; ++jj) acc_f[jj] = fmaf(__uint_as_float(rr[q][jj]), sc, acc_f[jj]);
+              for (int jj = 0; jj < DC; ++jj) acc_f[jj] += (long long)__float2int_rn(__uint_as_float(rr[q][jj])) << sh;
+            } else {
+              const float sc = (L == 5) ? 1.f : (L == 6) ? 0x1p-7f : (L == 7) ? 0x1p-14f : 0x1p-21f;
+#pragma unroll
+              for (int jj = 0; jj < DC; ++jj) acc_f[jj] = fmaf(__uint_as_float(rr[q][jj]), sc, acc_f[jj]);
+            }
           }
         }
       }
@@ -468,14 +479,15 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
             if (j < KP) {
               const size_t o = ((size_t)slice * KP + j) * n + row;
               qp.qi[o] = acc_i[jj];
-              qp.qf[o] = acc_f[jj];
+              if constexpr (ONCE) qp.ql[o] = acc_f[jj];
+              else qp.qf[o] = acc_f[jj];
             }
           }
         }
 #pragma unroll
         for (int jj = 0; jj < DC; ++jj) {
           acc_i[jj] = 0;
-          acc_f[jj] = 0.f;
+          acc_f[jj] = 0;
         }
       }
     }
@@ -500,40 +512,44 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
 }
 
 // Sums of the raw partials of output o over the ns slices of its tile (slice stride `stride`
-// entries): the int64 parts exactly, the FP32 parts in FP64 in slice order. The first kOzSliceBatch
-// slices are loaded at once (predicated), so their L2 latencies overlap.
+// entries): the int64 parts exactly; the levels 5..8 parts exactly too when they are integers
+// (ONCE), else FP32 values summed in FP64 in slice order. The first kOzSliceBatch slices are loaded
+// at once (predicated), so their L2 latencies overlap. Returns the product before its scale.
 constexpr int kOzSliceBatch = 8;
-__device__ __forceinline__ void oz_slice_sums(const OzPart& qp, size_t o, size_t stride, int ns, long long& si,
-                                              double& sf) {
+template <bool ONCE>
+__device__ __forceinline__ double oz_slice_value(const OzPart& qp, size_t o, size_t stride, int ns) {
   long long vi[kOzSliceBatch];
-  float vf[kOzSliceBatch];
+  typename std::conditional<ONCE, long long, float>::type vf[kOzSliceBatch];
 #pragma unroll
   for (int k = 0; k < kOzSliceBatch; ++k) {
     vi[k] = 0;
-    vf[k] = 0.f;
+    vf[k] = 0;
     if (k < ns) {
       vi[k] = qp.qi[(size_t)k * stride + o];
-      vf[k] = qp.qf[(size_t)k * stride + o];
+      if constexpr (ONCE) vf[k] = qp.ql[(size_t)k * stride + o];
+      else vf[k] = qp.qf[(size_t)k * stride + o];
     }
   }
-  si = 0;
-  sf = 0.0;
+  long long si = 0;
+  typename std::conditional<ONCE, long long, double>::type sf = 0;
 #pragma unroll
   for (int k = 0; k < kOzSliceBatch; ++k) {
     si += vi[k];
-    sf += (double)vf[k];
+    if constexpr (ONCE) sf += vf[k];
+    else if (k < ns) sf += (double)vf[k];
   }
   for (int k = kOzSliceBatch; k < ns; ++k) {
     si += qp.qi[(size_t)k * stride + o];
-    sf += (double)qp.qf[(size_t)k * stride + o];
+    if constexpr (ONCE) sf += qp.ql[(size_t)k * stride + o];
+    else sf += (double)qp.qf[(size_t)k * stride + o];
   }
+  // levels 0..4 in units of 2^-42, levels 5..8 in units of 2^-49 (FP32 carry) or 2^-70 (exact)
+  if constexpr (ONCE) return fma((double)sf, 0x1p-70, (double)si * 0x1p-42);
+  else return fma(sf, 0x1p-49, (double)si * 0x1p-42);
 }
 
-// (A P)_ij from the raw partials of the slices of row i's tile: the int64 parts summed exactly, the
-// FP32 parts summed in FP64 in slice order, one FMA, then the scale 2^(F_i + G_j) (a product by a
-// power of two: exact wherever ldexp is, which takes the rest).
-__device__ __forceinline__ double oz_finish(long long si, double sf, int e) {
-  const double v = fma(sf, 0x1p-49, (double)si * 0x1p-42);
+// v 2^e: a product by a power of two (exact) wherever ldexp is, which takes the rest.
+__device__ __forceinline__ double oz_scale(double v, int e) {
   if (e >= -1022 && e <= 1023) return v * __longlong_as_double((long long)(e + 1023) << 52);
   return ldexp(v, e);
 }
@@ -541,7 +557,7 @@ __device__ __forceinline__ double oz_finish(long long si, double sf, int e) {
 // Q[i][j] = the product from the slices of row i's tile (in slice order). Block 0 then clears the
 // column exponents of P for the next product (they are rebuilt by the W/P update, which writes
 // P); the scaling reads the copy the MMA kernel made of them.
-template <int KP>
+template <int KP, bool ONCE>
 __global__ void k_oz_sum(int n, int nW, const double* __restrict__ Qpart, double* __restrict__ Q,
                          const int* __restrict__ emaxA, int* __restrict__ emaxP, const SolveState* __restrict__ st,
                          int nctas, int ksplit) {
@@ -552,17 +568,14 @@ __global__ void k_oz_sum(int n, int nW, const double* __restrict__ Qpart, double
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(q / n), i = (int)(q % n);  // consecutive threads: consecutive rows of column j
     const int ns = oz_slices(i / kOzMT, nW, nctas, U);
-    long long si;
-    double sf;
-    oz_slice_sums(qp, q, total, ns, si, sf);
-    Q[(size_t)i * KP + j] = oz_finish(si, sf, emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
+    Q[(size_t)i * KP + j] = oz_scale(oz_slice_value<ONCE>(qp, q, total, ns), emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
   }
   if (blockIdx.x == 0 && threadIdx.x < KP) emaxP[threadIdx.x] = 0;
 }
 
 // The same split sum fused with the CTA partials of the upper triangle of P^T Q (the Gram of the
 // Xi step of Algorithm 1), one pass over balanced row ranges (partials as k_gram writes them).
-template <int KP>
+template <int KP, bool ONCE>
 __global__ void __launch_bounds__(kThreads)
 k_oz_sum_gram(int n, int nW, const double* __restrict__ Qpart, const double* __restrict__ P, double* __restrict__ Q,
               const int* __restrict__ emaxA, int* __restrict__ emaxP, double* __restrict__ part, int pstride,
@@ -590,10 +603,8 @@ k_oz_sum_gram(int n, int nW, const double* __restrict__ Qpart, const double* __r
       double y = 0.0;
       if (i < r1) {
         const int ns = oz_slices(i / kOzMT, nW, nctas, U);
-        long long si;
-        double sf;
-        oz_slice_sums(qp, (size_t)j * n + i, total, ns, si, sf);
-        y = oz_finish(si, sf, emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
+        y = oz_scale(oz_slice_value<ONCE>(qp, (size_t)j * n + i, total, ns),
+                     emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
       }
       Ys[rr * KP + j] = y;
     }
@@ -662,12 +673,12 @@ void oz_prepare_a(cudaStream_t s, int n, const double* A, int* emaxA, uint8_t* A
   k_oz_slice_a8<<<4096, 256, 0, s>>>(n, nS, A, emaxA, Atiles);
 }
 
-template <int KP, int KPT>
+template <int KP, int KPT, bool ONCE>
 static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
                           uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st,
                           double* part, int pstride, int nb, int exp_ready) {
   using C = OzCfg<KPT>;
-  ensure_dynamic_smem(k_dense_tc<KPT>, C::kSmem);
+  ensure_dynamic_smem(k_dense_tc<KPT, ONCE>, C::kSmem);
   const OzSplit sp(n, sms > 0 ? sms : 1);
   const int g = (int)(((size_t)n * KP + 255) / 256);
   if (!exp_ready) {
@@ -676,22 +687,22 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
   }
   k_oz_slice_p<KP, KPT><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
   const int ks = oz_ksplit(n, sms);
-  k_dense_tc<KPT><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks, emaxP,
-                                                       Qpart, ks, err, st, 0);
+  k_dense_tc<KPT, ONCE><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks,
+                                                             emaxP, Qpart, ks, err, st, 0);
   if (part != nullptr)
-    k_oz_sum_gram<KP><<<nb, kThreads, 0, s>>>(n, sp.nW, Qpart, P, Q, emaxA, emaxP, part, pstride, st, sp.G, ks);
-  else k_oz_sum<KP><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, sp.nW, Qpart, Q, emaxA, emaxP, st, sp.G, ks);
+    k_oz_sum_gram<KP, ONCE><<<nb, kThreads, 0, s>>>(n, sp.nW, Qpart, P, Q, emaxA, emaxP, part, pstride, st, sp.G, ks);
+  else k_oz_sum<KP, ONCE><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, sp.nW, Qpart, Q, emaxA, emaxP, st, sp.G, ks);
 }
 
 template <int KPT>
 static void oz_mma_kp(cudaStream_t s, int n, int KP, int sms, const uint8_t* Atiles, const int* emaxA,
                       const uint8_t* Pchunks, const int* emaxP, double* Qpart) {
   using C = OzCfg<KPT>;
-  ensure_dynamic_smem(k_dense_tc<KPT>, C::kSmem);
+  ensure_dynamic_smem(k_dense_tc<KPT, false>, C::kSmem);
   const OzSplit sp(n, sms > 0 ? sms : 1);
-  k_dense_tc<KPT><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks,
-                                                       const_cast<int*>(emaxP), Qpart, oz_ksplit(n, sms), nullptr,
-                                                       nullptr, 0);
+  k_dense_tc<KPT, false><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks,
+                                                              const_cast<int*>(emaxP), Qpart, oz_ksplit(n, sms),
+                                                              nullptr, nullptr, 0);
 }
 
 void oz_mma(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const uint8_t* Pchunks,
@@ -702,16 +713,20 @@ void oz_mma(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const
 
 void oz_product(cudaStream_t s, int n, int kp, int sms, const uint8_t* Atiles, const int* emaxA, const double* P,
                 uint8_t* Pchunks, int* emaxP, double* Qpart, double* Q, int* err, const SolveState* st, double* part,
-                int pstride, int nb, int exp_ready) {
+                int pstride, int nb, int exp_ready, int once) {
 #define OZ_ARGS s, n, sms, Atiles, emaxA, P, Pchunks, emaxP, Qpart, Q, err, st, part, pstride, nb, exp_ready
+#define OZ_CASE(KP, KPT)                                                         \
+  if (once) oz_product_kp<KP, KPT, true>(OZ_ARGS);                                \
+  else oz_product_kp<KP, KPT, false>(OZ_ARGS);
   switch (kp) {
-    case 1: oz_product_kp<1, 16>(OZ_ARGS); break;
-    case 2: oz_product_kp<2, 16>(OZ_ARGS); break;
-    case 4: oz_product_kp<4, 16>(OZ_ARGS); break;
-    case 8: oz_product_kp<8, 16>(OZ_ARGS); break;
-    case 16: oz_product_kp<16, 16>(OZ_ARGS); break;
-    default: oz_product_kp<32, 32>(OZ_ARGS); break;
+    case 1: OZ_CASE(1, 16) break;
+    case 2: OZ_CASE(2, 16) break;
+    case 4: OZ_CASE(4, 16) break;
+    case 8: OZ_CASE(8, 16) break;
+    case 16: OZ_CASE(16, 16) break;
+    default: OZ_CASE(32, 32) break;
   }
+#undef OZ_CASE
 #undef OZ_ARGS
 }
 

@@ -569,3 +569,31 @@ def test_breakdown_matches_oracle(mb, orc, form, case):
     assert io["status"] == 6
     assert (info["status"], info["iterations"], info["restarts"]) == (io["status"], io["iterations"], io["restarts"])
     assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo), (x, xo)
+
+
+@pytest.mark.parametrize("name", ["dense300_s32_tc", "dense257_s12_jacobi_tc"])
+def test_round_once_product_solves_and_leaves_the_default_intact(mb, orc, name):
+    """MBPCG_ROUND_ONCE (levels 5..8 of the digit-split product exact, one rounding at the end): the
+    solve meets tol on the true residual recomputed here, its solution is within 2 kappa tol of the
+    oracle's, and switching back to the default rounding gives the default's bits again."""
+    _, factory, s, precond = next(c for c in TC_CASES if c[0] == name)
+    A = factory()
+    n = A.n
+    b = wl.rhs(n, 0)
+    U = wl.initial_block(n, s, 1)
+    sv = mb.Solver(A, s=s, precond=precond, precision=mb.MBPCG_FP64_TC)
+    try:
+        x0, i0 = sv.solve(b, U, tol=1e-8, maxit=100000)
+        sv.set_product_rounding(mb.MBPCG_ROUND_ONCE)
+        x1, i1 = sv.solve(b, U, tol=1e-8, maxit=100000)
+        sv.set_product_rounding(mb.MBPCG_ROUND_FP32_TAIL)
+        x2, i2 = sv.solve(b, U, tol=1e-8, maxit=100000)
+    finally:
+        sv.close()
+    assert np.array_equal(x0, x2) and i0["iterations"] == i2["iterations"]
+    M = np.asarray(A.a)
+    assert i1["status"] == 0 and np.linalg.norm(b - M @ x1) <= 1.1e-8 * np.linalg.norm(b)
+    xo, _, io = orc.mbpcg(A, b, U, precond=precond, tol=1e-8)
+    kap = kappa_scaled(A, precond)
+    assert np.linalg.norm(x1 - xo) <= 2 * kap * 1e-8 * np.linalg.norm(xo)
+    print(f"[round once] {name}: {i1['iterations']} iterations (default {i0['iterations']}, oracle {io['iterations']})")

@@ -229,20 +229,26 @@ def test_small_systems_have_no_plan_and_dense_handles_one_product(mb):
         sv.close()
 
 
-@pytest.mark.parametrize("form", ["fp64", "tc", "mixed"])
+@pytest.mark.parametrize("form", ["fp64", "tc", "tc_once", "mixed"])
 def test_dense_apply_matches_the_oracle(mb, form):
     """mbpcg_apply_dev on dense handles: the FP64 product (rounding of an FP64 row sum), the
-    tensor-core product (1e-14 |A||P|, the bound of the digit-split product) and the FP32 product of a
-    mixed handle (FP32 rounding of the oracle's product of the same FP32 data); n = 1031 spans several
+    tensor-core product in both rounding modes (1e-14 |A||P|, the bound of the digit-split product)
+    and the FP32 product of a mixed handle (FP32 rounding of the oracle's product of the same FP32 data); n = 1031 spans several
     128-row tiles and a ragged last one."""
     A = wl.dense_spd(1031, 3, 0.0, 4.0)
     n, s = A.n, 16
-    prec = {"fp64": mb.MBPCG_FP64, "tc": mb.MBPCG_FP64_TC, "mixed": mb.MBPCG_MIXED_FP32}[form]
+    prec = {"fp64": mb.MBPCG_FP64, "tc": mb.MBPCG_FP64_TC, "tc_once": mb.MBPCG_FP64_TC,
+            "mixed": mb.MBPCG_MIXED_FP32}[form]
     sv = mb.Solver(A, s=s, precision=prec)
     try:
+        if form == "tc_once":
+            sv.set_product_rounding(mb.MBPCG_ROUND_ONCE)
+        elif form != "tc":
+            with pytest.raises(mb.MBPCGError):  # the rounding mode belongs to tensor-core handles
+                sv.set_product_rounding(mb.MBPCG_ROUND_ONCE)
         kernel = sv.product_kernel(fp32=form == "mixed")[0]
         assert kernel == {"fp64": mb.MBPCG_PRODUCT_DENSE, "tc": mb.MBPCG_PRODUCT_DENSE_TC,
-                          "mixed": mb.MBPCG_PRODUCT_DENSE_FP32}[form]
+                          "tc_once": mb.MBPCG_PRODUCT_DENSE_TC, "mixed": mb.MBPCG_PRODUCT_DENSE_FP32}[form]
         X = torch.as_tensor(wl.initial_block(n, s, 4)).reshape(n, s).contiguous().cuda()
         absA = np.abs(np.asarray(A.a))
         if form == "mixed":
