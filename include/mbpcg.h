@@ -200,12 +200,14 @@ int mbpcg_apply_dev(mbpcg_handle h, int32_t fp32, const void* X, void* Y);
  * shared-memory window (a plan built at create), the rows of P a tile reads are staged in shared
  * memory once and the nonzeros address them by 16-bit local indices. All sum each row in the order
  * of its nonzeros: A P is the same bits whichever runs; TILED groups the loop's Gram partials by
- * tile (other rounding). For FP64, GATHER and (with a plan) TILED are timed at create on the
- * handle's own matrix, with the loop's Gram, for the record -- times_us (may be NULL) receives the
- * two measured microseconds per launch, 0 when not timed -- and GATHER is kept, so a solve's result
- * never depends on a timing. For FP32 the autotuner of mbpcg_get_spmm_tuning picks among all.
- * mbpcg_set_product_kernel imposes the FP64 kernel of a CSR handle (CSR_TILED needs a plan; mixed
- * handles have none for FP64). */
+ * tile (other rounding). For FP64, GATHER is the loop's product, so a solve's result never
+ * depends on a timing; it is timed at create on the handle's own matrix, with the loop's Gram, and
+ * TILED when imposed -- times_us (may be NULL) receives the two measured microseconds per launch,
+ * 0 when not timed. The plan of an FP64 handle is built on the host when CSR_TILED is first
+ * imposed (a sort of every tile's columns: it is not paid at create); mixed handles build it at
+ * create for the autotuner of mbpcg_get_spmm_tuning, which picks among all FP32 kernels.
+ * mbpcg_set_product_kernel imposes the FP64 kernel of a CSR handle (CSR_TILED needs a plan;
+ * MBPCG_ERR_INVALID when the matrix has none, or for a mixed handle). */
 typedef enum {
   MBPCG_PRODUCT_CSR_GATHER = 0,
   MBPCG_PRODUCT_CSR_TILED = 1,

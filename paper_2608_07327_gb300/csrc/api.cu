@@ -249,6 +249,7 @@ struct mbpcg_ctx {
   int use_cond;     // 1 while the loop body is captured into the WHILE node
   SpmmPlan plan;    // CSR: rows of P staged per tile (see spmm_tiled.cu)
   int use_tiled;    // 1: the matrix has a tiling plan
+  int plan_tried;   // 1: build_plan has run (a plan is built at most once)
   int prod64;       // the FP64 CSR product kernel: MBPCG_PRODUCT_CSR_GATHER or _TILED
   int round_once;   // tensor-core product: MBPCG_ROUND_ONCE (levels 5..8 exact) instead of the FP32 carry
   float spmm64_us[2];  // the FP64 product at create: gather and tiled kernels (0: not timed)
@@ -490,10 +491,14 @@ int autotune_spmm_f(mbpcg_ctx* h) {
 
 // The tiled product's plan (spmm_tiled.cu) for a validated CSR matrix of at least kTiledMinRows
 // rows, when every tile's window fits and the runs fit the workspace; otherwise the handle keeps
-// the gather kernel. The structure is read on the host (copied back when it was given on the device).
+// the gather kernel. The structure is read on the host (copied back when it was given on the device,
+// or when row_ptr is NULL: the handle's own copy). Built at most once per handle.
 int build_plan(mbpcg_ctx* h, const int* row_ptr, const int* col_idx, int mem) {
   const Dims& dm = h->dm;
+  if (h->plan_tried) return MBPCG_OK;
+  h->plan_tried = 1;
   h->use_tiled = 0;
+  if (!row_ptr) mem = 1;
   if (dm.n < kTiledMinRows || dm.nnz < 1) return MBPCG_OK;
   std::vector<int> rp_h, ci_h;
   const int* rp = row_ptr;
@@ -531,34 +536,31 @@ int build_plan(mbpcg_ctx* h, const int* row_ptr, const int* col_idx, int mem) {
 }
 
 // The FP64 CSR product of the loop (with the Gram partials for MBPCG, as the loop launches it) timed
-// with the gather kernel and, with a plan, the tiled kernel on the handle's own matrix, for the
-// record (mbpcg_get_product_kernel). Both sum each row of A P in the same order (the same bits); the
-// tiled kernel groups the Gram partials by tile (other rounding). The gather kernel stays the
-// loop's product -- it was the faster on every stencil measured, and a solve's result must not
-// depend on a timing -- and the tiled kernel runs only when imposed (mbpcg_set_product_kernel).
+// with kernel v on the handle's own matrix, for the record (mbpcg_get_product_kernel): the gather
+// kernel at create, the tiled kernel when its plan is built. Both sum each row of A P in the same
+// order (the same bits); the tiled kernel groups the Gram partials by tile (other rounding). The
+// gather kernel stays the loop's product -- it was the faster on every stencil measured, and a
+// solve's result must not depend on a timing -- and the tiled kernel runs only when imposed.
 void enqueue_product(mbpcg_ctx* h, const RowOps* ops, const double* X, double* Y, int gram, const SolveState* st);
 
-int autotune_spmm64(mbpcg_ctx* h) {
+int time_spmm64(mbpcg_ctx* h, int v) {
   const Dims& dm = h->dm;
   const RowOps* ops = row_ops(dm.kp);
   const int gram = h->algo == MBPCG_ALGO_MBPCG ? 1 : 0;
   const double* X = gram ? h->P : h->r;
   double* Y = gram ? h->Q : h->w;
+  const int keep = h->prod64;
   CUDA_TRY(cudaMemsetAsync((void*)X, 0, (size_t)dm.n * dm.kp * sizeof(double), h->stream));
-  for (int v : {MBPCG_PRODUCT_CSR_GATHER, MBPCG_PRODUCT_CSR_TILED}) {
-    h->spmm64_us[v] = 0.f;
-    if (v == MBPCG_PRODUCT_CSR_TILED && !h->use_tiled) continue;
-    h->prod64 = v;
-    enqueue_product(h, ops, X, Y, gram, nullptr);
-    CUDA_TRY(cudaEventRecord(h->e0, h->stream));
-    for (int r = 0; r < 3; ++r) enqueue_product(h, ops, X, Y, gram, nullptr);
-    CUDA_TRY(cudaEventRecord(h->e1, h->stream));
-    CUDA_TRY(cudaEventSynchronize(h->e1));
-    float ms = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&ms, h->e0, h->e1));
-    h->spmm64_us[v] = ms * 1e3f / 3.f;
-  }
-  h->prod64 = MBPCG_PRODUCT_CSR_GATHER;
+  h->prod64 = v;
+  enqueue_product(h, ops, X, Y, gram, nullptr);
+  CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+  for (int r = 0; r < 3; ++r) enqueue_product(h, ops, X, Y, gram, nullptr);
+  CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+  CUDA_TRY(cudaEventSynchronize(h->e1));
+  h->prod64 = keep;
+  float ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, h->e0, h->e1));
+  h->spmm64_us[v] = ms * 1e3f / 3.f;
   return MBPCG_OK;
 }
 
@@ -604,7 +606,8 @@ int finish_create(mbpcg_ctx* h) {
   }
   // (a mixed handle's loop has no FP64 product: mbpcg_apply_dev alone reaches it, by the gather kernel)
   if (!h->dm.dense && !h->dm.mixed) {
-    int rc = autotune_spmm64(h);
+    h->prod64 = MBPCG_PRODUCT_CSR_GATHER;
+    int rc = time_spmm64(h, MBPCG_PRODUCT_CSR_GATHER);
     if (rc) return rc;
   }
   if (h->dm.cg_fused) CUDA_TRY(cg_dense_configure(n, h->dm.nb_cg));
@@ -1124,7 +1127,10 @@ int mbpcg_create_csr(mbpcg_handle* out, int32_t n, int64_t nnz, const int32_t* r
   int flag = 0;
   rc = read_flag(h, &flag);
   if (!rc && (flag & 1)) rc = set_err(MBPCG_ERR_INVALID, "malformed CSR (row_ptr or col_idx out of range)");
-  if (!rc) rc = build_plan(h, row_ptr, col_idx, mem);
+  // the plan costs a sort of every tile's columns on the host: built at create only where the
+  // autotuner may pick the tiled kernel (the FP32 product of a mixed handle); an FP64 handle builds
+  // it when the tiled kernel is imposed (mbpcg_set_product_kernel)
+  if (!rc && h->dm.mixed) rc = build_plan(h, row_ptr, col_idx, mem);
   if (!rc) rc = finish_create(h);
   if (rc) {
     release(h);
@@ -1270,6 +1276,11 @@ int mbpcg_set_product_kernel(mbpcg_handle h, int32_t kernel) {
   if (h->dm.dense) return set_err(MBPCG_ERR_INVALID, "a dense handle has one FP64 product");
   if (kernel != MBPCG_PRODUCT_CSR_GATHER && kernel != MBPCG_PRODUCT_CSR_TILED)
     return set_err(MBPCG_ERR_INVALID, "kernel must be MBPCG_PRODUCT_CSR_GATHER or MBPCG_PRODUCT_CSR_TILED");
+  if (kernel == MBPCG_PRODUCT_CSR_TILED && !h->dm.mixed && !h->plan_tried) {
+    int rc = build_plan(h, nullptr, nullptr, 1);
+    if (!rc && h->use_tiled) rc = time_spmm64(h, MBPCG_PRODUCT_CSR_TILED);
+    if (rc) return rc;
+  }
   if (kernel == MBPCG_PRODUCT_CSR_TILED && (!h->use_tiled || h->dm.mixed))
     return set_err(MBPCG_ERR_INVALID, "this handle's FP64 product has no tiling plan");
   if (h->graph_ready && kernel != h->prod64) {  // the captured launches change

@@ -34,7 +34,13 @@ __device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDig
   for (int t = 0; t < kOzDigits; ++t) d[t] = sgn * (int)((X >> (49 - 7 * t)) & 127ull);
 }
 
-// FP16 bit pattern of a small integer (exact: |v| <= 127).
-__device__ __forceinline__ uint16_t f16_of_int(int v) { return __half_as_ushort(__int2half_rn(v)); }
+// Two digits (|d| <= 127) as an FP16 pair (the first in the low half), with integer operations and
+// one half-precision subtraction: 1024 + (d + 128) is an FP16 with bits 0x6400 + d + 128 (exact for
+// 0 <= d + 128 < 1024), and subtracting 1024 + 128 from both halves at once leaves d exactly.
+__device__ __forceinline__ uint32_t oz_f16_pair_of_ints(int d0, int d1) {
+  const uint32_t b = (uint32_t)(0x6480 + d0) | ((uint32_t)(0x6480 + d1) << 16);
+  const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&b), __half2half2(__ushort_as_half(0x6480)));
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
 
 }  // namespace mbpcg

@@ -108,20 +108,32 @@ __global__ void k_oz_colexp(int n, const double* __restrict__ P, int* __restrict
 }
 
 // Digits of P into chunks [kchunk] of (8 * KPT) x 64 fp16, row index KPT * t + j (canonical
-// K-major layout, so digit t of every column j is one contiguous N-range).
+// K-major layout, so digit t of every column j is one contiguous N-range). A thread takes 8
+// consecutive values of l of one column (lanes: consecutive columns, so each of its 8 loads is
+// coalesced across the warp) and writes digit t of them as one 16-byte store (8 consecutive k of a
+// core-matrix row); values past n are written as zero digits.
 template <int KP, int KPT>
 __global__ void k_oz_slice_p(int n, const double* __restrict__ P, const int* __restrict__ emaxP,
                              uint16_t* __restrict__ chunks, const SolveState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   constexpr uint32_t kChunkElems = kOzDigits * KPT * kOzKC;
-  const size_t total = (size_t)n * KP;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-    const int l = (int)(q / KP), j = (int)(q % KP);
-    int d[kOzDigits];
-    ozaki_digits(P[q], emaxP[j], d);
-    uint16_t* ch = chunks + (size_t)(l / kOzKC) * kChunkElems;
+  const size_t groups = (size_t)((n + 7) / 8) * KP;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < groups; q += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q % KP), l0 = (int)(q / KP) * 8;
+    const int ej = emaxP[j];
+    int d[8][kOzDigits];
 #pragma unroll
-    for (int t = 0; t < kOzDigits; ++t) ch[umma_kmajor_offset(KPT * t + j, l % kOzKC, kOzKC) / 2] = f16_of_int(d[t]);
+    for (int e = 0; e < 8; ++e) ozaki_digits(l0 + e < n ? P[(size_t)(l0 + e) * KP + j] : 0.0, ej, d[e]);
+    uint16_t* ch = chunks + (size_t)(l0 / kOzKC) * kChunkElems;
+#pragma unroll
+    for (int t = 0; t < kOzDigits; ++t) {
+      uint4 v;
+      v.x = oz_f16_pair_of_ints(d[0][t], d[1][t]);
+      v.y = oz_f16_pair_of_ints(d[2][t], d[3][t]);
+      v.z = oz_f16_pair_of_ints(d[4][t], d[5][t]);
+      v.w = oz_f16_pair_of_ints(d[6][t], d[7][t]);
+      *reinterpret_cast<uint4*>(ch + umma_kmajor_offset(KPT * t + j, l0 % kOzKC, kOzKC) / 2) = v;
+    }
   }
 }
 
@@ -185,17 +197,19 @@ __host__ __device__ inline OzPart oz_part(double* Qpart, int n, int kp, int kspl
   return p;
 }
 
-// Qpart[k][i][j] = the part of (A P)_ij over the K range of slice k of row i's tile, for j < KP.
-// Warp-specialised, all waits bounded:
-//   producers (one thread each): A digit blocks (32 KB, 32 values of l) into kOzAStages shared
-//     stages, and P digit chunks (64 values of l) into kOzPBufs buffers, by 1-D TMA bulk copies on
-//     mbarriers;
-//   converters (4 warps, thread = row): a block's bytes -> FP16 digits in one of two TMEM A buffers;
-//   MMA issuer (one thread): per block and digit t of A, two tcgen05.mma (K = 16 each) with A from
-//     TMEM and the P digits from shared memory into levels t..7 of the accumulator;
-//   drain (8 warps, thread = row, half of the columns each): after each window of 128 values of l,
-//     levels 0..4 exact into int64, 5..7 in FP32, then the accumulator is released to the next
-//     window (one accumulator: the tensor memory also holds the two A buffers).
+// Raw partials of (A P)_ij over the K range of slice k of row i's tile (OzPart layout), for j < KP.
+// Warp-specialised (23 warps), all waits bounded:
+//   producers (one thread each): A digit blocks (16 KB: 128 rows x 16 values of l x 8 digit bytes)
+//     into kOzAStages shared stages, and P digit chunks (64 values of l) into kOzPBufs buffers, by
+//     1-D TMA bulk copies on mbarriers;
+//   converters (4 warps, thread = row): a block's bytes -> FP16 digits in one of kOzABufs TMEM A
+//     buffers (tcgen05.st);
+//   MMA issuer (one thread): per block and digit t of A, one tcgen05.mma (K = 16) with A from TMEM
+//     and all needed digits of P from shared memory into levels t..min(t + 7, 8) of the accumulator;
+//   drain (16 warps, thread = row, a quarter of the columns each): after each window of 128 values
+//     of l, the 9 levels are copied out of TMEM in two rounds and the accumulator is released to
+//     the next window (one accumulator: the tensor memory also holds the A buffers); levels 0..4
+//     are added exactly into int64, levels 5..8 in FP32 (or exactly into int64 with ONCE).
 template <int KPT, bool ONCE>
 __global__ void __launch_bounds__(kOzTcThreads, 1)
 k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ablocks, const int* __restrict__ emaxA,
@@ -685,7 +699,8 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
     cudaMemsetAsync(emaxP, 0, sizeof(int) * KP, s);
     k_oz_colexp<KP><<<g < 1024 ? g : 1024, 256, 0, s>>>(n, P, emaxP, st);
   }
-  k_oz_slice_p<KP, KPT><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
+  const int gs = (int)(((size_t)(n + 7) / 8 * KP + 255) / 256);
+  k_oz_slice_p<KP, KPT><<<gs < 4096 ? gs : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
   const int ks = oz_ksplit(n, sms);
   k_dense_tc<KPT, ONCE><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks,
                                                              emaxP, Qpart, ks, err, st, 0);

@@ -55,22 +55,13 @@ __device__ __forceinline__ double scale2(double v, int k) {
                                                             : ldexp(v, k);
 }
 
-// Two digits (|d| <= 127) as an FP16 pair (the first in the low half), with integer operations and
-// one half-precision subtraction: 1024 + (d + 128) is an FP16 with bits 0x6400 + d + 128 (exact for
-// 0 <= d + 128 < 1024), and subtracting 1024 + 128 from both halves at once leaves d exactly.
-__device__ __forceinline__ uint32_t f16_pair_of_ints(int d0, int d1) {
-  const uint32_t b = (uint32_t)(0x6480 + d0) | ((uint32_t)(0x6480 + d1) << 16);
-  const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&b), __half2half2(__ushort_as_half(0x6480)));
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-
 // 8 FP16 digits (16 bytes) for 8 consecutive values of the reduction index
 __device__ __forceinline__ uint4 pack8(const int (&d)[8]) {
   uint4 v;
-  v.x = f16_pair_of_ints(d[0], d[1]);
-  v.y = f16_pair_of_ints(d[2], d[3]);
-  v.z = f16_pair_of_ints(d[4], d[5]);
-  v.w = f16_pair_of_ints(d[6], d[7]);
+  v.x = oz_f16_pair_of_ints(d[0], d[1]);
+  v.y = oz_f16_pair_of_ints(d[2], d[3]);
+  v.z = oz_f16_pair_of_ints(d[4], d[5]);
+  v.w = oz_f16_pair_of_ints(d[6], d[7]);
   return v;
 }
 

@@ -109,11 +109,13 @@ def test_fp64_tiled_product_matches_the_oracle_and_the_gather_kernel(mb, name, s
     sv = mb.Solver(A, s=s, algo=algo)
     try:
         kernel, times = sv.product_kernel()
-        assert min(times) > 0.0, "a plan is expected for this matrix"
         assert kernel == mb.MBPCG_PRODUCT_CSR_GATHER  # the loop's FP64 product never depends on a timing
+        assert times[0] > 0.0 and times[1] == 0.0  # the plan is built when the tiled kernel is imposed
         kp = 1 if algo == 1 else mb.mbpcg_k_padded_width(s)
         X = torch.as_tensor(wl.initial_block(A.n, kp, 3)).reshape(A.n, kp).contiguous().cuda()
         sv.set_product_kernel(mb.MBPCG_PRODUCT_CSR_TILED)
+        kernel, times = sv.product_kernel()
+        assert kernel == mb.MBPCG_PRODUCT_CSR_TILED and times[1] > 0.0, "a plan is expected for this matrix"
         Yt = sv.apply(X)
         sv.set_product_kernel(mb.MBPCG_PRODUCT_CSR_GATHER)
         Yg = sv.apply(X)
