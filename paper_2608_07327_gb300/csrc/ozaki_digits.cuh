@@ -17,8 +17,8 @@ __device__ __forceinline__ int biased_exponent(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// The 8 signed base-128 digits of x relative to the scale 2^(emax - 1022).
-__device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDigits]) {
+// |x| 2^(1022 - emax) 2^56 as an integer below 2^56 (the 8 digits' bits), and the sign of x.
+__device__ __forceinline__ unsigned long long ozaki_magnitude(double x, int emax, int& sgn) {
   const long long bits = __double_as_longlong(x);
   const int e = (int)((bits >> 52) & 0x7FF);
   unsigned long long X = 0;
@@ -29,9 +29,21 @@ __device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDig
     // to nearest there (a truncation would bias every product towards zero)
     X = shift >= 0 ? (mant << shift) : (shift > -60 ? ((mant + (1ull << (-shift - 1))) >> (-shift)) : 0ull);
   }
-  const int sgn = bits < 0 ? -1 : 1;
+  sgn = bits < 0 ? -1 : 1;
+  return X;
+}
+
+// Digit t of a magnitude from ozaki_magnitude.
+__device__ __forceinline__ int ozaki_digit(unsigned long long X, int sgn, int t) {
+  return sgn * (int)((X >> (49 - 7 * t)) & 127ull);
+}
+
+// The 8 signed base-128 digits of x relative to the scale 2^(emax - 1022).
+__device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDigits]) {
+  int sgn;
+  const unsigned long long X = ozaki_magnitude(x, emax, sgn);
 #pragma unroll
-  for (int t = 0; t < kOzDigits; ++t) d[t] = sgn * (int)((X >> (49 - 7 * t)) & 127ull);
+  for (int t = 0; t < kOzDigits; ++t) d[t] = ozaki_digit(X, sgn, t);
 }
 
 // Two digits (|d| <= 127) as an FP16 pair (the first in the low half), with integer operations and

@@ -108,31 +108,25 @@ __global__ void k_oz_colexp(int n, const double* __restrict__ P, int* __restrict
 }
 
 // Digits of P into chunks [kchunk] of (8 * KPT) x 64 fp16, row index KPT * t + j (canonical
-// K-major layout, so digit t of every column j is one contiguous N-range). A thread takes 8
-// consecutive values of l of one column (lanes: consecutive columns, so each of its 8 loads is
-// coalesced across the warp) and writes digit t of them as one 16-byte store (8 consecutive k of a
-// core-matrix row); values past n are written as zero digits.
+// K-major layout, so digit t of every column j is one contiguous N-range). One thread per value.
+// (Forms with 16-byte stores -- a thread taking 8 consecutive values of a column, or digit t of
+// them -- were slower: 8.4 against 5.5 us at n = 4096, KP = 32.)
 template <int KP, int KPT>
 __global__ void k_oz_slice_p(int n, const double* __restrict__ P, const int* __restrict__ emaxP,
                              uint16_t* __restrict__ chunks, const SolveState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   constexpr uint32_t kChunkElems = kOzDigits * KPT * kOzKC;
-  const size_t groups = (size_t)((n + 7) / 8) * KP;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < groups; q += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(q % KP), l0 = (int)(q / KP) * 8;
-    const int ej = emaxP[j];
-    int d[8][kOzDigits];
+  const size_t total = (size_t)n * KP;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(q / KP), j = (int)(q % KP);
+    int d[kOzDigits];
+    ozaki_digits(P[q], emaxP[j], d);
+    uint16_t* ch = chunks + (size_t)(l / kOzKC) * kChunkElems;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) ozaki_digits(l0 + e < n ? P[(size_t)(l0 + e) * KP + j] : 0.0, ej, d[e]);
-    uint16_t* ch = chunks + (size_t)(l0 / kOzKC) * kChunkElems;
-#pragma unroll
-    for (int t = 0; t < kOzDigits; ++t) {
-      uint4 v;
-      v.x = oz_f16_pair_of_ints(d[0][t], d[1][t]);
-      v.y = oz_f16_pair_of_ints(d[2][t], d[3][t]);
-      v.z = oz_f16_pair_of_ints(d[4][t], d[5][t]);
-      v.w = oz_f16_pair_of_ints(d[6][t], d[7][t]);
-      *reinterpret_cast<uint4*>(ch + umma_kmajor_offset(KPT * t + j, l0 % kOzKC, kOzKC) / 2) = v;
+    for (int t = 0; t < kOzDigits; t += 2) {
+      const uint32_t h2 = oz_f16_pair_of_ints(d[t], d[t + 1]);
+      ch[umma_kmajor_offset(KPT * t + j, l % kOzKC, kOzKC) / 2] = (uint16_t)(h2 & 0xFFFFu);
+      ch[umma_kmajor_offset(KPT * (t + 1) + j, l % kOzKC, kOzKC) / 2] = (uint16_t)(h2 >> 16);
     }
   }
 }
@@ -699,8 +693,7 @@ static void oz_product_kp(cudaStream_t s, int n, int sms, const uint8_t* Atiles,
     cudaMemsetAsync(emaxP, 0, sizeof(int) * KP, s);
     k_oz_colexp<KP><<<g < 1024 ? g : 1024, 256, 0, s>>>(n, P, emaxP, st);
   }
-  const int gs = (int)(((size_t)(n + 7) / 8 * KP + 255) / 256);
-  k_oz_slice_p<KP, KPT><<<gs < 4096 ? gs : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
+  k_oz_slice_p<KP, KPT><<<g < 4096 ? g : 4096, 256, 0, s>>>(n, P, emaxP, reinterpret_cast<uint16_t*>(Pchunks), st);
   const int ks = oz_ksplit(n, sms);
   k_dense_tc<KPT, ONCE><<<sp.G, kOzTcThreads, C::kSmem, s>>>(n, KP, sp.nK, sp.wl, sp.nW, Atiles, emaxA, Pchunks,
                                                              emaxP, Qpart, ks, err, st, 0);
