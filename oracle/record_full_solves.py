@@ -6,6 +6,7 @@ which calls only the oracle and the shared input generators, and writes full_sol
 
     python oracle/record_full_solves.py dense4096 8 16 32 cg
     python oracle/record_full_solves.py stencil27_96 16 cg
+    python oracle/record_full_solves.py diffusion128 1 4 cg
 
 With --band the script measures the oracle's rounding band instead: the same solve on the
 rounding-level perturbations b(1 + 1e-16 u) of the right-hand side (workloads.perturbed_rhs,
@@ -40,6 +41,8 @@ def load_workload(name):
         return wl.poisson2d(64), 0, 1e-8
     if name == "stencil27_96":
         return wl.stencil27(96, 0), 0, 1e-10
+    if name == "diffusion128":
+        return wl.diffusion3d(128, 0), 1, 1e-8
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -460,10 +460,23 @@ def test_stencil27_96_mixed_full_size_solution(mb):
     assert np.array_equal(x, x2)
 
 
-def test_diffusion128_full_size_first_iteration_and_solution(mb, orc):
-    A = wl.diffusion3d(128, 0)
+_DIFF128 = {}
+
+
+def diffusion128():
+    if "A" not in _DIFF128:
+        _DIFF128["A"] = wl.diffusion3d(128, 0)
+    return _DIFF128["A"]
+
+
+@pytest.mark.parametrize("s", [1, 4])
+def test_diffusion128_full_size_first_iteration_and_solution(mb, orc, s):
+    """The SpMM workload at full size (n = 2 097 152, Jacobi), in the bench's launch configuration:
+    the state after one iteration element-wise against the oracle, the full solve's true residual
+    recomputed here, and its iteration count within +-2 % of the oracle's recorded full solve (this
+    system stays far below the exact-termination bound, where the oracle's count does not move)."""
+    A = diffusion128()
     b = wl.rhs(A.n, 0)
-    s = 4
     U = wl.initial_block(A.n, s, 1)
     solver = mb.Solver(A, s=s, precond=1)
     try:
@@ -476,6 +489,24 @@ def test_diffusion128_full_size_first_iteration_and_solution(mb, orc):
         solver.close()
     assert info["status"] == 0
     assert relres(A, b, x) <= 1e-8
+    rec = json.load(open(FULL_SOLVE_COUNTS)).get("diffusion128", {}).get(str(s))
+    assert rec is not None, "oracle count not recorded (oracle/record_full_solves.py diffusion128 1 4 cg)"
+    it_o = rec["iterations"]
+    assert abs(info["iterations"] - it_o) <= max(1, int(0.02 * it_o)), (info["iterations"], it_o)
+
+
+def test_diffusion128_full_size_cg_count(mb):
+    """CG from the same library on the same system: iteration count within +-2 % of the oracle's."""
+    A = diffusion128()
+    b = wl.rhs(A.n, 0)
+    solver = mb.Solver(A, s=1, precond=1, algo=mb.MBPCG_ALGO_CG)
+    try:
+        x, info = solver.solve(b, tol=1e-8)
+    finally:
+        solver.close()
+    assert info["status"] == 0 and relres(A, b, x) <= 1e-8
+    it_o = json.load(open(FULL_SOLVE_COUNTS))["diffusion128"]["cg"]["iterations"]
+    assert abs(info["iterations"] - it_o) <= max(1, int(0.02 * it_o)), (info["iterations"], it_o)
 
 
 RFREE_CASES = [

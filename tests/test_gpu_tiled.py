@@ -270,3 +270,27 @@ def test_dense_apply_matches_the_oracle(mb, form):
         assert np.all(err <= bound), float((err / bound).max())
     finally:
         sv.close()
+
+
+@pytest.mark.parametrize("s", [1, 4])
+def test_full_size_diffusion_product_matches_the_oracle(mb, s):
+    """The product the bench's SpMM roofline times (diffusion 128^3, Jacobi-scaled, the handle's own
+    kernel through mbpcg_apply_dev) against the oracle's product of the same scaled matrix, every
+    entry, at the rounding of a row sum."""
+    A = wl.diffusion3d(128, 0)
+    n = A.n
+    sv = mb.Solver(A, s=s, precond=mb.MBPCG_PRECOND_JACOBI)
+    try:
+        kp = mb.mbpcg_k_padded_width(s)
+        X = torch.as_tensor(wl.initial_block(n, kp, 5)).reshape(n, kp).contiguous().cuda()
+        Y = sv.apply(X).cpu().numpy()
+    finally:
+        sv.close()
+    d = 1.0 / np.sqrt(A.diagonal())
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    As = wl.CSR(n, A.row_ptr, A.col_idx, A.val * d[rows] * d[A.col_idx])  # D^-1/2 A D^-1/2
+    Xh = X.cpu().numpy()
+    err = np.abs(Y - oracle.matmat(As, Xh))
+    # the GPU scales the values itself (one rounding per value): bound the product of either scaling
+    assert np.all(err <= row_bound(As, Xh, 2.0 ** -52) + 4 * 2.0 ** -53 * (np.abs(As.to_scipy()) @ np.abs(Xh))), \
+        float(err.max())
