@@ -90,6 +90,7 @@ def parse():
     p.add_argument("--kernel-launches", type=int, default=20, help="launches of the dominant kernel timed alone")
     p.add_argument("--cpu-sample-iters", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-sweep", action="store_true", help="skip the sweep of s on the dense tensor-core workload")
     p.add_argument("--no-spmm-roofline", action="store_true",
                    help="skip the SpMM HBM roofline (diffusion 128^3 at s = 1, 4 in FP64; 27-point 96^3 at s = 16 in FP32)")
     p.add_argument("--precision", default=None, choices=["fp64", "tc", "mixed"],
@@ -439,6 +440,23 @@ def run_ours(args, world, rank, local):
         solver.set_product_rounding(mb.MBPCG_ROUND_FP32_TAIL)
         once = {"ms": round(sum(o_times) / len(o_times), 4), "iterations": o_infos[-1]["iterations"],
                 "restarts": o_infos[-1]["restarts"], "relres_true": o_infos[-1]["relres_true"]}
+    sweep = None
+    if dense and prec == mb.MBPCG_FP64_TC and world == 1 and not args.no_sweep:
+        # the configuration's sweep of s on the same system: one warm-up and one timed solve each
+        sweep = {}
+        for sw in (1, 2, 4, 8, 16, 32):
+            if sw == s:
+                sweep[str(sw)] = {"ms": round(sum(times) / len(times), 4), "iterations": infos[-1]["iterations"]}
+                continue
+            svw = mb.Solver(A, s=sw, precond=cfg["precond"], launch_mode=mode, precision=prec)
+            try:
+                Uw = torch.as_tensor(np.asfortranarray(wl.initial_block(A.n, sw, 1)).ravel(order="F"), device=dev)
+                timed(svw, Uw, 1)
+                w_times, w_infos, _ = timed(svw, Uw, 1)
+                sweep[str(sw)] = {"ms": round(w_times[0], 4), "iterations": w_infos[-1]["iterations"],
+                                  "restarts": w_infos[-1]["restarts"]}
+            finally:
+                svw.close()
     total_ms = sum(times)
     cg_total = sum(cg_times)
     total_ms, cg_total = max_over_ranks([total_ms, cg_total], world, dev)
@@ -673,6 +691,10 @@ def run_ours(args, world, rank, local):
         if once is not None:
             once["speedup_vs_cg"] = round(cg_ms / once["ms"], 4)
             line["round_once"] = once
+        if sweep is not None:
+            for v in sweep.values():
+                v["speedup_vs_cg"] = round(cg_ms / v["ms"], 4)
+            line["sweep_s"] = sweep
         if fp64 is not None:
             f_ms = sum(f_times) / len(f_times)
             xfh = xf.cpu().numpy()
