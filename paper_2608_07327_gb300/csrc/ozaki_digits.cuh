@@ -46,6 +46,39 @@ __device__ __forceinline__ void ozaki_digits(double x, int emax, int (&d)[kOzDig
   for (int t = 0; t < kOzDigits; ++t) d[t] = ozaki_digit(X, sgn, t);
 }
 
+// The digits of a magnitude from ozaki_magnitude, one per byte: hi holds digits 0..3 (digit t in byte
+// 3 - t), lo digits 4..7 (digit t in byte 7 - t); every byte is below 128.
+__device__ __forceinline__ uint32_t oz_spread4(uint32_t v) {  // v < 2^28: its 7-bit fields to bytes
+  return (v & 0x7Fu) | ((v << 1) & 0x7F00u) | ((v << 2) & 0x7F0000u) | ((v << 3) & 0x7F000000u);
+}
+__device__ __forceinline__ void oz_digit_bytes(unsigned long long X, uint32_t& hi, uint32_t& lo) {
+  hi = oz_spread4((uint32_t)(X >> 28));
+  lo = oz_spread4((uint32_t)X & 0xFFFFFFFu);
+}
+
+// Signs of two values as the FP16 pairs (s_a, s_b) and (-1024 s_a, -1024 s_b) (s = +-1) that
+// oz_f16_digit_pair takes.
+__device__ __forceinline__ void oz_sign_pair(int sa, int sb, uint32_t& s2, uint32_t& c2) {
+  s2 = (sa < 0 ? 0xBC00u : 0x3C00u) | ((sb < 0 ? 0xBC00u : 0x3C00u) << 16);
+  c2 = (sa < 0 ? 0x6400u : 0xE400u) | ((sb < 0 ? 0x6400u : 0xE400u) << 16);
+}
+
+// Digit t of two values as an FP16 pair (value a in the low half), from their digit bytes (wa, wb:
+// the hi or lo word of each, by t) and their signs: one byte permutation puts the two digit bytes in
+// the low bytes of the halves with zero high bytes (the selector's sign-replicate bit copies the top
+// bit of a byte below 128), an OR makes them 1024 + d (exact in FP16), and one FP16 multiply-add
+// s (1024 + d) - 1024 s leaves s d exactly.
+__device__ __forceinline__ uint32_t oz_f16_digit_pair(uint32_t wa, uint32_t wb, int t, uint32_t s2, uint32_t c2) {
+  const uint32_t b = 3u - (uint32_t)(t & 3);
+  const uint32_t sel = b | ((8u | b) << 4) | ((4u + b) << 8) | ((12u + b) << 12);
+  uint32_t w;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(w) : "r"(wa), "r"(wb), "r"(sel));
+  w |= 0x64006400u;
+  const __half2 v = __hfma2(*reinterpret_cast<const __half2*>(&w), *reinterpret_cast<const __half2*>(&s2),
+                            *reinterpret_cast<const __half2*>(&c2));
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
 // Two digits (|d| <= 127) as an FP16 pair (the first in the low half), with integer operations and
 // one half-precision subtraction: 1024 + (d + 128) is an FP16 with bits 0x6400 + d + 128 (exact for
 // 0 <= d + 128 < 1024), and subtracting 1024 + 128 from both halves at once leaves d exactly.
