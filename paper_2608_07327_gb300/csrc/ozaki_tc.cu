@@ -33,6 +33,7 @@
 
 #include <type_traits>
 
+#include "int_to_fp64.cuh"
 #include "kernels.h"
 #include "ozaki_digits.cuh"
 #include "tcgen05.cuh"
@@ -519,10 +520,25 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
   if (warp == 0) tmem_dealloc(tmem, C::kTmemCols);
 }
 
+// An FP32 value as FP64 (exact) with integer operations, zeros as +0 (the sums below start from +0,
+// so the sign of a zero term never shows); subnormal, infinite and NaN inputs take the conversion
+// instruction, which on this GPU runs on the FP64 pipe.
+__device__ __forceinline__ double oz_f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if ((b << 1) == 0) return 0.0;
+  if (e == 0 || e == 0xFFu) return (double)f;
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                          ((unsigned long long)(e + 896u) << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 // Sums of the raw partials of output o over the ns slices of its tile (slice stride `stride`
 // entries): the int64 parts exactly; the levels 5..8 parts exactly too when they are integers
 // (ONCE), else FP32 values summed in FP64 in slice order. The first kOzSliceBatch slices are loaded
-// at once (predicated), so their L2 latencies overlap. Returns the product before its scale.
+// at once (predicated), so their L2 latencies overlap. Returns the product before its scale. The
+// conversions to FP64 and the scalings by powers of two are integer operations (int_to_fp64.cuh):
+// the FP64 pipe keeps only the adds of the FP32 parts and the final multiply-add.
 constexpr int kOzSliceBatch = 8;
 template <bool ONCE>
 __device__ __forceinline__ double oz_slice_value(const OzPart& qp, size_t o, size_t stride, int ns) {
@@ -544,20 +560,28 @@ __device__ __forceinline__ double oz_slice_value(const OzPart& qp, size_t o, siz
   for (int k = 0; k < kOzSliceBatch; ++k) {
     si += vi[k];
     if constexpr (ONCE) sf += vf[k];
-    else if (k < ns) sf += (double)vf[k];
+    else if (k == 0) sf = oz_f32_to_f64(vf[0]);  // = 0 + vf[0]
+    else if (k < ns) sf += oz_f32_to_f64(vf[k]);
   }
   for (int k = kOzSliceBatch; k < ns; ++k) {
     si += qp.qi[(size_t)k * stride + o];
     if constexpr (ONCE) sf += qp.ql[(size_t)k * stride + o];
-    else sf += (double)qp.qf[(size_t)k * stride + o];
+    else sf += oz_f32_to_f64(qp.qf[(size_t)k * stride + o]);
   }
-  // levels 0..4 in units of 2^-42, levels 5..8 in units of 2^-49 (FP32 carry) or 2^-70 (exact)
-  if constexpr (ONCE) return fma((double)sf, 0x1p-70, (double)si * 0x1p-42);
-  else return fma(sf, 0x1p-49, (double)si * 0x1p-42);
+  // levels 0..4 in units of 2^-42, levels 5..8 in units of 2^-49 (FP32 carry) or 2^-70 (exact);
+  // si 2^-42 is a normal number or zero, so the scaled conversion never leaves the normal range
+  bool normal;
+  const double hi = ll_to_double_scaled_rn(si, -42, normal);
+  if constexpr (ONCE) return fma(ll_to_double_rn(sf), 0x1p-70, hi);
+  else return fma(sf, 0x1p-49, hi);
 }
 
-// v 2^e: a product by a power of two (exact) wherever ldexp is, which takes the rest.
+// v 2^e: an integer add to the exponent field when v and the result are normal numbers (the same
+// bits as the product), else a product by a power of two (exact wherever ldexp is), else ldexp.
 __device__ __forceinline__ double oz_scale(double v, int e) {
+  const long long b = __double_as_longlong(v);
+  const int ev = (int)((b >> 52) & 0x7FF);
+  if (ev != 0 && ev + e >= 1 && ev + e <= 2046) return __longlong_as_double(b + (long long)e * (1LL << 52));
   if (e >= -1022 && e <= 1023) return v * __longlong_as_double((long long)(e + 1023) << 52);
   return ldexp(v, e);
 }

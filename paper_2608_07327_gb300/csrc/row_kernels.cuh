@@ -302,9 +302,14 @@ k_axpy_pre(int n, const double* __restrict__ PT, const double* __restrict__ QT, 
       stv<C::CPT>(Xt + o, xv);
       stv<C::CPT>(R + o, rv);
       stv<C::CPT>(V + o, vv);
-      const double w2 = wdiag != nullptr ? __ldg(wdiag + i) : 1.0;
+      if (wdiag != nullptr) {
+        const double w2 = __ldg(wdiag + i);
 #pragma unroll
-      for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c] * w2, rv[c], nu[c]);
+        for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c] * w2, rv[c], nu[c]);
+      } else {  // the same bits as with w2 = 1, one FP64 product fewer per entry
+#pragma unroll
+        for (int c = 0; c < C::CPT; ++c) nu[c] = fma(rv[c], rv[c], nu[c]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < C::CPT; ++c) Vs[rl * KP + j0 + c] = vv[c];
