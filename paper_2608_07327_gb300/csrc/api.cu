@@ -45,7 +45,7 @@ constexpr int kMixedRestarts = 12;       // refinement steps of the mixed-precis
 constexpr int kTuneVariants = 11;        // FP32 A P launch shapes tried by the autotuner
 constexpr int kTiledMinRows = 65536;     // smaller systems sit in L2 and keep the gather kernel
 constexpr double kMixedInnerTol = 1e-5;  // smallest relative tolerance asked of an FP32 inner solve
-constexpr int kBodyUnroll = 4;           // loop iterations per pass of the graph's WHILE node
+constexpr int kBodyUnroll = 8;           // loop iterations per pass of the graph's WHILE node
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Runs of staged rows the workspace holds for a CSR plan (a stencil needs a few per tile; a
 // matrix that needs more keeps the gather kernel).

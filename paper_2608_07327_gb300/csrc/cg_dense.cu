@@ -105,6 +105,7 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
   double* u = cg_smem;                      // r_j, the whole vector
   double* fsum = cg_smem + ((n + 1) & ~1);  // row-fragment sums, [warp][fragment]
   __shared__ double red[3 * kCgWarps];
+  __shared__ int wrow[2 * kCgWarps];  // first and last local row of each warp's chunk range (empty: 1, 0)
   __shared__ int last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (st->done) {
@@ -119,6 +120,10 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
   const int nchunks = (r1 - r0) * cpr;
   const int fmax = cg_dense_fragments(n, gridDim.x);
   const int c0 = (int)((long long)nchunks * warp / kCgWarps), c1 = (int)((long long)nchunks * (warp + 1) / kCgWarps);
+  if (lane == 0) {
+    wrow[2 * warp] = c0 < c1 ? c0 / cpr : 1;
+    wrow[2 * warp + 1] = c0 < c1 ? (c1 - 1) / cpr : 0;
+  }
   // the first chunk's loads do not depend on r_j: issue them before the vector updates
   double2 bufA[kSegD2], bufB[kSegD2];
   if (c0 < c1) load_chunk(A, n, r0, cpr, c0, lane, pol, bufA);
@@ -135,14 +140,29 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
     const double* ro = v.r[par ^ 1];
     const double* wo = v.w[par ^ 1];
     const double* so = v.s[par];
-    for (int e = tid; e < n2; e += kCgThreads) {
-      const double2 rr = __ldcg(reinterpret_cast<const double2*>(ro) + e);
-      const double2 ww = __ldcg(reinterpret_cast<const double2*>(wo) + e);
-      const double2 ss = __ldcg(reinterpret_cast<const double2*>(so) + e);
-      double2 r2;
-      r2.x = fma(-alpha, fma(beta, ss.x, ww.x), rr.x);
-      r2.y = fma(-alpha, fma(beta, ss.y, ww.y), rr.y);
-      reinterpret_cast<double2*>(u)[e] = r2;
+    // batches of kUpd elements per thread, every load of a batch in flight before its arithmetic
+    constexpr int kUpd = 4;
+    for (int e0 = tid; e0 < n2; e0 += kUpd * kCgThreads) {
+      double2 rr[kUpd], ww[kUpd], ss[kUpd];
+#pragma unroll
+      for (int b = 0; b < kUpd; ++b) {
+        const int e = e0 + b * kCgThreads;
+        if (e < n2) {
+          rr[b] = __ldcg(reinterpret_cast<const double2*>(ro) + e);
+          ww[b] = __ldcg(reinterpret_cast<const double2*>(wo) + e);
+          ss[b] = __ldcg(reinterpret_cast<const double2*>(so) + e);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kUpd; ++b) {
+        const int e = e0 + b * kCgThreads;
+        if (e < n2) {
+          double2 r2;
+          r2.x = fma(-alpha, fma(beta, ss[b].x, ww[b].x), rr[b].x);
+          r2.y = fma(-alpha, fma(beta, ss[b].y, ww[b].y), rr[b].y);
+          reinterpret_cast<double2*>(u)[e] = r2;
+        }
+      }
     }
     // own rows: p, s, x and r of iteration j (the same expressions as u above, so the same bits)
     double* rn = v.r[par];
@@ -205,9 +225,10 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
   double g = 0.0, dl = 0.0, nu = 0.0;
   for (int t = tid; t < r1 - r0; t += kCgThreads) {
     double w = 0.0;
+#pragma unroll
     for (int wp = 0; wp < kCgWarps; ++wp) {  // warps whose chunk range meets row t, in warp order
-      const int a0 = (int)((long long)nchunks * wp / kCgWarps), a1 = (int)((long long)nchunks * (wp + 1) / kCgWarps);
-      if (a0 < a1 && a0 / cpr <= t && t <= (a1 - 1) / cpr) w += fsum[wp * fmax + t - a0 / cpr];
+      const int f0 = wrow[2 * wp];
+      if (f0 <= t && t <= wrow[2 * wp + 1]) w += fsum[wp * fmax + t - f0];
     }
     const int row = r0 + t;
     v.w[par][row] = w;
@@ -240,28 +261,39 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
   __syncthreads();
 
   // 4. the last CTA: fixed-order sum of the partials, the test and the scalars of iteration j
-  if (tid == 0) {
-    __threadfence();
-    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  if (tid == 0) {  // the arrival releases this CTA's partials (ordered before it by the barrier)
+    unsigned int old;  // and acquires the other CTAs' ones
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(counter) : "memory");
+    last = old == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || warp != 0) return;
-  __threadfence();
-  double sg = 0.0, sd = 0.0, sn2 = 0.0;
-  for (int q = lane; q < (int)gridDim.x; q += 32) {
-    sg += __ldcg(part + (size_t)q * pstride);
-    sd += __ldcg(part + (size_t)q * pstride + 1);
-    sn2 += __ldcg(part + (size_t)q * pstride + 2);
-  }
+  if (!last) return;
+  // warps 0, 1, 2 of the last CTA sum the partials of gamma, delta and ||D r||^2, one sum each (a
+  // warp has one FP64 instruction in flight: three chains in one warp would run one after another),
+  // each over the CTAs in lane-strided order and then a butterfly
+  __shared__ double tot[3];
+  if (warp < 3) {
+    double a = 0.0;
+    constexpr int kTail = 8;  // partials per lane loaded together (grids up to 256 CTAs in one batch)
+    for (int q0 = lane; q0 < (int)gridDim.x; q0 += 32 * kTail) {
+      double pv[kTail];
 #pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    sg += __shfl_xor_sync(0xffffffffu, sg, off);
-    sd += __shfl_xor_sync(0xffffffffu, sd, off);
-    sn2 += __shfl_xor_sync(0xffffffffu, sn2, off);
+      for (int b = 0; b < kTail; ++b) {
+        const int q = q0 + 32 * b;
+        if (q < (int)gridDim.x) pv[b] = __ldcg(part + (size_t)q * pstride + warp);
+      }
+#pragma unroll
+      for (int b = 0; b < kTail; ++b)
+        if (q0 + 32 * b < (int)gridDim.x) a += pv[b];
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    if (lane == 0) tot[warp] = warp == 2 ? sqrt(a) : a;  // the norm's root beside the other sums
   }
-  if (lane != 0) return;
+  __syncthreads();
+  if (tid != 0) return;
   *counter = 0u;
-  const double gamma = sg, delta = sd, nrm = sqrt(sn2);
+  const double gamma = tot[0], delta = tot[1], nrm = tot[2];
   st->nu_h = nrm;
   st->ls_res = nrm;
   int cont = 0;
