@@ -11,19 +11,37 @@ namespace mbpcg {
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce(const double* __restrict__ part, int nparts, int pstride, double* __restrict__ out, int nent,
          const SolveState* __restrict__ st) {
-  if (st != nullptr && st->done) return;
   __shared__ double ws[kReduceThreads / 32];
   const int e = blockIdx.x, tid = threadIdx.x;
   if (e >= nent) return;
+  // batches of kB partials per thread, all loads of a batch in flight together; the first batch
+  // is loaded with the solve state (a skipped launch discards it), so the two L2 round trips
+  // overlap. The adds keep the partials' order.
+  constexpr int kB = 4;
+  double v[kB];
+  auto load = [&](int p0) {
+#pragma unroll
+    for (int b = 0; b < kB; ++b) {
+      const int p = p0 + b * kReduceThreads;
+      v[b] = p < nparts ? part[(size_t)p * pstride + e] : 0.0;
+    }
+  };
+  load(tid);
+  if (st != nullptr && st->done) return;
   double a = 0.0;
-  for (int p = tid; p < nparts; p += kReduceThreads) a += part[(size_t)p * pstride + e];
+  for (int p0 = tid; p0 < nparts; p0 += kB * kReduceThreads) {
+    if (p0 != tid) load(p0);
+#pragma unroll
+    for (int b = 0; b < kB; ++b)
+      if (p0 + b * kReduceThreads < nparts) a += v[b];
+  }
   for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
   if ((tid & 31) == 0) ws[tid >> 5] = a;
   __syncthreads();
   if (tid == 0) {
-    double v = ws[0];
-    for (int w = 1; w < kReduceThreads / 32; ++w) v += ws[w];
-    out[e] = v;
+    double t = ws[0];
+    for (int w = 1; w < kReduceThreads / 32; ++w) t += ws[w];
+    out[e] = t;
   }
 }
 
