@@ -435,12 +435,14 @@ k_dense_tc(int n, int KP, int nK, int wl, int nW, const uint8_t* __restrict__ Ab
       ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // tcgen05.ld needs the whole warp
       if (!ok) break;
       const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(DC * half);
-      // two rounds (levels 0..4, then 5..8): the loads of a round are in flight together (one wait
-      // each); the accumulator is released as soon as the second round is in registers
+      // two rounds (levels 5..8, then 0..4): the loads of a round are in flight together (one wait
+      // each); the accumulator is released as soon as the second round is in registers. Levels
+      // 5..8 go first because their adds are FP32 FMAs; the 40 integer conversions of levels 0..4
+      // (a slow unit: 16 per clock per SM) then run after the release, beside the next MMAs.
 #pragma unroll
       for (int rd = 0; rd < 2; ++rd) {
         constexpr int kR = 5;
-        const int L0 = rd * kR, nl = rd == 0 ? kR : kOzLevels - kR;
+        const int L0 = rd == 0 ? kR : 0, nl = rd == 0 ? kOzLevels - kR : kR;
         uint32_t rr[kR][DC];
 #pragma unroll
         for (int q = 0; q < kR; ++q) {
