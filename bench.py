@@ -94,7 +94,7 @@ def parse():
     p.add_argument("--no-spmm-roofline", action="store_true",
                    help="skip the SpMM HBM roofline (diffusion 128^3 at s = 1, 4 in FP64; 27-point 96^3 at s = 16 in FP32)")
     p.add_argument("--precision", default=None, choices=["fp64", "tc", "mixed"],
-                   help="tc: dense product on the BF16 tensor cores by exact digit splitting (FP64 accuracy); "
+                   help="tc: dense product on the FP16 tensor cores by exact digit splitting (FP64 accuracy); "
                         "mixed: FP32 inner solves in FP64 refinement (CSR); default: the workload's own")
     p.add_argument("--residual", default="explicit", choices=["explicit", "implicit"],
                    help="implicit: the loop carries R = W Sigma instead of updating R (MBPCG_RESIDUAL_IMPLICIT)")
@@ -164,7 +164,7 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "k_dense": ("row_kernels.cuh", "mbpcg_device.cuh"),
     "k_spmm": ("row_kernels.cuh", "mbpcg_device.cuh"),
-    "k_dense_tc": ("ozaki_tc.cu", "ozaki_digits.cuh", "tcgen05.cuh", "tma.cuh", "mbpcg_device.cuh"),
+    "k_dense_tc": ("ozaki_tc.cu", "ozaki_digits.cuh", "int_to_fp64.cuh", "tcgen05.cuh", "tma.cuh", "mbpcg_device.cuh"),
 }
 
 

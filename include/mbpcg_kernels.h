@@ -99,9 +99,10 @@ int mbpcg_k_dense_product(int32_t n, const double* A, int32_t s, const double* P
                           void* stream);
 
 /* The tensor-core form of the dense product (precision MBPCG_FP64_TC), as accurate as an FP64
- * product. mbpcg_k_dense_tc_prepare writes the BF16 digits of A into `scratch`
- * (mbpcg_k_dense_tc_scratch_bytes(n, s) bytes of device memory, 256-byte aligned);
- * mbpcg_k_dense_tc_product then splits P and computes AP = A P with tcgen05 MMAs, reusing them. */
+ * product. mbpcg_k_dense_tc_prepare writes the base-128 digits of A into `scratch` as bytes (8 per
+ * entry; mbpcg_k_dense_tc_scratch_bytes(n, s) bytes of device memory, 256-byte aligned);
+ * mbpcg_k_dense_tc_product then splits P into FP16 digits and computes AP = A P with tcgen05 MMAs
+ * (the digits of A converted to FP16 operands on chip), reusing them. */
 size_t mbpcg_k_dense_tc_scratch_bytes(int32_t n, int32_t s);
 int mbpcg_k_dense_tc_prepare(int32_t n, const double* A, int32_t s, void* scratch,
                              size_t scratch_bytes, void* stream);
@@ -117,7 +118,7 @@ int mbpcg_k_dense_tc_mma(int32_t n, int32_t s, void* scratch, size_t scratch_byt
 
 /* The k x k-row products of the block update and of the W/P update of Algorithm 1 (P T, (AP) T,
  * (AP) Xi, V zeta^{-1}, P zeta^T) as the solver runs them for tensor-core handles at s > 8:
- * Y = X M on the BF16 tensor cores by exact digit splitting (X row by row, M column by column;
+ * Y = X M on the FP16 tensor cores by exact digit splitting (X row by row, M column by column;
  * 8 base-128 digits each), with the accuracy of an FP64 product: error about 2^-53 times
  * (max_l |X_il|) (sum_l |M_lj|) per entry, against an FP64 product's w u sum_l |X_il||M_lj|.
  * width = 32 or 16 (the padded width KP). X, Y: device, row-major n x width FP64, 16-byte
