@@ -388,14 +388,27 @@ struct LdlWork {
   int bad;
 };
 
+// The entries of the packed Gram that this thread's share of ldl_init uses. Every entry of the KP x KP
+// triangle exists whatever s is, so the loads need no solve state: issued before the state is read,
+// their L2 round trip overlaps its own.
 template <int KP>
-__device__ void ldl_init(LdlWork<KP>& W, const double* __restrict__ packed, int s) {
-  constexpr int LD = LdlWork<KP>::LD, NT = ClusterCfg<KP>::NF, NI = KP * KP / NT;
-  double v[NI];
+__device__ __forceinline__ void ldl_load(const double* __restrict__ packed, double (&g)[KP * KP / ClusterCfg<KP>::NF]) {
+  constexpr int NT = ClusterCfg<KP>::NF, NI = KP * KP / NT;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {  // all loads in flight at once
     const int q = threadIdx.x + NT * i, r = q / KP, c = q % KP;
-    v[i] = (r < s && c < s) ? ((r <= c) ? packed[pidx(r, c)] : packed[pidx(c, r)]) : (r == c ? 1.0 : 0.0);
+    g[i] = (r <= c) ? packed[pidx(r, c)] : packed[pidx(c, r)];
+  }
+}
+
+template <int KP>
+__device__ void ldl_init(LdlWork<KP>& W, const double (&g)[KP * KP / ClusterCfg<KP>::NF], int s) {
+  constexpr int LD = LdlWork<KP>::LD, NT = ClusterCfg<KP>::NF, NI = KP * KP / NT;
+  double v[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int q = threadIdx.x + NT * i, r = q / KP, c = q % KP;
+    v[i] = (r < s && c < s) ? g[i] : (r == c ? 1.0 : 0.0);
   }
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
@@ -522,12 +535,18 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
   __shared__ LdlWork<KP> W;
   __shared__ double Sg[KP * CC::CPC], V[KP * CC::CPC];
   cg::cluster_group cluster = cg::this_cluster();
-  if (st->done) return;
-  const int s = st->s, tid = threadIdx.x, c = (int)cluster.block_rank();
+  const int tid = threadIdx.x, c = (int)cluster.block_rank();
   const bool ct = tid < CC::NT;  // column-phase thread: column b = c + CS r, row a
   const int r = tid / KP, a = tid % KP, b = c + CC::CS * r;
-  if (ct) Sg[a * CC::CPC + r] = (a < KL && b < KL) ? Sigma[a + b * KL] : 0.0;  // own columns (upper)
-  ldl_init<KP>(W, G1p, s);
+  // the Gram and Sigma first: a launch that returns discards them, the others overlap the round
+  // trips of these loads and of the solve state
+  double gv[KP * KP / CC::NF];
+  ldl_load<KP>(G1p, gv);
+  const double sg = (ct && a < KL && b < KL) ? Sigma[a + b * KL] : 0.0;  // own columns (upper)
+  if (st->done) return;
+  const int s = st->s;
+  if (ct) Sg[a * CC::CPC + r] = sg;
+  ldl_init<KP>(W, gv, s);
   ldl_factor<KP>(W, s);
   if (W.bad) {  // every CTA reaches the same verdict
     if (c == 0 && tid == 0) {
@@ -583,8 +602,17 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
   __shared__ double nh_s;
   __shared__ int h_s, stop_s;
   cg::cluster_group cluster = cg::this_cluster();
-  const int s = st->s, tid = threadIdx.x, c = (int)cluster.block_rank();
+  const int tid = threadIdx.x, c = (int)cluster.block_rank();
   const bool lead = (c == 0 && tid == 0);
+  const bool ct = tid < CC::NT;
+  const int r = tid / KP, a = tid % KP, b = c + CC::CS * r;
+  // the Gram, Sigma and the norms first, as in k_small_xi_x
+  double gv[KP * KP / CC::NF];
+  ldl_load<KP>(G2nu, gv);
+  const double sg = (ct && a < KL && b < KL) ? Sigma[a + b * KL] : 0.0;
+  const int jn = tid & 31;
+  const long long nvb = ((tid >> 5) == CC::IDLE && jn < KL) ? __double_as_longlong(G2nu[npack(KL) + jn]) : 0;
+  const int s = st->s;
   if (st->done) {  // the solve stopped in an earlier iteration: no W, P update in this one
     if (lead) {
       st->pw_skip = 1;
@@ -592,13 +620,11 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
     }
     return;
   }
-  const bool ct = tid < CC::NT;
-  const int r = tid / KP, a = tid % KP, b = c + CC::CS * r;
-  if (ct) Sg[a * CC::CPC + r] = (a < KL && b < KL) ? Sigma[a + b * KL] : 0.0;
-  ldl_init<KP>(W, G2nu, s);
+  if (ct) Sg[a * CC::CPC + r] = sg;
+  ldl_init<KP>(W, gv, s);
   if ((tid >> 5) == CC::IDLE) {  // a warp without early factorisation work decides the stopping test
-    const int j = tid & 31;  // h = argmin_j nu_j, lowest index on ties (nu >= 0: bit order = value order)
-    long long nv = (j < s) ? __double_as_longlong(G2nu[npack(KL) + j]) : 0x7FF0000000000000LL;
+    const int j = jn;  // h = argmin_j nu_j, lowest index on ties (nu >= 0: bit order = value order)
+    long long nv = (j < s) ? nvb : 0x7FF0000000000000LL;
     int h = j;
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
