@@ -388,16 +388,17 @@ struct LdlWork {
   int bad;
 };
 
-// The entries of the packed Gram that this thread's share of ldl_init uses. Every entry of the KP x KP
-// triangle exists whatever s is, so the loads need no solve state: issued before the state is read,
-// their L2 round trip overlaps its own.
-template <int KP>
+// The entries of the packed Gram that this thread's share of ldl_init uses. The buffer holds the
+// triangle of the handle's padded width KL (<= KP; s <= KL), whatever s is, so the loads need no
+// solve state: issued before the state is read, their L2 round trip overlaps its own. Entries past
+// KL are not read (zero here; ldl_init replaces them by the identity).
+template <int KP, int KL>
 __device__ __forceinline__ void ldl_load(const double* __restrict__ packed, double (&g)[KP * KP / ClusterCfg<KP>::NF]) {
   constexpr int NT = ClusterCfg<KP>::NF, NI = KP * KP / NT;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {  // all loads in flight at once
     const int q = threadIdx.x + NT * i, r = q / KP, c = q % KP;
-    g[i] = (r <= c) ? packed[pidx(r, c)] : packed[pidx(c, r)];
+    g[i] = (r < KL && c < KL) ? ((r <= c) ? packed[pidx(r, c)] : packed[pidx(c, r)]) : 0.0;
   }
 }
 
@@ -541,7 +542,7 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
   // the Gram and Sigma first: a launch that returns discards them, the others overlap the round
   // trips of these loads and of the solve state
   double gv[KP * KP / CC::NF];
-  ldl_load<KP>(G1p, gv);
+  ldl_load<KP, KL>(G1p, gv);
   const double sg = (ct && a < KL && b < KL) ? Sigma[a + b * KL] : 0.0;  // own columns (upper)
   if (st->done) return;
   const int s = st->s;
@@ -608,7 +609,7 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
   const int r = tid / KP, a = tid % KP, b = c + CC::CS * r;
   // the Gram, Sigma and the norms first, as in k_small_xi_x
   double gv[KP * KP / CC::NF];
-  ldl_load<KP>(G2nu, gv);
+  ldl_load<KP, KL>(G2nu, gv);
   const double sg = (ct && a < KL && b < KL) ? Sigma[a + b * KL] : 0.0;
   const int jn = tid & 31;
   const long long nvb = ((tid >> 5) == CC::IDLE && jn < KL) ? __double_as_longlong(G2nu[npack(KL) + jn]) : 0;
