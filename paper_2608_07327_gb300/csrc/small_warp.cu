@@ -374,6 +374,11 @@ __device__ __forceinline__ void named_bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// A cluster barrier split in two: every thread of every CTA arrives once, then waits once; work
+// between the two overlaps the barrier's latency.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 // Shared working set of the factorisation (matrices row-major with ld KP+1).
 template <int KP>
 struct LdlWork {
@@ -574,6 +579,7 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
   cluster.sync();  // also: every CTA has finished reading the L^{-1} columns of the others
   cluster_gather_columns<KP>(X, c, true);
   __syncthreads();
+  cluster_arrive();  // this CTA reads no other CTA's shared memory from here on
   if (ct) {
     const bool in = (a < s && b < s);
     double v = 0.0;  // T[a][b] = sum_{l <= b} Xi[a][l] Sigma[l][b]
@@ -583,7 +589,7 @@ k_small_xi_x(SolveState* st, const double* __restrict__ G1p, const double* __res
       T[a + b * KL] = in ? v : 0.0;
     }
   }
-  cluster.sync();  // no CTA leaves while another may still read its shared memory
+  cluster_wait();  // no CTA leaves while another may still read its shared memory
   if (c == 0 && tid == 0) st->it += 1;
 }
 
@@ -670,6 +676,7 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
     }
     return;
   }
+  cluster_arrive();  // this CTA has read all of the solve state it uses
   if (ct) {
     const double ra = rsqrt_pos(W.d[a]);              // d_a^{-1/2}
     const double rb = __shfl_sync(kFull, ra, b, KP);  // d_b^{-1/2} (lane b of this column's segment)
@@ -684,7 +691,7 @@ k_small_zeta_x(SolveState* st, const double* __restrict__ G2nu, double* __restri
       ZetaInv[a + b * KL] = up ? lr * rb : 0.0;
     }
   }
-  cluster.sync();  // every CTA has read the state before the leader updates it
+  cluster_wait();  // every CTA has read the state before the leader updates it
   if (lead) {
     st->best_col = h;
     st->nu_h = nh;
