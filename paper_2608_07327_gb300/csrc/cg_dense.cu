@@ -108,11 +108,12 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
   __shared__ int wrow[2 * kCgWarps];  // first and last local row of each warp's chunk range (empty: 1, 0)
   __shared__ int last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int it = st->it, par = it & 1;  // read with the done flag: one round trip for both
+  const double alpha = st->cg_alpha, beta = st->cg_beta;
   if (st->done) {
     if (use_cond && blockIdx.x == 0 && tid == 0) cudaGraphSetConditional(cond, 0);
     return;
   }
-  const int it = st->it, par = it & 1;
   int r0, r1;
   row_range(n, r0, r1);
   const uint64_t pol = l2_policy_evict_first();
@@ -136,7 +137,6 @@ k_cg_dense_iter(int n, const double* __restrict__ A, CgVectors v, const double* 
     const double2* rv = reinterpret_cast<const double2*>(v.r[0]);
     for (int e = tid; e < n2; e += kCgThreads) reinterpret_cast<double2*>(u)[e] = __ldcg(rv + e);
   } else {
-    const double alpha = st->cg_alpha, beta = st->cg_beta;
     const double* ro = v.r[par ^ 1];
     const double* wo = v.w[par ^ 1];
     const double* so = v.s[par];

@@ -115,13 +115,22 @@ __global__ void k_oz_colexp(int n, const double* __restrict__ P, int* __restrict
 template <int KP, int KPT>
 __global__ void k_oz_slice_p(int n, const double* __restrict__ P, const int* __restrict__ emaxP,
                              uint16_t* __restrict__ chunks, const SolveState* __restrict__ st) {
-  if (st != nullptr && st->done) return;
   constexpr uint32_t kChunkElems = kOzDigits * KPT * kOzKC;
-  const size_t total = (size_t)n * KP;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+  const size_t total = (size_t)n * KP, stride = (size_t)gridDim.x * blockDim.x;
+  size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  // the first value and its column scale are loaded with the solve state (a skipped launch discards
+  // them), so the two L2 round trips overlap
+  double pv = q < total ? P[q] : 0.0;
+  int ev = q < total ? emaxP[q % KP] : 0;
+  if (st != nullptr && st->done) return;
+  for (; q < total; q += stride) {
     const int l = (int)(q / KP), j = (int)(q % KP);
+    if (q >= stride) {  // (not the thread's first value)
+      pv = P[q];
+      ev = emaxP[j];
+    }
     int d[kOzDigits];
-    ozaki_digits(P[q], emaxP[j], d);
+    ozaki_digits(pv, ev, d);
     uint16_t* ch = chunks + (size_t)(l / kOzKC) * kChunkElems;
 #pragma unroll
     for (int t = 0; t < kOzDigits; t += 2) {

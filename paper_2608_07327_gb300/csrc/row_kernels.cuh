@@ -331,15 +331,21 @@ k_axpy_pre(int n, const double* __restrict__ PT, const double* __restrict__ QT, 
 template <int KP>
 __global__ void k_pw_pre(int n, const double* __restrict__ VZi, const double* __restrict__ PZt, double* __restrict__ W,
                          double* __restrict__ P, const SolveState* __restrict__ st, int* __restrict__ emax) {
+  const size_t total = (size_t)n * KP, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  // the first element's loads go out with the solve state's (a skipped launch discards them)
+  double w0 = q0 < total ? VZi[q0] : 0.0, z0 = q0 < total ? PZt[q0] : 0.0;
   if (st != nullptr && st->pw_skip) return;
   __shared__ int em[KP];
   if (threadIdx.x < KP) em[threadIdx.x] = 0;
   __syncthreads();
-  const size_t total = (size_t)n * KP, stride = (size_t)gridDim.x * blockDim.x;
-  const size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   int loc = 0;
   for (size_t q = q0; q < total; q += stride) {
-    const double w = VZi[q], p = w + PZt[q];
+    if (q != q0) {
+      w0 = VZi[q];
+      z0 = PZt[q];
+    }
+    const double w = w0, p = w + z0;
     W[q] = w;
     P[q] = p;
     loc = max(loc, (int)((__double_as_longlong(p) >> 52) & 0x7FF));

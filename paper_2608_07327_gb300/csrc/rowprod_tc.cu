@@ -71,7 +71,6 @@ template <int K>
 __global__ void __launch_bounds__(kRpThreads, 1)
 k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int skip_on_pw, int* __restrict__ err) {
   using C = RpCfg<K>;
-  if (st != nullptr && (skip_on_pw ? st->pw_skip : st->done)) return;
   extern __shared__ __align__(1024) uint8_t rsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(rsm);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rsm + 8);
@@ -82,12 +81,8 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
   const RowProdJob J = blockIdx.y == 0 ? jobs.j[0] : blockIdx.y == 1 ? jobs.j[1] : jobs.j[2];  // no local copy
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    mbar_fence_init();
-  }
 
-  // loads first: this thread's values of X (row r of the tile, values Vpt q .. Vpt q + Vpt - 1) and
+  // loads first (issued before the solve state is read: a skipped launch discards them): this thread's values of X (row r of the tile, values Vpt q .. Vpt q + Vpt - 1) and
   // of M (reduction index lane, columns warp + 16 c)
   const int r = 8 * warp + (lane & 7), q = lane >> 3;
   const int row = blockIdx.x * kRpRows + r;
@@ -109,6 +104,11 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
   for (int c = 0; c < C::Cpw; ++c) {
     const int j = warp + 16 * c;
     mv[c] = lane < K ? (J.transM ? J.M[j + lane * K] : J.M[lane + j * K]) : 0.0;
+  }
+  if (st != nullptr && (skip_on_pw ? st->pw_skip : st->done)) return;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
   }
   if (warp == 0) tmem_alloc(tmem_slot, C::TmemCols);  // while the loads are in flight
 
