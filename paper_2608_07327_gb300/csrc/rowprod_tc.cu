@@ -81,9 +81,9 @@ k_rowprod_tc(int n, RowProdJobs jobs, const SolveState* __restrict__ st, int ski
   const RowProdJob J = blockIdx.y == 0 ? jobs.j[0] : blockIdx.y == 1 ? jobs.j[1] : jobs.j[2];  // no local copy
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-
-  // loads first (issued before the solve state is read: a skipped launch discards them): this thread's values of X (row r of the tile, values Vpt q .. Vpt q + Vpt - 1) and
-  // of M (reduction index lane, columns warp + 16 c)
+  // loads first, before the solve state is read (a skipped launch discards them): this thread's
+  // values of X (row r of the tile, values Vpt q .. Vpt q + Vpt - 1) and of M (reduction index
+  // lane, columns warp + 16 c)
   const int r = 8 * warp + (lane & 7), q = lane >> 3;
   const int row = blockIdx.x * kRpRows + r;
   double x[C::Vpt];
