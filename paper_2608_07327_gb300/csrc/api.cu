@@ -614,6 +614,9 @@ int finish_create(mbpcg_ctx* h) {
   if (h->dm.tc) {
     oz_prepare_a(h->stream, n, h->A, h->oz_ea, h->oz_a);
     CUDA_TRY(cudaMemsetAsync(h->oz_p, 0, oz_p_chunks_bytes(n, h->dm.kp), h->stream));
+    // the split sum reads every slice of the partials buffer (those past a tile's count unused)
+    CUDA_TRY(cudaMemsetAsync(h->oz_q, 0, (size_t)oz_ksplit(n, h->dm.sms) * n * h->dm.kp * 2 * sizeof(long long),
+                             h->stream));
     CUDA_TRY(cudaGetLastError());
   }
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -1601,6 +1604,9 @@ int mbpcg_k_dense_tc_prepare(int32_t n, const double* A, int32_t s, void* scratc
   const TcScratch t = tc_scratch(scratch, n, kp);
   oz_prepare_a(st, n, A, t.ea, t.at);
   CUDA_TRY(cudaMemsetAsync(t.pc, 0, oz_p_chunks_bytes(n, kp), st));
+  // the split sum reads every slice of the partials buffer (those past a tile's count unused)
+  CUDA_TRY(cudaMemsetAsync(t.qp, 0, (size_t)oz_ksplit(n, num_sms() > 0 ? num_sms() : 1) * n * kp * 2 * sizeof(long long),
+                           st));
   CUDA_TRY(cudaGetLastError());
   return MBPCG_OK;
 }

@@ -71,8 +71,10 @@ __host__ __device__ constexpr int npack(int kp) { return kp * (kp + 1) / 2; }
 // packed index of entry (l, j), l <= j, of a symmetric KP x KP matrix (upper triangle, by column)
 __host__ __device__ inline int pidx(int l, int j) { return j * (j + 1) / 2 + l; }
 __device__ inline void punpack(int e, int& l, int& j) {
-  j = 0;
-  while ((j + 1) * (j + 2) / 2 <= e) ++j;
+  // j = floor((sqrt(8e + 1) - 1) / 2) from an FP32 square root, then made exact by one step each way
+  j = (int)((sqrtf((float)(8 * e + 1)) - 1.f) * 0.5f);
+  if ((j + 1) * (j + 2) / 2 <= e) ++j;
+  if (j * (j + 1) / 2 > e) --j;
   l = e - j * (j + 1) / 2;
 }
 

@@ -547,19 +547,21 @@ __device__ __forceinline__ double oz_f32_to_f64(float f) {
 // Sums of the raw partials of output o over the ns slices of its tile (slice stride `stride`
 // entries): the int64 parts exactly; the levels 5..8 parts exactly too when they are integers
 // (ONCE), else FP32 values summed in FP64 in slice order. The first kOzSliceBatch slices are loaded
-// at once (predicated), so their L2 latencies overlap. Returns the product before its scale. The
-// conversions to FP64 and the scalings by powers of two are integer operations (int_to_fp64.cuh):
-// the FP64 pipe keeps only the adds of the FP32 parts and the final multiply-add.
+// at once, as many as the buffer holds (ksplit) whatever ns is, so that the loads need not wait for
+// ns (two 64-bit divisions): slices past ns are read and left out of the sums. Returns the product
+// before its scale. The conversions to FP64 and the scalings by powers of two are integer
+// operations (int_to_fp64.cuh): the FP64 pipe keeps only the adds of the FP32 parts and the final
+// multiply-add.
 constexpr int kOzSliceBatch = 8;
 template <bool ONCE>
-__device__ __forceinline__ double oz_slice_value(const OzPart& qp, size_t o, size_t stride, int ns) {
+__device__ __forceinline__ double oz_slice_value(const OzPart& qp, size_t o, size_t stride, int ns, int ksplit) {
   long long vi[kOzSliceBatch];
   typename std::conditional<ONCE, long long, float>::type vf[kOzSliceBatch];
 #pragma unroll
   for (int k = 0; k < kOzSliceBatch; ++k) {
     vi[k] = 0;
     vf[k] = 0;
-    if (k < ns) {
+    if (k < ksplit) {
       vi[k] = qp.qi[(size_t)k * stride + o];
       if constexpr (ONCE) vf[k] = qp.ql[(size_t)k * stride + o];
       else vf[k] = qp.qf[(size_t)k * stride + o];
@@ -569,10 +571,11 @@ __device__ __forceinline__ double oz_slice_value(const OzPart& qp, size_t o, siz
   typename std::conditional<ONCE, long long, double>::type sf = 0;
 #pragma unroll
   for (int k = 0; k < kOzSliceBatch; ++k) {
+    if (k >= ns) break;
     si += vi[k];
     if constexpr (ONCE) sf += vf[k];
     else if (k == 0) sf = oz_f32_to_f64(vf[0]);  // = 0 + vf[0]
-    else if (k < ns) sf += oz_f32_to_f64(vf[k]);
+    else sf += oz_f32_to_f64(vf[k]);
   }
   for (int k = kOzSliceBatch; k < ns; ++k) {
     si += qp.qi[(size_t)k * stride + o];
@@ -611,7 +614,8 @@ __global__ void k_oz_sum(int n, int nW, const double* __restrict__ Qpart, double
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(q / n), i = (int)(q % n);  // consecutive threads: consecutive rows of column j
     const int ns = oz_slices(i / kOzMT, nW, nctas, U);
-    Q[(size_t)i * KP + j] = oz_scale(oz_slice_value<ONCE>(qp, q, total, ns), emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
+    Q[(size_t)i * KP + j] =
+        oz_scale(oz_slice_value<ONCE>(qp, q, total, ns, ksplit), emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
   }
   if (blockIdx.x == 0 && threadIdx.x < KP) emaxP[threadIdx.x] = 0;
 }
@@ -646,7 +650,7 @@ k_oz_sum_gram(int n, int nW, const double* __restrict__ Qpart, const double* __r
       double y = 0.0;
       if (i < r1) {
         const int ns = oz_slices(i / kOzMT, nW, nctas, U);
-        y = oz_scale(oz_slice_value<ONCE>(qp, (size_t)j * n + i, total, ns),
+        y = oz_scale(oz_slice_value<ONCE>(qp, (size_t)j * n + i, total, ns, ksplit),
                      emaxA[i] - 1022 + emaxP[kMaxKP + j] - 1022);
       }
       Ys[rr * KP + j] = y;
